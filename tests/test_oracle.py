@@ -1,0 +1,298 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against things other than itself:
+* the four partition tables the paper prints for its worked example;
+* brute-force k-bisimilarity iterated pair by pair from the definitions;
+* closed forms (paths, cycles, trees, edgeless graphs, symmetric graphs);
+* invariants the paper states (refinement, counts never drop, stop on a
+  stable count) and invariance under vertex renumbering.
+A last group plants plausible mistakes in a throw-away Python copy of the
+signature step and shows that the brute-force pin catches every one.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from oracle import bruteforce
+from paper_fixture import load, partition
+
+
+# ---------------------------------------------------------------- paper tables
+
+
+@pytest.mark.parametrize("table", ["fw", "bw", "sch", "kau"])
+def test_paper_tables_oracle(table):
+    g, tables = load()
+    t = tables[table]
+    L, C, _ = oracle.refine_graph(g, t["direction"], t["use_vertex_labels"], t["use_edge_labels"], k=2,
+                                  early_stop=False)
+    for i, expected in t["levels"].items():
+        assert partition(L[i]) == expected, (table, i)
+        assert C[i] == len(expected)
+
+
+@pytest.mark.parametrize("table", ["fw", "bw", "sch", "kau"])
+def test_paper_tables_bruteforce(table):
+    g, tables = load()
+    t = tables[table]
+    src, dst, lab = g.edges()
+    ids, Rs = bruteforce.levels(g.n, src, dst, lab, g.vlabel, t["direction"], t["use_vertex_labels"],
+                                t["use_edge_labels"], 2)
+    for i, expected in t["levels"].items():
+        assert bruteforce.is_equivalence(Rs[i])
+        assert partition(ids[i]) == expected, (table, i)
+
+
+def test_generator_matches_fixture():
+    g, _ = load()
+    h = graphgen.paper_example()
+    assert h.n == g.n and h.m == g.m
+    assert np.array_equal(h.row_offsets, g.row_offsets)
+    assert np.array_equal(h.col, g.col)
+    # label ids differ in naming only; the induced partitions must agree
+    assert partition(h.vlabel) == partition(g.vlabel)
+    assert partition(h.elabel) == partition(g.elabel)
+
+
+def test_schaetzle_example_stable_at_level_one():
+    # Section 3.3: full bisimulation of the example is reached at k = 1
+    g, tables = load()
+    t = tables["sch"]
+    L, C, lc = oracle.refine_graph(g, t["direction"], False, True, k=10, early_stop=True)
+    assert lc == 2 and C.tolist() == [1, 3] + [3] * 9
+    assert all(np.array_equal(L[i], L[1]) for i in range(1, 11))
+
+
+# ---------------------------------------------------------------- brute force
+
+
+def _random_cases(count, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for _ in range(count):
+        g = graphgen.tiny_random(rng, n_max=10, m_max=24, n_labels=int(rng.integers(1, 4)))
+        d = int(rng.integers(0, 3))
+        vl = bool(rng.integers(0, 2))
+        el = bool(rng.integers(0, 2))
+        k = int(rng.integers(0, 6))
+        yield g, d, vl, el, k
+
+
+def test_oracle_matches_bruteforce_random_tiny():
+    for g, d, vl, el, k in _random_cases(400, 11):
+        L, C, _ = oracle.refine_graph(g, d, vl, el, k=k, early_stop=False)
+        src, dst, lab = g.edges()
+        ids, Rs = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k)
+        for i in range(k + 1):
+            assert L[i].tolist() == ids[i], (d, vl, el, i)
+            assert C[i] == max(ids[i]) + 1
+
+
+@pytest.mark.slow
+def test_oracle_matches_bruteforce_many():
+    for g, d, vl, el, k in _random_cases(4000, 12):
+        L, _, _ = oracle.refine_graph(g, d, vl, el, k=k, early_stop=False)
+        src, dst, lab = g.edges()
+        ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k)
+        assert [r.tolist() for r in L] == ids
+
+
+def test_bruteforce_relation_is_equivalence():
+    for g, d, vl, el, k in itertools.islice(_random_cases(60, 13), 60):
+        src, dst, lab = g.edges()
+        _, Rs = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k)
+        assert all(bruteforce.is_equivalence(R) for R in Rs)
+
+
+# ---------------------------------------------------------------- closed forms
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 13])
+def test_path_counts(n):
+    # directed path, out-edges: vertex v is distinguished by its distance to the
+    # sink, capped at i, so level i has min(i+1, n) blocks
+    g = graphgen.path_graph(n)
+    L, C, _ = oracle.refine_graph(g, 0, False, False, k=15, early_stop=False)
+    assert C.tolist() == [min(i + 1, n) for i in range(16)]
+    # in-edges: distance from the source instead
+    L2, C2, _ = oracle.refine_graph(g, 1, False, False, k=15, early_stop=False)
+    assert C2.tolist() == [min(i + 1, n) for i in range(16)]
+
+
+@pytest.mark.parametrize("n", [1, 3, 8])
+def test_cycle_single_block(n):
+    g = graphgen.cycle_graph(n)
+    for d in (0, 1, 2):
+        _, C, _ = oracle.refine_graph(g, d, False, False, k=6, early_stop=False)
+        assert C.tolist() == [1] * 7
+
+
+def test_edgeless_graph_keeps_level0():
+    g = graphgen.from_edges(7, [], [], [], [3, 1, 3, 2, 1, 1, 9])
+    for d in (0, 1, 2):
+        L, C, lc = oracle.refine_graph(g, d, True, True, k=5, early_stop=False)
+        assert C.tolist() == [4] * 6
+        assert all(np.array_equal(L[i], L[0]) for i in range(6))
+        assert L[0].tolist() == [0, 1, 0, 2, 1, 1, 3]
+
+
+@pytest.mark.parametrize("h", [0, 1, 3, 5])
+def test_binary_tree_counts(h):
+    # out-edges: blocks are heights (distance to the leaves) capped at i
+    g = graphgen.binary_tree(h)
+    _, C, _ = oracle.refine_graph(g, 0, False, False, k=8, early_stop=False)
+    assert C.tolist() == [min(i + 1, h + 1) for i in range(9)]
+    # in-edges: blocks are depths capped at i
+    _, C2, _ = oracle.refine_graph(g, 1, False, False, k=8, early_stop=False)
+    assert C2.tolist() == [min(i + 1, h + 1) for i in range(9)]
+
+
+def test_symmetric_graph_directions_agree():
+    rng = np.random.Generator(np.random.PCG64(5))
+    for _ in range(30):
+        n = int(rng.integers(1, 30))
+        m = int(rng.integers(0, 60))
+        s = rng.integers(0, n, size=m)
+        t = rng.integers(0, n, size=m)
+        lab = rng.integers(0, 3, size=m)
+        g = graphgen.from_edges(n, np.concatenate([s, t]), np.concatenate([t, s]), np.concatenate([lab, lab]),
+                                rng.integers(0, 2, size=n))
+        outs = [oracle.refine_graph(g, d, True, True, k=6, early_stop=False)[0] for d in (0, 1, 2)]
+        assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+# ---------------------------------------------------------------- invariants
+
+
+def _tiny_config_graph():
+    return graphgen.make(graphgen.CONFIG_TINY)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_invariants_er(d):
+    g = _tiny_config_graph()
+    L, C, lc = oracle.refine_graph(g, d, True, True, k=10, early_stop=False)
+    for i in range(11):
+        ids = L[i]
+        # canonical: first occurrences of ids appear in order 0,1,2,...
+        _, first = np.unique(ids, return_index=True)
+        assert np.array_equal(np.sort(first), first)
+        assert ids.min() == 0 and ids.max() == C[i] - 1 and C[i] <= g.n
+        if i > 0:
+            assert C[i] >= C[i - 1]
+            # level i refines level i-1: each new block maps to one old block
+            pairs = np.unique(np.stack([ids, L[i - 1]], 1), axis=0)
+            assert pairs.shape[0] == C[i]
+
+
+def test_early_stop_matches_full_run():
+    for d in (0, 1, 2):
+        g = graphgen.erdos_renyi(300, 400, 2, 2, seed=d)
+        A, CA, la = oracle.refine_graph(g, d, True, True, k=30, early_stop=True)
+        B, CB, lb = oracle.refine_graph(g, d, True, True, k=30, early_stop=False)
+        assert np.array_equal(A, B) and np.array_equal(CA, CB)
+        assert lb == 30 and la <= 30
+        if la < 30:
+            assert CA[la] == CA[la - 1]
+
+
+def test_vertex_renumbering_invariance():
+    g = graphgen.erdos_renyi(500, 2000, 3, 3, seed=9)
+    rng = np.random.Generator(np.random.PCG64(2))
+    perm = rng.permutation(g.n)  # new id of old vertex v is perm[v]
+    src, dst, lab = g.edges()
+    vl = np.empty_like(g.vlabel)
+    vl[perm] = g.vlabel
+    h = graphgen.from_edges(g.n, perm[src], perm[dst], lab, vl)
+    for d in (0, 1, 2):
+        A, CA, _ = oracle.refine_graph(g, d, True, True, k=6, early_stop=False)
+        B, CB, _ = oracle.refine_graph(h, d, True, True, k=6, early_stop=False)
+        assert np.array_equal(CA, CB)
+        for i in range(7):
+            # old vertex v is new vertex perm[v]
+            assert partition(A[i]) == partition(B[i][perm])
+
+
+def test_initial_partition_equals_label_partition():
+    g = graphgen.erdos_renyi(400, 1500, 5, 3, seed=4)
+    A, CA, _ = oracle.refine_graph(g, 0, True, True, k=6, early_stop=False)
+    B, CB, _ = oracle.refine_graph(g, 0, False, True, k=6, early_stop=False, initial=g.vlabel * 7 - 3)
+    assert np.array_equal(A, B) and np.array_equal(CA, CB)
+
+
+def test_own_block_reading_is_harmless_without_labels():
+    # Schaetzle's signature omits the vertex's own block; with P_0 = {V} keeping
+    # it changes nothing (P_i refines P_{i-1}).  Compare with a signature-only
+    # refinement written here.
+    g = graphgen.erdos_renyi(300, 700, 1, 3, seed=8)
+    L, _, _ = oracle.refine_graph(g, 0, False, True, k=6, early_stop=False)
+    prev = np.zeros(g.n, dtype=np.int64)
+    for i in range(1, 7):
+        sigs = [oracle.signature(g.row_offsets, g.col, g.elabel, prev, v) for v in range(g.n)]
+        ids, cur = {}, np.empty(g.n, dtype=np.int64)
+        for v in range(g.n):
+            cur[v] = ids.setdefault(sigs[v], len(ids))
+        assert np.array_equal(cur, L[i])
+        prev = cur
+
+
+# ---------------------------------------------------------------- the pins catch planted mistakes
+
+
+def _mutant_refine(g, d, vl, el, k, mistake):
+    """A deliberately simple signature refinement with one planted mistake."""
+    n = g.n
+    src, dst, lab = g.edges()
+    if mistake == "transposed":
+        src, dst = dst, src
+    labels = g.vlabel if vl else np.zeros(n, dtype=np.int64)
+    ids0 = {}
+    prev = np.array([ids0.setdefault(int(x), len(ids0)) for x in labels])
+    out = [prev]
+    for _ in range(k):
+        sig = [[] for _ in range(n)]
+        for s, t, l in zip(src, dst, lab):
+            ll = int(l) if (el and mistake != "drop_label") else 0
+            if d in (0, 2):
+                sig[s].append((0, ll, int(prev[t])))
+            if d in (1, 2):
+                sig[t].append((1, ll, int(prev[s])))
+        keys = []
+        for v in range(n):
+            body = tuple(sorted(sig[v])) if mistake == "multiset" else tuple(sorted(set(sig[v])))
+            own = 0 if mistake == "drop_own_block" else int(prev[v])
+            keys.append((own, body))
+        ids = {}
+        prev = np.array([ids.setdefault(kk, len(ids)) for kk in keys])
+        out.append(prev)
+    return out
+
+
+@pytest.mark.parametrize("mistake", ["drop_own_block", "multiset", "drop_label", "transposed"])
+def test_bruteforce_catches_planted_mistakes(mistake):
+    caught = False
+    for g, d, vl, el, k in _random_cases(300, 21):
+        if mistake == "drop_own_block":
+            vl = True
+        if mistake == "drop_label":
+            el = True
+        if mistake == "transposed":
+            d = 0
+        k = max(k, 2)
+        src, dst, lab = g.edges()
+        ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k)
+        got = _mutant_refine(g, d, vl, el, k, mistake)
+        if any(list(got[i]) != ids[i] for i in range(k + 1)):
+            caught = True
+            break
+    assert caught, mistake
+
+
+def test_unmutated_copy_agrees():
+    for g, d, vl, el, k in _random_cases(100, 22):
+        src, dst, lab = g.edges()
+        ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k)
+        got = _mutant_refine(g, d, vl, el, k, None)
+        assert [list(x) for x in got] == ids
