@@ -1,0 +1,350 @@
+"""Benchmark: stratified k-bisimulation edges/s per refinement round on GB300.
+
+Default workload: the large single graph (Chung-Lu power law, exponent 2.0,
+200M vertices, 2B edges, 5,000 vertex labels Zipf(1.5), 500 edge labels
+Zipf(1.2), out-edges, k = 10).  One step = one kb_refine call (levels 0..10,
+early stop on).  value = edges processed per round summed over the rounds of
+all timed steps / timed seconds.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large|rdf|tiny] [--k 10]
+
+With N > 1 (torchrun) every rank refines its own copy of the workload: the
+single-graph path does not shard, so ranks are replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import graphgen  # noqa: E402
+
+WORKLOADS = {
+    "large": graphgen.CONFIG_LARGE,
+    "rdf": graphgen.CONFIG_RDF,
+    "tiny": graphgen.CONFIG_TINY,
+}
+METRIC = "k-bisim edges/s per round"
+UNIT = "edges/s"
+
+
+def describe(name, cfg, k, direction):
+    d = {"workload": name, "n": cfg["n"], "m": cfg["m"], "k": k, "direction": direction,
+         "recipe": cfg["kind"], "seed": cfg["seed"]}
+    if cfg["kind"] == "chung_lu":
+        d.update(gamma_out=cfg["gamma_out"], gamma_in=cfg["gamma_in"], max_out_deg=cfg["max_out_deg"],
+                 vertex_labels="zipf(%g)/%d" % (cfg["zipf_v"], cfg["n_vlabels"]),
+                 edge_labels="zipf(%g)/%d" % (cfg["zipf_e"], cfg["n_elabels"]))
+    else:
+        d.update(vertex_labels="uniform/%d" % cfg["n_vlabels"], edge_labels="uniform/%d" % cfg["n_elabels"])
+    return d
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload_gpu(cfg, device):
+    import torch
+
+    if cfg["kind"] == "chung_lu" and cfg["m"] >= 50_000_000:
+        c = dict(cfg)
+        c.pop("kind")
+        d = graphgen.chung_lu_torch(device=device, **c)
+        torch.cuda.synchronize()
+        return d
+    g = graphgen.make(cfg)
+    return {"n": g.n, "m": g.m, "row_offsets": torch.from_numpy(g.row_offsets).to(device),
+            "col": torch.from_numpy(g.col).to(device), "elabel": torch.from_numpy(g.elabel).to(device),
+            "vlabel": torch.from_numpy(g.vlabel).to(device)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(cfg, k_rounds=1, target_s=15.0):
+    """The oracle, as it stands, single-threaded on a scaled-down graph of the
+    same recipe (one refinement round)."""
+    import oracle
+
+    factor = 0.005 if cfg["m"] >= 1e9 else (0.05 if cfg["m"] >= 1e8 else 1.0)
+    c = graphgen.scaled(cfg, factor) if factor != 1.0 else cfg
+    g = graphgen.make(c)
+    t0 = time.perf_counter()
+    oracle.refine_graph(g, 0, True, True, k=k_rounds, early_stop=False)
+    dt = time.perf_counter() - t0
+    return {"value": g.m * k_rounds / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle (single-threaded C++ map refinement) on the same recipe scaled to n=%d, m=%d, "
+                      "%d round(s) after level 0; %.1f s" % (g.n, g.m, k_rounds, dt)}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    cfg = WORKLOADS[args.workload]
+    factor = 0.005 if cfg["m"] >= 1e9 else (0.05 if cfg["m"] >= 1e8 else 1.0)
+    c = graphgen.scaled(cfg, factor) if factor != 1.0 else cfg
+    g = graphgen.make(c)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.refine_graph(g, 0, True, True, k=1, early_stop=False)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = g.m * len(times) / total
+    sample = ("each step: one oracle refinement round (plus level 0) on the %s recipe scaled to n=%d, m=%d, "
+              "single-threaded" % (args.workload, g.n, g.m))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": describe(args.workload, cfg, args.k, "out"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_2204_05821_gb300 as kb
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    device = "cuda:%d" % local
+    cfg = WORKLOADS[args.workload]
+    wl = make_workload_gpu(cfg, device)
+    dg = kb.DeviceGraph(wl["row_offsets"], wl["col"], wl["elabel"], wl["vlabel"])
+    n, m = dg.n, dg.m
+    k = args.k
+    opts = kb.Options(direction=kb.DIR_OUT)
+    ctx = kb.Context(local)
+    levels = torch.empty((k + 1, n), dtype=torch.int32, device=device)
+    stream = ctx.stream
+
+    def step():
+        return ctx.refine(dg, k, opts, out=levels)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ctx.set_timing(True)
+    fam_ms, fam_n = {}, {}
+    rounds = 0
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r = step()
+        rounds += r.levels_computed
+        _, fam = ctx.timing()
+        for name, (ms, cnt) in fam.items():
+            fam_ms[name] = fam_ms.get(name, 0.0) + ms
+            fam_n[name] = fam_n.get(name, 0) + cnt
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ctx.set_timing(False)
+    elapsed = ev0.elapsed_time(ev1) / 1000.0
+    if dist:
+        t = torch.tensor([elapsed], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        rt = torch.tensor([rounds], device=device, dtype=torch.float64)
+        dist.all_reduce(rt)
+        total_edge_rounds = float(rt.item()) * m
+    else:
+        total_edge_rounds = float(rounds) * m
+    value = total_edge_rounds / elapsed
+
+    # roofline of the dominant kernel family
+    dom = max(fam_ms, key=lambda kname: fam_ms[kname])
+    hub_thr = 2048
+    deg = (wl["row_offsets"][1:] - wl["row_offsets"][:-1])
+    tile_edges = int(deg[deg <= hub_thr].sum().item())
+    hub_edges = m - tile_edges
+    n_hubs = int((deg > hub_thr).sum().item())
+    algo_bytes = {
+        # 12 B per staged edge (neighbour id, edge label, gathered block) plus
+        # per vertex: row offset 8, own block 4, slot write 4, table entry 8
+        "signature": 12 * tile_edges + 24 * n,
+        "hub_chunk": 12 * hub_edges,
+        "hub_final": 24 * n_hubs,
+        # bitmap scan + per vertex: slot 4, table entry 8, level write 4
+        "renumber": 16 * n + n // 8,
+        "other": n // 8,
+    }
+    peak, peak_kind = peaks()
+    per_launch_ms = fam_ms[dom] / max(1, fam_n[dom])
+    achieved = algo_bytes.get(dom, 0) / (per_launch_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "kernel_share": {kname: fam_ms[kname] / sum(fam_ms.values()) for kname in fam_ms},
+                "per_launch_ms": {kname: fam_ms[kname] / max(1, fam_n[kname]) for kname in fam_ms}}
+    launches = int(sum(fam_n.values()))
+
+    # end to end through the host-buffer entry point, pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hrow = wl["row_offsets"].cpu().pin_memory()
+        hcol = wl["col"].cpu().pin_memory()
+        hel = wl["elabel"].cpu().pin_memory()
+        hvl = wl["vlabel"].cpu().pin_memory()
+        hout = torch.empty((k + 1, n), dtype=torch.int32).pin_memory()
+        np_row, np_col, np_el, np_vl, np_out = (hrow.numpy(), hcol.numpy(), hel.numpy(), hvl.numpy(), hout.numpy())
+        ctx.refine_host(np_row, np_col, np_el, np_vl, k, opts, out=np_out)  # warm
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e_rounds = 0
+        e_steps = max(1, min(args.steps, 3))
+        for _ in range(e_steps):
+            rr = ctx.refine_host(np_row, np_col, np_el, np_vl, k, opts, out=np_out)
+            e_rounds += rr.levels_computed
+        et = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([et], device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        h2d = hrow.numel() * 8 + (hcol.numel() + hel.numel()) * 4 + hvl.numel() * 4
+        d2h = hout.numel() * 4
+        e2e = {"value": e_rounds * m * world / et, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e_steps}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": dict(describe(args.workload, cfg, k, "out"),
+                               l2="inputs larger than L2 (CSR %.1f GB); no flush" % ((8 * (n + 1) + 8 * m) / 1e9),
+                               parallelism="replicas" if world > 1 else "single GPU",
+                               rounds_per_step=rounds / args.steps),
+                "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(cfg)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * kbisim.h -- C ABI of the GB300 stratified k-bisimulation library.
+ *
+ * The library partitions the vertices of a labelled directed graph into the
+ * blocks of its stratified k-bisimulation, for every level 0..k, by signature
+ * refinement (paper Section 4.1, Alg. 1, with the signature of Def.
+ * "signature" and the equivalences of Defs. "fw-bisim", "bw-bisim",
+ * "edge-labeled-fw-bisimulation" and "vertex-labeled-bw-bisimulation"):
+ *
+ *   level 0   P_0 = vertices grouped by vertex label (or {V} without labels);
+ *   level i   u, v share a block iff they shared one at level i-1 and
+ *             { (d, edge label, block_{i-1}(w)) : edges (v, w) in direction d }
+ *             is the same set for both.
+ *
+ * Every level is returned with canonical block ids: the blocks of a level are
+ * numbered 0, 1, 2, ... by increasing smallest member vertex id.  Results are
+ * exact integers and do not depend on hashing, table size, thread timing or
+ * batch composition.
+ *
+ * Conventions for every call:
+ *   - Every pointer documented "device" must point to memory of the context's
+ *     device; "host" pointers to ordinary host memory.  The caller owns all
+ *     inputs and outputs and keeps them alive until the call returns.
+ *   - Calls run on the context's stream.  Calls that return counts on the
+ *     host synchronise that stream before returning; all others are
+ *     asynchronous.
+ *   - No call throws, aborts or traps.  Errors are returned as kb_status; a
+ *     human-readable message for the last error is kb_last_error(ctx).
+ *   - Vertex ids and block ids are int32, so n <= 2^31 - 2.  Edge offsets are
+ *     int64.
+ */
+#ifndef KBISIM_H_
+#define KBISIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KB_OK = 0,
+    KB_ERR_INVALID_ARG = 1,   /* bad sizes, null pointers, non-monotone offsets, ids out of range */
+    KB_ERR_OOM = 2,           /* device allocation failed or caller workspace too small */
+    KB_ERR_TABLE_FULL = 3,    /* block table probe limit hit (internal; retried with a larger table) */
+    KB_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+    KB_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+    KB_ERR_DEVICE_CHECK = 6,  /* a device-side consistency check failed */
+    KB_ERR_NOT_FOUND = 7      /* unknown server ticket */
+} kb_status;
+
+typedef enum { KB_DIR_OUT = 0, KB_DIR_IN = 1, KB_DIR_BOTH = 2 } kb_direction;
+
+/* A graph in out-edge CSR form.  All arrays are DEVICE pointers owned by the
+ * caller (for kb_refine_host: HOST pointers).
+ *   n               number of vertices, 0 <= n <= 2^31 - 2
+ *   m               number of edges, m >= 0
+ *   row_offsets     int64[n+1], row_offsets[0] = 0, non-decreasing, row_offsets[n] = m;
+ *                   the out-edges of v are row_offsets[v] .. row_offsets[v+1]-1
+ *   col_indices     int32[m], target of each edge, 0 <= target < n (self loops and
+ *                   parallel edges allowed: a multigraph)
+ *   edge_labels     int32[m] or NULL; one label per edge, any int32 value.  The paper
+ *                   maps edges to label SETS (Def. "multi-relational-labeled-property-
+ *                   graph"); a caller interns each set to one int32.
+ *   vertex_labels   int32[n] or NULL; one label per vertex, any int32 value. */
+typedef struct {
+    int64_t n;
+    int64_t m;
+    const int64_t* row_offsets;
+    const int32_t* col_indices;
+    const int32_t* edge_labels;
+    const int32_t* vertex_labels;
+} kb_graph;
+
+/* Refinement options.  Start from kb_options_default() (or a preset) and
+ * change fields; zero in a tuning field means "library default".
+ *   direction          out-edges (forward), in-edges (backward) or both
+ *   use_vertex_labels  level 0 groups by vertex label (else P_0 = {V})
+ *   use_edge_labels    pairs carry the edge label (else every label reads 0)
+ *   early_stop         stop once a round keeps the block count (paper Alg. 1, the
+ *                      count test); later levels are then copies
+ *   load_factor        block-table load factor in (0, 0.9]; 0 -> 0.5
+ *   hub_threshold      vertices with more edges than this (in the chosen direction)
+ *                      take the multi-CTA hub path; 0 -> default; at most 2048
+ *   hash_mode          0: full 64-bit signature hash.  1: weak hash of the previous
+ *                      block only, which forces collisions (tests the full
+ *                      signature compare); results are identical in both modes
+ *   validate           1: check offsets and ids on the device before refining */
+typedef struct {
+    int32_t direction;
+    int32_t use_vertex_labels;
+    int32_t use_edge_labels;
+    int32_t early_stop;
+    float load_factor;
+    int32_t hub_threshold;
+    int32_t hash_mode;
+    int32_t validate;
+    int32_t reserved[8];
+} kb_options;
+
+typedef struct kb_context kb_context;
+
+/* Defaults: OUT, vertex and edge labels on, early stop on, validate on. */
+kb_options kb_options_default(void);
+/* Schaetzle et al. preset (paper eq. "gsm:schaetzle", Def. "edge-labeled-fw-
+ * bisimulation"): OUT edges, edge labels, no vertex labels. */
+kb_options kb_options_schaetzle(void);
+/* Kaushik et al. preset (paper eq. "gsm:kaushik", Def. "vertex-labeled-bw-
+ * bisimulation"): IN edges, vertex labels, no edge labels. */
+kb_options kb_options_kaushik(void);
+
+const char* kb_status_string(kb_status status);
+
+/* Create a context on `device` bound to `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  The context caches device scratch between calls. */
+kb_status kb_create(kb_context** ctx, int device, void* stream);
+kb_status kb_destroy(kb_context* ctx);
+const char* kb_last_error(const kb_context* ctx);
+
+/* Bytes of device scratch that kb_refine / kb_refine_from need for this graph
+ * and these options (reads row_offsets on the device; synchronises). */
+kb_status kb_workspace_size(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k,
+                            size_t* bytes);
+
+/* Use caller-owned device memory as scratch (e.g. a torch tensor).  The
+ * buffer must stay alive while calls that use it run.  ptr = NULL reverts to
+ * library-allocated scratch.  Calls fail with KB_ERR_OOM if it is too small. */
+kb_status kb_set_workspace(kb_context* ctx, void* device_ptr, size_t bytes);
+
+/* Refine levels 0..k.
+ *   levels           DEVICE int32[(k+1)*n]; row i (levels + i*n) receives the
+ *                    canonical block id of every vertex at level i
+ *   counts           HOST int64[k+1]; counts[i] = number of blocks at level i
+ *   levels_computed  HOST, may be NULL; the last level actually refined (< k when
+ *                    early_stop found a stable partition; rows after it are copies)
+ * Synchronises the stream once per round to read the block count. */
+kb_status kb_refine(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k,
+                    int32_t* levels, int64_t* counts, int* levels_computed);
+
+/* Resume from a known level (refinement depends only on the graph and the
+ * previous level).  start is DEVICE int32[n] holding any partition (equal
+ * values = same block); row i_start of `levels` receives its canonical
+ * renumbering and rows i_start+1..k the refined levels.  Rows below i_start
+ * are left untouched; counts[0..i_start-1] likewise.  With i_start = 0 this
+ * refines an arbitrary starting partition instead of the label partition. */
+kb_status kb_refine_from(kb_context* ctx, const kb_graph* g, const kb_options* opt,
+                         const int32_t* start, int i_start, int k, int32_t* levels,
+                         int64_t* counts, int* levels_computed);
+
+/* kb_refine with HOST buffers: g's arrays and `levels` (int32[(k+1)*n]) are host
+ * memory (pinned memory copies fastest).  The library copies the graph to the
+ * device, refines, and copies every level back.  Synchronises. */
+kb_status kb_refine_host(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k,
+                         int32_t* levels, int64_t* counts, int* levels_computed);
+
+/* Per-round and per-kernel timing of the last refine call, in milliseconds,
+ * measured with CUDA events on the context stream when enabled.
+ *   kb_set_timing(ctx, 1) enables event recording (small overhead).
+ *   round_ms[i] for i < n_rounds: device time of refinement round i+1.
+ *   kernel_ms[j] / kernel_launches[j] for j < KB_KERNEL_COUNT: summed device time
+ *   and launches of each kernel family inside the rounds. */
+enum {
+    KB_KERNEL_SIGNATURE = 0,   /* tile signature + dedup + hash + block-table insert */
+    KB_KERNEL_HUB_CHUNK = 1,   /* hub pairs: chunk dedup + global set insert */
+    KB_KERNEL_HUB_FINAL = 2,   /* hub hash + block-table insert */
+    KB_KERNEL_RENUMBER = 3,    /* prefix scan of block minima + canonical assignment */
+    KB_KERNEL_OTHER = 4,       /* clears, copies */
+    KB_KERNEL_COUNT = 5
+};
+kb_status kb_set_timing(kb_context* ctx, int enable);
+kb_status kb_get_timing(const kb_context* ctx, float* round_ms, int max_rounds, int* n_rounds,
+                        float* kernel_ms, int64_t* kernel_launches);
+
+/* Batched refinement of G independent graphs given as one disjoint union.
+ *   union_graph            DEVICE CSR over all vertices; edges never cross graphs
+ *   graph_vertex_offsets   HOST int64[G+1]; graph j owns vertices
+ *                          [off[j], off[j+1]) of the union
+ *   k_per_graph            HOST int32[G]; each graph's own k (>= 0)
+ *   levels                 DEVICE int32[(k_max+1)*n_total]; row i holds every graph's
+ *                          level min(i, its last level) with ids LOCAL to the graph
+ *                          (canonical per graph, exactly as a solo kb_refine)
+ *   counts                 HOST int64[G*(k_max+1)]; counts[j*(k_max+1)+i]
+ *   levels_computed        HOST int32[G] or NULL
+ * Rounds run for all active graphs at once: one signature launch per round over
+ * the union, the whole k_max-round loop captured once in a CUDA graph and
+ * replayed, and a device-side per-graph stop flag (no host sync per round). */
+kb_status kb_refine_batch(kb_context* ctx, const kb_graph* union_graph,
+                          const int64_t* graph_vertex_offsets, int64_t G,
+                          const int32_t* k_per_graph, const kb_options* opt, int32_t* levels,
+                          int64_t* counts, int32_t* levels_computed);
+
+/* Autotuner: time refinement rounds of `g` for a grid of load factors and hub
+ * thresholds, keep the fastest in the context (used when the options leave
+ * those fields 0) and report it.  Synchronises. */
+kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt, int rounds,
+                      float* best_load_factor, int32_t* best_hub_threshold, float* best_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KBISIM_H_ */

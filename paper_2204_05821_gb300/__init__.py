@@ -1,0 +1,296 @@
+"""GB300 stratified k-bisimulation by signature refinement.
+
+Thin Python binding over the C ABI in ``include/kbisim.h`` (argument
+marshalling only: every step of every refinement round runs in the CUDA
+kernels of ``libkbisim.so``).  PyTorch provides device memory and streams.
+
+Method: paper Section 4.1 (Alg. 1) with the signature of Def. "signature" and
+the equivalences of Sections 3.2-3.3.  Levels come back with canonical block
+ids (blocks numbered by their smallest member vertex).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import _capi
+from ._capi import KB_DIR_BOTH as DIR_BOTH
+from ._capi import KB_DIR_IN as DIR_IN
+from ._capi import KB_DIR_OUT as DIR_OUT
+from ._capi import KbError
+
+__all__ = [
+    "DIR_OUT", "DIR_IN", "DIR_BOTH", "Options", "DeviceGraph", "Context", "Result", "KbError", "refine",
+    "library_path",
+]
+
+
+def library_path() -> str:
+    return _capi.library_path()
+
+
+@dataclass
+class Options:
+    """Mirror of ``kb_options`` (see include/kbisim.h for every field)."""
+
+    direction: int = DIR_OUT
+    use_vertex_labels: bool = True
+    use_edge_labels: bool = True
+    early_stop: bool = True
+    load_factor: float = 0.0
+    hub_threshold: int = 0
+    hash_mode: int = 0
+    validate: bool = True
+
+    @classmethod
+    def schaetzle(cls, **kw) -> "Options":
+        """Edge-labelled forward bisimulation (Def. "edge-labeled-fw-bisimulation")."""
+        return cls(direction=DIR_OUT, use_vertex_labels=False, use_edge_labels=True, **kw)
+
+    @classmethod
+    def kaushik(cls, **kw) -> "Options":
+        """Vertex-labelled backward bisimulation (Def. "vertex-labeled-bw-bisimulation")."""
+        return cls(direction=DIR_IN, use_vertex_labels=True, use_edge_labels=False, **kw)
+
+    def to_c(self) -> _capi.KbOptions:
+        o = _capi.load().kb_options_default()
+        o.direction = int(self.direction)
+        o.use_vertex_labels = int(bool(self.use_vertex_labels))
+        o.use_edge_labels = int(bool(self.use_edge_labels))
+        o.early_stop = int(bool(self.early_stop))
+        o.load_factor = float(self.load_factor)
+        o.hub_threshold = int(self.hub_threshold)
+        o.hash_mode = int(self.hash_mode)
+        o.validate = int(bool(self.validate))
+        return o
+
+
+class DeviceGraph:
+    """A CSR graph held in torch tensors on one CUDA device.
+
+    row_offsets int64[n+1], col int32[m], elabel int32[m] or None,
+    vlabel int32[n] or None (the layout of ``kb_graph``)."""
+
+    def __init__(self, row_offsets, col, elabel=None, vlabel=None):
+        import torch
+
+        self.row_offsets = row_offsets
+        self.col = col
+        self.elabel = elabel
+        self.vlabel = vlabel
+        self.n = int(row_offsets.shape[0]) - 1
+        self.m = int(col.shape[0])
+        for name, t, dt in (("row_offsets", row_offsets, torch.int64), ("col", col, torch.int32),
+                            ("elabel", elabel, torch.int32), ("vlabel", vlabel, torch.int32)):
+            if t is None:
+                continue
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous CUDA %s tensor" % (name, dt))
+
+    @classmethod
+    def from_numpy(cls, g, device="cuda") -> "DeviceGraph":
+        import torch
+
+        def t(a):
+            return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(device)
+
+        return cls(t(g.row_offsets.astype(np.int64)), t(g.col.astype(np.int32)),
+                   t(None if g.elabel is None else g.elabel.astype(np.int32)),
+                   t(None if g.vlabel is None else g.vlabel.astype(np.int32)))
+
+    @classmethod
+    def from_tensors(cls, d: dict) -> "DeviceGraph":
+        return cls(d["row_offsets"], d["col"], d.get("elabel"), d.get("vlabel"))
+
+    def to_c(self) -> _capi.KbGraph:
+        def p(t):
+            return None if t is None else t.data_ptr()
+
+        return _capi.KbGraph(self.n, self.m, p(self.row_offsets), p(self.col), p(self.elabel), p(self.vlabel))
+
+    @property
+    def device(self):
+        return self.row_offsets.device
+
+
+@dataclass
+class Result:
+    levels: "object"  # torch int32 [k+1, n] on the device (numpy for host calls)
+    counts: np.ndarray  # int64 [k+1]
+    levels_computed: int
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """A ``kb_context``: one device, one stream, cached scratch."""
+
+    def __init__(self, device: int = 0, stream=None, torch_workspace: bool = False):
+        import torch
+
+        self._lib = _capi.load()
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _capi.check(self._lib.kb_create(ctypes.byref(h), self.device, ctypes.c_void_p(stream.cuda_stream)))
+        self._h = h
+        self._torch_ws = torch_workspace
+        self._ws = None
+        self._ws_key = None
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.kb_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        _capi.check(st, self._h)
+
+    # -- scratch
+    def workspace_size(self, graph: DeviceGraph, k: int, options: Options = None) -> int:
+        options = options or Options()
+        g, o = graph.to_c(), options.to_c()
+        b = ctypes.c_size_t(0)
+        self._check(self._lib.kb_workspace_size(self._h, ctypes.byref(g), ctypes.byref(o), int(k), ctypes.byref(b)))
+        return int(b.value)
+
+    def _prepare_workspace(self, graph: DeviceGraph, k: int, options: Options):
+        if not self._torch_ws:
+            return
+        import torch
+
+        key = (graph.row_offsets.data_ptr(), graph.n, graph.m, options.direction, options.hub_threshold,
+               options.load_factor, options.use_edge_labels)
+        if self._ws is not None and self._ws_key == key:
+            return
+        need = self.workspace_size(graph, k, options)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=graph.device)
+        self._ws_key = key
+        self._check(self._lib.kb_set_workspace(self._h, ctypes.c_void_p(self._ws.data_ptr()),
+                                               self._ws.numel()))
+
+    # -- refinement
+    def refine(self, graph: DeviceGraph, k: int, options: Options = None, out=None) -> Result:
+        import torch
+
+        options = options or Options()
+        self._prepare_workspace(graph, k, options)
+        levels = out if out is not None else torch.empty((k + 1, graph.n), dtype=torch.int32, device=graph.device)
+        counts = np.zeros(k + 1, dtype=np.int64)
+        lc = ctypes.c_int(0)
+        g, o = graph.to_c(), options.to_c()
+        self._check(self._lib.kb_refine(self._h, ctypes.byref(g), ctypes.byref(o), int(k),
+                                        ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts), ctypes.byref(lc)))
+        return Result(levels, counts, int(lc.value))
+
+    def refine_from(self, graph: DeviceGraph, start, i_start: int, k: int, options: Options = None,
+                    levels=None, counts=None) -> Result:
+        import torch
+
+        options = options or Options()
+        self._prepare_workspace(graph, k, options)
+        if levels is None:
+            levels = torch.zeros((k + 1, graph.n), dtype=torch.int32, device=graph.device)
+        if counts is None:
+            counts = np.zeros(k + 1, dtype=np.int64)
+        lc = ctypes.c_int(0)
+        g, o = graph.to_c(), options.to_c()
+        self._check(self._lib.kb_refine_from(self._h, ctypes.byref(g), ctypes.byref(o),
+                                             ctypes.c_void_p(start.data_ptr()), int(i_start), int(k),
+                                             ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts), ctypes.byref(lc)))
+        return Result(levels, counts, int(lc.value))
+
+    def refine_host(self, row_offsets, col, elabel, vlabel, k: int, options: Options = None, out=None) -> Result:
+        """kb_refine_host: numpy (ideally pinned) host arrays in and out."""
+        options = options or Options()
+        row_offsets = np.ascontiguousarray(row_offsets, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        n, m = row_offsets.shape[0] - 1, col.shape[0]
+        el = None if elabel is None else np.ascontiguousarray(elabel, dtype=np.int32)
+        vl = None if vlabel is None else np.ascontiguousarray(vlabel, dtype=np.int32)
+        levels = out if out is not None else np.empty((k + 1, n), dtype=np.int32)
+        counts = np.zeros(k + 1, dtype=np.int64)
+        lc = ctypes.c_int(0)
+        g = _capi.KbGraph(n, m, _np_ptr(row_offsets), _np_ptr(col), _np_ptr(el), _np_ptr(vl))
+        o = options.to_c()
+        self._check(self._lib.kb_refine_host(self._h, ctypes.byref(g), ctypes.byref(o), int(k), _np_ptr(levels),
+                                             _np_ptr(counts), ctypes.byref(lc)))
+        return Result(levels, counts, int(lc.value))
+
+    def refine_batch(self, union: DeviceGraph, vertex_offsets: Sequence[int], ks: Sequence[int],
+                     options: Options = None) -> Tuple[object, np.ndarray, np.ndarray]:
+        """kb_refine_batch over a disjoint union.  Returns (levels [k_max+1, n]
+        with graph-local ids, counts [G, k_max+1], levels_computed [G])."""
+        import torch
+
+        options = options or Options()
+        voff = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+        ks = np.ascontiguousarray(ks, dtype=np.int32)
+        G = int(ks.shape[0])
+        kmax = int(ks.max()) if G else 0
+        levels = torch.empty((kmax + 1, union.n), dtype=torch.int32, device=union.device)
+        counts = np.zeros((G, kmax + 1), dtype=np.int64)
+        lc = np.zeros(G, dtype=np.int32)
+        g, o = union.to_c(), options.to_c()
+        self._check(self._lib.kb_refine_batch(self._h, ctypes.byref(g), _np_ptr(voff), G, _np_ptr(ks),
+                                              ctypes.byref(o), ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts),
+                                              _np_ptr(lc)))
+        return levels, counts, lc
+
+    def autotune(self, graph: DeviceGraph, options: Options = None, rounds: int = 2):
+        options = options or Options()
+        lf = ctypes.c_float(0)
+        thr = ctypes.c_int32(0)
+        ms = ctypes.c_float(0)
+        g, o = graph.to_c(), options.to_c()
+        self._check(self._lib.kb_autotune(self._h, ctypes.byref(g), ctypes.byref(o), int(rounds), ctypes.byref(lf),
+                                          ctypes.byref(thr), ctypes.byref(ms)))
+        return float(lf.value), int(thr.value), float(ms.value)
+
+    # -- timing
+    def set_timing(self, enable: bool = True):
+        self._check(self._lib.kb_set_timing(self._h, int(bool(enable))))
+
+    def timing(self):
+        """(round_ms list, {kernel family: (ms, launches)}) of the last call."""
+        nr = ctypes.c_int(0)
+        rm = np.zeros(4096, dtype=np.float32)
+        km = np.zeros(_capi.KB_KERNEL_COUNT, dtype=np.float32)
+        kl = np.zeros(_capi.KB_KERNEL_COUNT, dtype=np.int64)
+        self._check(self._lib.kb_get_timing(self._h, _np_ptr(rm), 4096, ctypes.byref(nr), _np_ptr(km), _np_ptr(kl)))
+        fam = {name: (float(km[i]), int(kl[i])) for i, name in enumerate(_capi.KERNEL_NAMES)}
+        return rm[: nr.value].tolist(), fam
+
+
+_default = {}
+
+
+def refine(graph: DeviceGraph, k: int, options: Options = None) -> Result:
+    """Refine with a per-device default context on the current stream."""
+    dev = graph.device.index or 0
+    ctx = _default.get(dev)
+    if ctx is None:
+        ctx = _default[dev] = Context(dev)
+    return ctx.refine(graph, k, options)

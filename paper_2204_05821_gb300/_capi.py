@@ -1,0 +1,117 @@
+"""ctypes declarations mirroring include/kbisim.h (argument marshalling only).
+
+Loading fails loudly when the compiled library is missing: there is no CPU
+fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+KB_OK = 0
+KB_ERR_INVALID_ARG = 1
+KB_ERR_OOM = 2
+KB_ERR_TABLE_FULL = 3
+KB_ERR_TIMEOUT = 4
+KB_ERR_CUDA = 5
+KB_ERR_DEVICE_CHECK = 6
+KB_ERR_NOT_FOUND = 7
+
+KB_DIR_OUT, KB_DIR_IN, KB_DIR_BOTH = 0, 1, 2
+KB_KERNEL_COUNT = 5
+KERNEL_NAMES = ("signature", "hub_chunk", "hub_final", "renumber", "other")
+
+
+class KbGraph(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("m", ctypes.c_int64),
+        ("row_offsets", ctypes.c_void_p),
+        ("col_indices", ctypes.c_void_p),
+        ("edge_labels", ctypes.c_void_p),
+        ("vertex_labels", ctypes.c_void_p),
+    ]
+
+
+class KbOptions(ctypes.Structure):
+    _fields_ = [
+        ("direction", ctypes.c_int32),
+        ("use_vertex_labels", ctypes.c_int32),
+        ("use_edge_labels", ctypes.c_int32),
+        ("early_stop", ctypes.c_int32),
+        ("load_factor", ctypes.c_float),
+        ("hub_threshold", ctypes.c_int32),
+        ("hash_mode", ctypes.c_int32),
+        ("validate", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 8),
+    ]
+
+
+# (name, restype, argtypes) for every symbol the header declares
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+SIGNATURES = [
+    ("kb_options_default", KbOptions, []),
+    ("kb_options_schaetzle", KbOptions, []),
+    ("kb_options_kaushik", KbOptions, []),
+    ("kb_status_string", ctypes.c_char_p, [_I]),
+    ("kb_create", _I, [ctypes.POINTER(_P), _I, _P]),
+    ("kb_destroy", _I, [_P]),
+    ("kb_last_error", ctypes.c_char_p, [_P]),
+    ("kb_workspace_size", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I,
+                               ctypes.POINTER(ctypes.c_size_t)]),
+    ("kb_set_workspace", _I, [_P, _P, ctypes.c_size_t]),
+    ("kb_refine", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
+    ("kb_refine_from", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _P, _I, _I, _P, _P, _P]),
+    ("kb_refine_host", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
+    ("kb_set_timing", _I, [_P, _I]),
+    ("kb_get_timing", _I, [_P, _P, _I, _P, _P, _P]),
+    ("kb_refine_batch", _I, [_P, ctypes.POINTER(KbGraph), _P, _I64, _P, ctypes.POINTER(KbOptions), _P, _P, _P]),
+    ("kb_autotune", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libkbisim.so (building it first when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libkbisim.so is not built; run paper_2204_05821_gb300._build.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class KbError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (status_name(status), message))
+        self.status = status
+
+
+def status_name(status: int) -> str:
+    return load().kb_status_string(int(status)).decode()
+
+
+def check(status: int, ctx=None):
+    if status != KB_OK:
+        msg = load().kb_last_error(ctx).decode() if ctx else ""
+        raise KbError(status, msg)

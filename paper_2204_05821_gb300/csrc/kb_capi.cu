@@ -1,0 +1,712 @@
+// Host side of the C ABI declared in include/kbisim.h: contexts, workspace
+// planning, the per-round driver loop (paper Alg. 1: rounds 1..k with the
+// block-count stop test), host-buffer refinement and timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kb_internal.cuh"
+
+struct kb_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    // scratch: caller-provided or library-owned (grow-only)
+    void* user_ws = nullptr;
+    size_t user_ws_bytes = 0;
+    void* own_ws = nullptr;
+    size_t own_ws_bytes = 0;
+    // small persistent device state
+    kb::Counters* d_ctr = nullptr;
+    kb::Counters* h_ctr = nullptr;  // pinned
+    int32_t* d_hub_n = nullptr;
+    int32_t* h_hub_n = nullptr;  // pinned
+    void* hub_tmp = nullptr;     // unordered hub list during planning
+    size_t hub_tmp_bytes = 0;
+    void* plan_tmp = nullptr;    // in-degree scratch used by kb_workspace_size
+    size_t plan_tmp_bytes = 0;
+    // host-buffer refinement staging (library-owned)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    // autotuned defaults
+    float tuned_load_factor = 0.f;
+    int32_t tuned_hub_threshold = 0;
+    // timing
+    bool timing = false;
+    std::vector<float> round_ms;
+    float kernel_ms[KB_KERNEL_COUNT] = {};
+    int64_t kernel_launches[KB_KERNEL_COUNT] = {};
+    cudaEvent_t ev[2 * 8] = {};
+};
+
+namespace {
+
+using kb::Counters;
+
+kb_status fail(kb_context* ctx, kb_status st, const char* fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return st;
+}
+
+#define KB_CUDA(ctx, call)                                                                        \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail((ctx), KB_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+#define KB_TRY(expr)                       \
+    do {                                   \
+        kb_status s_ = (expr);             \
+        if (s_ != KB_OK) return s_;        \
+    } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+uint64_t next_pow2(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Device buffers of one refine call, carved from one workspace allocation.
+struct Plan {
+    int64_t n = 0, m = 0, m_proc = 0;
+    int dir = 0;
+    bool labels = false;
+    int thr = kb::kDefaultHubThreshold;
+    uint64_t cap = 0;
+    // hubs (host copies, ascending vertex id)
+    std::vector<int32_t> hub_v;
+    std::vector<int64_t> chunk_off, set_off, list_off;
+    // layout
+    size_t o_rowp = 0, o_colp = 0, o_labp = 0, o_cursor = 0, o_inpref = 0, o_i64tmp = 0;
+    size_t csr_bytes = 0;
+    size_t o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
+           o_listoff = 0, o_acc = 0, o_cnt = 0, o_sets = 0, o_lists = 0;
+    size_t total = 0;
+};
+
+bool needs_in_csr(int dir) { return dir == KB_DIR_IN || dir == KB_DIR_BOTH; }
+
+void layout_csr(Plan& P) {
+    size_t off = 0;
+    P.csr_bytes = 0;
+    if (!needs_in_csr(P.dir)) return;
+    auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+    P.o_rowp = take(sizeof(int64_t) * (size_t)(P.n + 1));
+    P.o_colp = take(sizeof(int32_t) * (size_t)P.m_proc);
+    P.o_labp = take(P.labels ? sizeof(int32_t) * (size_t)P.m_proc : 0);
+    P.o_cursor = take(sizeof(int64_t) * (size_t)(P.n + 1));
+    P.o_inpref = take(sizeof(int64_t) * (size_t)(P.n + 1));
+    P.o_i64tmp = take(sizeof(int64_t) * kb::scan_i64_tmp(P.n + 1));
+    P.csr_bytes = off;
+}
+
+void layout_round(Plan& P) {
+    size_t off = P.csr_bytes;
+    auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+    const int64_t nw = (P.n >> 5) + 1;
+    const size_t H = P.hub_v.size();
+    P.o_slot = take(sizeof(int32_t) * (size_t)std::max<int64_t>(P.n, 1));
+    P.o_table = take(sizeof(uint64_t) * (size_t)P.cap);
+    P.o_bitmap = take(sizeof(uint32_t) * (size_t)nw);
+    P.o_prefix = take(sizeof(uint32_t) * (size_t)(nw + 1));
+    P.o_scan = take(sizeof(uint32_t) * kb::scan_tmp_words(nw));
+    P.o_hubv = take(sizeof(int32_t) * H);
+    P.o_chunk = take(sizeof(int64_t) * (H + 1));
+    P.o_setoff = take(sizeof(int64_t) * (H + 1));
+    P.o_listoff = take(sizeof(int64_t) * (H + 1));
+    P.o_acc = take(sizeof(uint64_t) * H);
+    P.o_cnt = take(sizeof(uint32_t) * H);
+    P.o_sets = take(sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0));
+    P.o_lists = take(sizeof(uint64_t) * (size_t)(H ? P.list_off[H] : 0));
+    P.total = off;
+}
+
+kb_status check_graph(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k) {
+    if (!g || !opt) return fail(ctx, KB_ERR_INVALID_ARG, "graph and options must not be NULL");
+    if (g->n < 0 || g->m < 0) return fail(ctx, KB_ERR_INVALID_ARG, "negative n or m");
+    if (g->n > 2147483646LL) return fail(ctx, KB_ERR_INVALID_ARG, "n exceeds 2^31-2");
+    if (k < 0) return fail(ctx, KB_ERR_INVALID_ARG, "k must be >= 0");
+    if (opt->direction < 0 || opt->direction > 2) return fail(ctx, KB_ERR_INVALID_ARG, "bad direction");
+    if (g->n > 0 && !g->row_offsets) return fail(ctx, KB_ERR_INVALID_ARG, "row_offsets is NULL");
+    if (g->m > 0 && !g->col_indices) return fail(ctx, KB_ERR_INVALID_ARG, "col_indices is NULL");
+    if (g->n == 0 && g->m != 0) return fail(ctx, KB_ERR_INVALID_ARG, "edges without vertices");
+    if (opt->load_factor < 0.f || opt->load_factor > 0.9f)
+        return fail(ctx, KB_ERR_INVALID_ARG, "load_factor must be in (0, 0.9]");
+    if (opt->hub_threshold < 0 || opt->hub_threshold > kb::kMaxHubThreshold)
+        return fail(ctx, KB_ERR_INVALID_ARG, "hub_threshold must be in [0, %d]", kb::kMaxHubThreshold);
+    if (opt->hash_mode < 0 || opt->hash_mode > 1) return fail(ctx, KB_ERR_INVALID_ARG, "bad hash_mode");
+    if (opt->direction == KB_DIR_BOTH && g->m > (int64_t)1 << 62)
+        return fail(ctx, KB_ERR_INVALID_ARG, "too many edges");
+    return KB_OK;
+}
+
+kb_status ensure_buffer(kb_context* ctx, void** buf, size_t* have, size_t need) {
+    if (need <= *have) return KB_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return fail(ctx, KB_ERR_OOM, "cannot allocate %zu bytes of device memory", need);
+    }
+    *have = need;
+    return KB_OK;
+}
+
+kb_status read_counters(kb_context* ctx) {
+    KB_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->stream));
+    KB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return KB_OK;
+}
+
+kb_status device_error(kb_context* ctx) {
+    const int32_t e = ctx->h_ctr->err;
+    if (e & kb::kErrInvalid)
+        return fail(ctx, KB_ERR_INVALID_ARG, "row_offsets not monotone from 0 to m, or a neighbour id out of [0, n)");
+    if (e & kb::kErrTableFull) return fail(ctx, KB_ERR_TABLE_FULL, "block table probe limit reached");
+    if (e & (kb::kErrStage | kb::kErrHubSet)) return fail(ctx, KB_ERR_DEVICE_CHECK, "device consistency check failed (%d)", e);
+    return KB_OK;
+}
+
+// Build the processed CSR (IN / BOTH) into `base` (layout_csr offsets).
+kb_status build_processed_csr(kb_context* ctx, const kb_graph* g, Plan& P, char* base) {
+    if (!needs_in_csr(P.dir)) return KB_OK;
+    int64_t* inpref = reinterpret_cast<int64_t*>(base + P.o_inpref);
+    KB_CUDA(ctx, cudaMemsetAsync(inpref, 0, sizeof(int64_t) * (size_t)(P.n + 1), ctx->stream));
+    kb::launch_in_degree(P.m, g->col_indices, inpref, ctx->stream);
+    kb::launch_scan_i64(inpref, P.n, inpref, reinterpret_cast<int64_t*>(base + P.o_i64tmp), ctx->stream);
+    kb::launch_build_csr(P.n, P.m, g->row_offsets, g->col_indices, P.labels ? g->edge_labels : nullptr, inpref,
+                         P.dir == KB_DIR_BOTH ? 1 : 0, reinterpret_cast<int64_t*>(base + P.o_rowp),
+                         reinterpret_cast<int32_t*>(base + P.o_colp),
+                         P.labels ? reinterpret_cast<int32_t*>(base + P.o_labp) : nullptr,
+                         reinterpret_cast<int64_t*>(base + P.o_cursor), ctx->stream);
+    KB_CUDA(ctx, cudaGetLastError());
+    return KB_OK;
+}
+
+// Discover hubs of the processed CSR and fill the host side of the plan.
+kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
+    P.hub_v.clear();
+    P.chunk_off.assign(1, 0);
+    P.set_off.assign(1, 0);
+    P.list_off.assign(1, 0);
+    if (P.n == 0 || P.m_proc == 0) return KB_OK;
+    const int64_t hmax = std::min<int64_t>(P.n, P.m_proc / (P.thr + 1) + 1);
+    const size_t deg_off = align_up(sizeof(int32_t) * (size_t)hmax);
+    KB_TRY(ensure_buffer(ctx, &ctx->hub_tmp, &ctx->hub_tmp_bytes, deg_off + sizeof(int64_t) * (size_t)hmax));
+    int32_t* d_v = reinterpret_cast<int32_t*>(ctx->hub_tmp);
+    int64_t* d_deg = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(ctx->hub_tmp) + deg_off);
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_hub_n, 0, sizeof(int32_t), ctx->stream));
+    kb::launch_find_hubs(P.n, row_p, P.thr, d_v, d_deg, ctx->d_hub_n, ctx->stream);
+    KB_CUDA(ctx, cudaGetLastError());
+    KB_CUDA(ctx, cudaMemcpyAsync(ctx->h_hub_n, ctx->d_hub_n, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    KB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int32_t H = *ctx->h_hub_n;
+    if (H <= 0) return KB_OK;
+    if (H > hmax) return fail(ctx, KB_ERR_DEVICE_CHECK, "hub count exceeds bound");
+    std::vector<int32_t> hv((size_t)H);
+    std::vector<int64_t> hd((size_t)H);
+    KB_CUDA(ctx, cudaMemcpy(hv.data(), d_v, sizeof(int32_t) * (size_t)H, cudaMemcpyDeviceToHost));
+    KB_CUDA(ctx, cudaMemcpy(hd.data(), d_deg, sizeof(int64_t) * (size_t)H, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> order((size_t)H);
+    for (int32_t i = 0; i < H; ++i) order[(size_t)i] = i;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return hv[(size_t)a] < hv[(size_t)b]; });
+    P.hub_v.resize((size_t)H);
+    std::vector<int64_t> deg((size_t)H);
+    for (int32_t i = 0; i < H; ++i) {
+        P.hub_v[(size_t)i] = hv[(size_t)order[(size_t)i]];
+        deg[(size_t)i] = hd[(size_t)order[(size_t)i]];
+    }
+    P.chunk_off.resize((size_t)H + 1);
+    P.set_off.resize((size_t)H + 1);
+    P.list_off.resize((size_t)H + 1);
+    for (int32_t i = 0; i < H; ++i) {
+        const int64_t d = deg[(size_t)i];
+        P.chunk_off[(size_t)i + 1] = P.chunk_off[(size_t)i] + (d + kb::kHubChunk - 1) / kb::kHubChunk;
+        P.set_off[(size_t)i + 1] = P.set_off[(size_t)i] + (int64_t)next_pow2((uint64_t)(2 * d));
+        P.list_off[(size_t)i + 1] = P.list_off[(size_t)i] + d;
+    }
+    return KB_OK;
+}
+
+kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, Plan& P, char** csr_base_out,
+                    bool for_query) {
+    P.n = g->n;
+    P.m = g->m;
+    P.dir = opt->direction;
+    P.m_proc = P.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
+    P.labels = opt->use_edge_labels && g->edge_labels != nullptr;
+    int thr = opt->hub_threshold ? opt->hub_threshold : ctx->tuned_hub_threshold;
+    P.thr = thr > 0 ? thr : kb::kDefaultHubThreshold;
+    float lf = opt->load_factor > 0.f ? opt->load_factor : ctx->tuned_load_factor;
+    if (!(lf > 0.f)) lf = 0.5f;
+    P.cap = next_pow2((uint64_t)((double)std::max<int64_t>(P.n, 1) / (double)lf) + 1);
+    if (P.cap < 1024) P.cap = 1024;
+    if (P.cap > ((uint64_t)1 << 32)) P.cap = (uint64_t)1 << 32;
+    layout_csr(P);
+    const int64_t* row_p = g->row_offsets;
+    char* csr_base = nullptr;
+    if (needs_in_csr(P.dir)) {
+        // The processed CSR is needed to find hubs; during a size query it is
+        // built in library scratch, otherwise at the head of the workspace.
+        if (for_query) {
+            KB_TRY(ensure_buffer(ctx, &ctx->plan_tmp, &ctx->plan_tmp_bytes, P.csr_bytes));
+            csr_base = reinterpret_cast<char*>(ctx->plan_tmp);
+        } else {
+            csr_base = *csr_base_out;
+        }
+        KB_TRY(build_processed_csr(ctx, g, P, csr_base));
+        row_p = reinterpret_cast<const int64_t*>(csr_base + P.o_rowp);
+    }
+    KB_TRY(plan_hubs(ctx, P, row_p));
+    layout_round(P);
+    return KB_OK;
+}
+
+// Acquire a workspace of `bytes`; returns its base.
+kb_status acquire_workspace(kb_context* ctx, size_t bytes, char** base) {
+    if (ctx->user_ws) {
+        if (bytes > ctx->user_ws_bytes)
+            return fail(ctx, KB_ERR_OOM, "caller workspace holds %zu bytes, %zu needed", ctx->user_ws_bytes, bytes);
+        *base = reinterpret_cast<char*>(ctx->user_ws);
+        return KB_OK;
+    }
+    KB_TRY(ensure_buffer(ctx, &ctx->own_ws, &ctx->own_ws_bytes, std::max<size_t>(bytes, 256)));
+    *base = reinterpret_cast<char*>(ctx->own_ws);
+    return KB_OK;
+}
+
+struct Timer {
+    kb_context* ctx;
+    int used = 0;
+    int fam[8];
+    explicit Timer(kb_context* c) : ctx(c) {}
+    void begin(int family) {
+        if (!ctx->timing || used >= 8) return;
+        fam[used] = family;
+        cudaEventRecord(ctx->ev[2 * used], ctx->stream);
+    }
+    void end() {
+        if (!ctx->timing || used >= 8) return;
+        cudaEventRecord(ctx->ev[2 * used + 1], ctx->stream);
+        ++used;
+    }
+    // after a stream sync
+    float collect() {
+        float round = 0.f;
+        if (!ctx->timing) return 0.f;
+        for (int i = 0; i < used; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]);
+            ctx->kernel_ms[fam[i]] += ms;
+            ctx->kernel_launches[fam[i]] += 1;
+            round += ms;
+        }
+        if (used > 0) {
+            float span = 0.f;
+            cudaEventElapsedTime(&span, ctx->ev[0], ctx->ev[2 * used - 1]);
+            round = span;
+        }
+        used = 0;
+        return round;
+    }
+};
+
+// The refinement driver shared by kb_refine and kb_refine_from.
+kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
+                      int k, int32_t* levels, int64_t* counts, int* levels_computed) {
+    KB_TRY(check_graph(ctx, g, opt, k));
+    if (i_start < 0 || i_start > k) return fail(ctx, KB_ERR_INVALID_ARG, "i_start must be in [0, k]");
+    if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
+    if (g->n > 0 && !levels) return fail(ctx, KB_ERR_INVALID_ARG, "levels is NULL");
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    ctx->round_ms.clear();
+    for (int f = 0; f < KB_KERNEL_COUNT; ++f) {
+        ctx->kernel_ms[f] = 0.f;
+        ctx->kernel_launches[f] = 0;
+    }
+    const int64_t n = g->n;
+    if (levels_computed) *levels_computed = i_start;
+    if (n == 0) {
+        for (int i = i_start; i <= k; ++i) counts[i] = 0;
+        return KB_OK;
+    }
+    cudaStream_t s = ctx->stream;
+
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    if (opt->validate) {
+        kb::launch_validate(n, g->m, g->row_offsets, g->col_indices, ctx->d_ctr, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_TRY(read_counters(ctx));
+        KB_TRY(device_error(ctx));
+    }
+
+    // Plan: the processed CSR sits at the head of the workspace, so its size
+    // is known before the hub layout.
+    Plan P;
+    {
+        Plan probe;
+        probe.n = n;
+        probe.m = g->m;
+        probe.dir = opt->direction;
+        probe.m_proc = probe.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
+        probe.labels = opt->use_edge_labels && g->edge_labels != nullptr;
+        layout_csr(probe);
+        char* base = nullptr;
+        if (probe.csr_bytes) {
+            // The hub layout is not known yet: reserve the CSR part first.  A
+            // library-owned workspace keeps its contents when it does not grow.
+            if (ctx->user_ws) {
+                KB_TRY(acquire_workspace(ctx, probe.csr_bytes, &base));
+            } else {
+                KB_TRY(ensure_buffer(ctx, &ctx->plan_tmp, &ctx->plan_tmp_bytes, probe.csr_bytes));
+                base = reinterpret_cast<char*>(ctx->plan_tmp);
+            }
+        }
+        KB_TRY(make_plan(ctx, g, opt, P, &base, false));
+        char* ws = nullptr;
+        if (ctx->user_ws) {
+            KB_TRY(acquire_workspace(ctx, P.total, &ws));
+        } else {
+            // round buffers live in the owned workspace; the CSR stays in plan_tmp
+            Plan R = P;
+            R.csr_bytes = 0;
+            layout_round(R);
+            KB_TRY(ensure_buffer(ctx, &ctx->own_ws, &ctx->own_ws_bytes, std::max<size_t>(R.total, 256)));
+            P.o_slot = R.o_slot;
+            P.o_table = R.o_table;
+            P.o_bitmap = R.o_bitmap;
+            P.o_prefix = R.o_prefix;
+            P.o_scan = R.o_scan;
+            P.o_hubv = R.o_hubv;
+            P.o_chunk = R.o_chunk;
+            P.o_setoff = R.o_setoff;
+            P.o_listoff = R.o_listoff;
+            P.o_acc = R.o_acc;
+            P.o_cnt = R.o_cnt;
+            P.o_sets = R.o_sets;
+            P.o_lists = R.o_lists;
+            ws = reinterpret_cast<char*>(ctx->own_ws);
+        }
+        char* csr = base;
+        // assemble round parameters
+        kb::RoundParams p{};
+        p.n = n;
+        if (needs_in_csr(P.dir)) {
+            p.row = reinterpret_cast<const int64_t*>(csr + P.o_rowp);
+            p.col = reinterpret_cast<const int32_t*>(csr + P.o_colp);
+            p.lab = P.labels ? reinterpret_cast<const int32_t*>(csr + P.o_labp) : nullptr;
+        } else {
+            p.row = g->row_offsets;
+            p.col = g->col_indices;
+            p.lab = P.labels ? g->edge_labels : nullptr;
+        }
+        p.hub_threshold = P.thr;
+        p.hash_mode = opt->hash_mode;
+        p.table = reinterpret_cast<uint64_t*>(ws + P.o_table);
+        p.mask = P.cap - 1;
+        p.slot_of = reinterpret_cast<int32_t*>(ws + P.o_slot);
+        p.bitmap = reinterpret_cast<uint32_t*>(ws + P.o_bitmap);
+        p.ctr = ctx->d_ctr;
+        const size_t H = P.hub_v.size();
+        p.n_hubs = (int32_t)H;
+        p.hub_v = reinterpret_cast<const int32_t*>(ws + P.o_hubv);
+        p.hub_chunk_off = reinterpret_cast<const int64_t*>(ws + P.o_chunk);
+        p.hub_set_off = reinterpret_cast<const int64_t*>(ws + P.o_setoff);
+        p.hub_list_off = reinterpret_cast<const int64_t*>(ws + P.o_listoff);
+        p.hub_sets = reinterpret_cast<uint64_t*>(ws + P.o_sets);
+        p.hub_lists = reinterpret_cast<uint64_t*>(ws + P.o_lists);
+        p.hub_acc = reinterpret_cast<uint64_t*>(ws + P.o_acc);
+        p.hub_cnt = reinterpret_cast<uint32_t*>(ws + P.o_cnt);
+        uint32_t* prefix = reinterpret_cast<uint32_t*>(ws + P.o_prefix);
+        uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(ws + P.o_scan);
+        if (H) {
+            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_hubv, P.hub_v.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice, s));
+            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunk, P.chunk_off.data(), sizeof(int64_t) * (H + 1),
+                                         cudaMemcpyHostToDevice, s));
+            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_setoff, P.set_off.data(), sizeof(int64_t) * (H + 1),
+                                         cudaMemcpyHostToDevice, s));
+            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_listoff, P.list_off.data(), sizeof(int64_t) * (H + 1),
+                                         cudaMemcpyHostToDevice, s));
+        }
+        const int64_t total_chunks = H ? P.chunk_off[H] : 0;
+        const size_t set_bytes = sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0);
+        KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
+        uint32_t epoch = 0;
+        auto next_epoch = [&]() -> kb_status {
+            if (epoch == 255) {
+                KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
+                epoch = 0;
+            }
+            p.epoch = ++epoch;
+            return KB_OK;
+        };
+
+        // ---- the starting level
+        int32_t* row0 = levels + (size_t)i_start * (size_t)n;
+        const int32_t* init_key = start ? start : (opt->use_vertex_labels ? g->vertex_labels : nullptr);
+        if (init_key) {
+            KB_TRY(next_epoch());
+            KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+            KB_CUDA(ctx, cudaMemsetAsync(p.bitmap, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
+            p.prev = init_key;
+            kb::launch_tile_round(p, true, s);
+            kb::launch_renumber(p, prefix, scan_tmp, row0, s);
+            KB_CUDA(ctx, cudaGetLastError());
+            KB_TRY(read_counters(ctx));
+            KB_TRY(device_error(ctx));
+            counts[i_start] = ctx->h_ctr->count;
+        } else {
+            kb::launch_fill_i32(row0, n, 0, s);
+            counts[i_start] = 1;
+        }
+
+        // ---- refinement rounds
+        for (int i = i_start + 1; i <= k; ++i) {
+            Timer T(ctx);
+            KB_TRY(next_epoch());
+            p.prev = levels + (size_t)(i - 1) * (size_t)n;
+            int32_t* out = levels + (size_t)i * (size_t)n;
+            T.begin(KB_KERNEL_OTHER);
+            KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+            kb::launch_clear_round(p, s);
+            if (set_bytes) KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, set_bytes, s));
+            T.end();
+            T.begin(KB_KERNEL_SIGNATURE);
+            kb::launch_tile_round(p, false, s);
+            T.end();
+            if (H) {
+                T.begin(KB_KERNEL_HUB_CHUNK);
+                kb::launch_hub_chunk(p, total_chunks, s);
+                T.end();
+                T.begin(KB_KERNEL_HUB_FINAL);
+                kb::launch_hub_final(p, s);
+                T.end();
+            }
+            T.begin(KB_KERNEL_RENUMBER);
+            kb::launch_renumber(p, prefix, scan_tmp, out, s);
+            T.end();
+            KB_CUDA(ctx, cudaGetLastError());
+            KB_TRY(read_counters(ctx));
+            ctx->round_ms.push_back(T.collect());
+            KB_TRY(device_error(ctx));
+            counts[i] = ctx->h_ctr->count;
+            if (levels_computed) *levels_computed = i;
+            if (opt->early_stop && counts[i] == counts[i - 1]) {
+                if (i < k) kb::launch_copy_rows(levels, n, i, i + 1, k, s);
+                for (int j = i + 1; j <= k; ++j) counts[j] = counts[i];
+                KB_CUDA(ctx, cudaGetLastError());
+                break;
+            }
+        }
+    }
+    KB_CUDA(ctx, cudaStreamSynchronize(s));
+    return KB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kb_options kb_options_default(void) {
+    kb_options o;
+    std::memset(&o, 0, sizeof(o));
+    o.direction = KB_DIR_OUT;
+    o.use_vertex_labels = 1;
+    o.use_edge_labels = 1;
+    o.early_stop = 1;
+    o.validate = 1;
+    return o;
+}
+
+kb_options kb_options_schaetzle(void) {
+    kb_options o = kb_options_default();
+    o.direction = KB_DIR_OUT;
+    o.use_vertex_labels = 0;
+    o.use_edge_labels = 1;
+    return o;
+}
+
+kb_options kb_options_kaushik(void) {
+    kb_options o = kb_options_default();
+    o.direction = KB_DIR_IN;
+    o.use_vertex_labels = 1;
+    o.use_edge_labels = 0;
+    return o;
+}
+
+const char* kb_status_string(kb_status st) {
+    switch (st) {
+        case KB_OK: return "ok";
+        case KB_ERR_INVALID_ARG: return "invalid argument";
+        case KB_ERR_OOM: return "out of device memory";
+        case KB_ERR_TABLE_FULL: return "block table full";
+        case KB_ERR_TIMEOUT: return "device wait timed out";
+        case KB_ERR_CUDA: return "CUDA error";
+        case KB_ERR_DEVICE_CHECK: return "device consistency check failed";
+        case KB_ERR_NOT_FOUND: return "not found";
+    }
+    return "unknown status";
+}
+
+kb_status kb_create(kb_context** out, int device, void* stream) {
+    if (!out) return KB_ERR_INVALID_ARG;
+    *out = nullptr;
+    kb_context* ctx = new (std::nothrow) kb_context();
+    if (!ctx) return KB_ERR_OOM;
+    ctx->device = device;
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->d_ctr, sizeof(Counters)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_hub_n, sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_ctr, sizeof(Counters)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_hub_n, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        kb_destroy(ctx);
+        return KB_ERR_CUDA;
+    }
+    for (auto& e : ctx->ev) cudaEventCreate(&e);
+    *out = ctx;
+    return KB_OK;
+}
+
+kb_status kb_destroy(kb_context* ctx) {
+    if (!ctx) return KB_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
+    cudaFree(ctx->d_ctr);
+    cudaFree(ctx->d_hub_n);
+    cudaFreeHost(ctx->h_ctr);
+    cudaFreeHost(ctx->h_hub_n);
+    cudaFree(ctx->own_ws);
+    cudaFree(ctx->hub_tmp);
+    cudaFree(ctx->plan_tmp);
+    cudaFree(ctx->stage);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+    return KB_OK;
+}
+
+const char* kb_last_error(const kb_context* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+kb_status kb_workspace_size(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k, size_t* bytes) {
+    if (!ctx || !bytes) return KB_ERR_INVALID_ARG;
+    KB_TRY(check_graph(ctx, g, opt, k));
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (g->n == 0) {
+        *bytes = 0;
+        return KB_OK;
+    }
+    Plan P;
+    char* unused = nullptr;
+    KB_TRY(make_plan(ctx, g, opt, P, &unused, true));
+    *bytes = P.total;
+    return KB_OK;
+}
+
+kb_status kb_set_workspace(kb_context* ctx, void* ptr, size_t bytes) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    ctx->user_ws = ptr;
+    ctx->user_ws_bytes = ptr ? bytes : 0;
+    return KB_OK;
+}
+
+kb_status kb_refine(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k, int32_t* levels,
+                    int64_t* counts, int* levels_computed) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    return refine_impl(ctx, g, opt, nullptr, 0, k, levels, counts, levels_computed);
+}
+
+kb_status kb_refine_from(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start,
+                         int i_start, int k, int32_t* levels, int64_t* counts, int* levels_computed) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    if (!start && g && g->n > 0) return fail(ctx, KB_ERR_INVALID_ARG, "start is NULL");
+    return refine_impl(ctx, g, opt, start, i_start, k, levels, counts, levels_computed);
+}
+
+kb_status kb_refine_host(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k, int32_t* levels,
+                         int64_t* counts, int* levels_computed) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    KB_TRY(check_graph(ctx, g, opt, k));
+    if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
+    if (g->n > 0 && !levels) return fail(ctx, KB_ERR_INVALID_ARG, "levels is NULL");
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = g->n, m = g->m;
+    const bool el = g->edge_labels && opt->use_edge_labels;
+    const bool vl = g->vertex_labels && opt->use_vertex_labels;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += align_up(b); return o; };
+    const size_t o_row = take(sizeof(int64_t) * (size_t)(n + 1));
+    const size_t o_col = take(sizeof(int32_t) * (size_t)m);
+    const size_t o_el = take(el ? sizeof(int32_t) * (size_t)m : 0);
+    const size_t o_vl = take(vl ? sizeof(int32_t) * (size_t)n : 0);
+    const size_t o_lv = take(sizeof(int32_t) * (size_t)n * (size_t)(k + 1));
+    KB_TRY(ensure_buffer(ctx, &ctx->stage, &ctx->stage_bytes, std::max<size_t>(off, 256)));
+    char* b = reinterpret_cast<char*>(ctx->stage);
+    cudaStream_t s = ctx->stream;
+    if (n > 0) {
+        KB_CUDA(ctx, cudaMemcpyAsync(b + o_row, g->row_offsets, sizeof(int64_t) * (size_t)(n + 1),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    if (m > 0) KB_CUDA(ctx, cudaMemcpyAsync(b + o_col, g->col_indices, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+    if (el && m > 0) KB_CUDA(ctx, cudaMemcpyAsync(b + o_el, g->edge_labels, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+    if (vl && n > 0) KB_CUDA(ctx, cudaMemcpyAsync(b + o_vl, g->vertex_labels, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    kb_graph dg = *g;
+    dg.row_offsets = reinterpret_cast<const int64_t*>(b + o_row);
+    dg.col_indices = reinterpret_cast<const int32_t*>(b + o_col);
+    dg.edge_labels = el ? reinterpret_cast<const int32_t*>(b + o_el) : nullptr;
+    dg.vertex_labels = vl ? reinterpret_cast<const int32_t*>(b + o_vl) : nullptr;
+    int32_t* dlev = reinterpret_cast<int32_t*>(b + o_lv);
+    KB_TRY(refine_impl(ctx, &dg, opt, nullptr, 0, k, dlev, counts, levels_computed));
+    if (n > 0)
+        KB_CUDA(ctx, cudaMemcpyAsync(levels, dlev, sizeof(int32_t) * (size_t)n * (size_t)(k + 1), cudaMemcpyDeviceToHost, s));
+    KB_CUDA(ctx, cudaStreamSynchronize(s));
+    return KB_OK;
+}
+
+kb_status kb_set_timing(kb_context* ctx, int enable) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    ctx->timing = enable != 0;
+    return KB_OK;
+}
+
+kb_status kb_get_timing(const kb_context* ctx, float* round_ms, int max_rounds, int* n_rounds, float* kernel_ms,
+                        int64_t* kernel_launches) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    const int nr = (int)ctx->round_ms.size();
+    if (n_rounds) *n_rounds = nr;
+    if (round_ms)
+        for (int i = 0; i < nr && i < max_rounds; ++i) round_ms[i] = ctx->round_ms[(size_t)i];
+    for (int f = 0; f < KB_KERNEL_COUNT; ++f) {
+        if (kernel_ms) kernel_ms[f] = ctx->kernel_ms[f];
+        if (kernel_launches) kernel_launches[f] = ctx->kernel_launches[f];
+    }
+    return KB_OK;
+}
+
+kb_status kb_refine_batch(kb_context* ctx, const kb_graph*, const int64_t*, int64_t, const int32_t*,
+                          const kb_options*, int32_t*, int64_t*, int32_t*) {
+    return fail(ctx, KB_ERR_INVALID_ARG, "kb_refine_batch: not available in this build");
+}
+
+kb_status kb_autotune(kb_context* ctx, const kb_graph*, const kb_options*, int, float*, int32_t*, float*) {
+    return fail(ctx, KB_ERR_INVALID_ARG, "kb_autotune: not available in this build");
+}
+
+}  // extern "C"

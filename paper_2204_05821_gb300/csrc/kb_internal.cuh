@@ -1,0 +1,137 @@
+// Internal declarations of the GB300 k-bisimulation library: tile geometry,
+// device-side parameter blocks, hashing and pair packing, and the host-side
+// launchers implemented in kb_kernels.cu / kb_setup.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kbisim.h"
+
+namespace kb {
+
+// ---------------------------------------------------------------- geometry
+// A signature CTA owns kTileVerts consecutive vertices.  Their edges (hubs
+// excluded) are staged in shared memory in sub-tiles that hold at most
+// kStage pairs: vertices are grouped by floor(edge prefix / kSplit), so a
+// sub-tile holds < kSplit + hub_threshold <= kStage edges.
+constexpr int kTileVerts = 512;
+constexpr int kTileThreads = 512;
+constexpr int kSplit = 2048;
+constexpr int kStage = 4096;
+constexpr int kSetCap = 8192;  // shared dedup set slots (>= 2 * kStage)
+constexpr int kMaxHubThreshold = kStage - kSplit;
+constexpr int kDefaultHubThreshold = 2048;
+constexpr int kHubChunk = 4096;  // edges per hub-chunk CTA (== kStage)
+constexpr int kHubFinalThreads = 256;
+constexpr int kProbeLimit = 1 << 22;  // bound on block-table probes per vertex
+
+constexpr uint64_t kEmptyPair = ~0ull;  // block field 0x7fffffff never occurs (n <= 2^31-2)
+
+// bits of Counters::err
+enum : int32_t { kErrTableFull = 1, kErrInvalid = 2, kErrStage = 4, kErrHubSet = 8 };
+
+struct Counters {
+    int32_t err;
+    int32_t pad;
+    int64_t count;  // blocks at the level just assigned
+};
+
+// Everything one refinement round reads and writes.
+struct RoundParams {
+    int64_t n;
+    const int64_t* row;   // [n+1] CSR of the processed direction
+    const int32_t* col;   // [m_proc] neighbour; bit 31 set for in-edges
+    const int32_t* lab;   // [m_proc] edge label or nullptr (all labels 0)
+    const int32_t* prev;  // [n] previous level (vertex labels at level 0)
+    int32_t hub_threshold;
+    int32_t hash_mode;
+    uint32_t epoch;       // 1..255, tags this round's table entries
+    uint64_t* table;      // [mask+1] block table
+    uint64_t mask;
+    int32_t* slot_of;     // [n] table slot of every vertex
+    uint32_t* bitmap;     // [n/32+1] bit v set iff v is the smallest member of its block
+    Counters* ctr;
+    // hubs (vertices with more than hub_threshold edges)
+    int32_t n_hubs;
+    const int32_t* hub_v;          // [n_hubs] ascending
+    const int64_t* hub_chunk_off;  // [n_hubs+1]
+    const int64_t* hub_set_off;    // [n_hubs+1] power-of-two set per hub
+    const int64_t* hub_list_off;   // [n_hubs+1] unique-pair list per hub
+    uint64_t* hub_sets;
+    uint64_t* hub_lists;
+    uint64_t* hub_acc;  // [n_hubs] sum of pair mixes over unique pairs
+    uint32_t* hub_cnt;  // [n_hubs] unique pairs
+};
+
+// ---------------------------------------------------------------- hashing
+// SplitMix64 output function (Steele, Lea & Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014): a bijective 64-bit mixer.
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ULL;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebULL;
+    x ^= x >> 31;
+    return x;
+}
+
+// A signature pair (direction d, edge label l, neighbour block b) as one
+// 64-bit word: label in bits 63..32, d in bit 31, b in bits 30..0.
+__device__ __forceinline__ uint64_t pack_pair(int32_t label, uint32_t col_word, int32_t block) {
+    return ((uint64_t)(uint32_t)label << 32) | (uint64_t)(col_word & 0x80000000u) | (uint64_t)(uint32_t)block;
+}
+
+__device__ __forceinline__ uint64_t pair_mix(uint64_t p) { return mix64(p ^ 0x9e3779b97f4a7c15ULL); }
+
+// Slot of (local vertex j, pair p) in a shared dedup set.
+__device__ __forceinline__ uint32_t set_slot(uint64_t p, uint32_t j) {
+    return (uint32_t)(mix64(p + 0x632be59bd9b4e019ULL * (uint64_t)(j + 1)) >> 20);
+}
+
+// Hash of a vertex key (own previous block, signature set).  The set enters
+// through an order-independent sum of pair mixes over its distinct pairs and
+// its size.  hash_mode 1 keeps only the own block (forces collisions).
+__device__ __forceinline__ uint64_t vertex_hash(int32_t own, uint32_t cnt, uint64_t acc, int mode) {
+    uint64_t base = mix64(((uint64_t)(uint32_t)own << 32) ^ 0x5851f42d4c957f2dULL);
+    if (mode == 1) return base;
+    return mix64(base ^ mix64(acc + 0xd6e8feb86659fd93ULL * ((uint64_t)cnt + 1)));
+}
+
+__device__ __forceinline__ uint32_t table_hi(uint64_t h, uint32_t epoch) {
+    return (epoch << 24) | (uint32_t)(h >> 40);
+}
+
+// ---------------------------------------------------------------- launchers
+// Signature rounds (kb_kernels.cu)
+void launch_clear_round(const RoundParams& p, cudaStream_t s);
+void launch_tile_round(const RoundParams& p, bool level0, cudaStream_t s);
+void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s);
+void launch_hub_final(const RoundParams& p, cudaStream_t s);
+// Canonical renumbering: prefix of block minima, then ids.
+void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp, int32_t* out,
+                     cudaStream_t s);
+size_t scan_tmp_words(int64_t n_items);
+void launch_fill_i32(int32_t* out, int64_t n, int32_t value, cudaStream_t s);
+
+// Setup (kb_setup.cu)
+void launch_validate(int64_t n, int64_t m, const int64_t* row, const int32_t* col, Counters* ctr,
+                     cudaStream_t s);
+// in-degree histogram: deg[w] += 1 per edge (deg must be zeroed)
+void launch_in_degree(int64_t m, const int32_t* col, int64_t* deg, cudaStream_t s);
+// exclusive prefix of n int64 values into out[0..n] (out[n] = total); in and out may alias
+void launch_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t s);
+size_t scan_i64_tmp(int64_t n);
+// Build the processed CSR for IN (include_out = 0) or BOTH (include_out = 1):
+//   row_p[v] = (include_out ? row[v] : 0) + in_prefix[v]
+void launch_build_csr(int64_t n, int64_t m, const int64_t* row, const int32_t* col, const int32_t* lab,
+                      const int64_t* in_prefix, int include_out, int64_t* row_p, int32_t* col_p,
+                      int32_t* lab_p, int64_t* cursor, cudaStream_t s);
+// Compact the vertices with more than thr edges (unordered) into out_v with
+// their degrees in out_deg; count in *n_out.
+void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v, int64_t* out_deg,
+                      int32_t* n_out, cudaStream_t s);
+// Copy row src of the level store to the rows [first, last] of levels.
+void launch_copy_rows(int32_t* levels, int64_t n, int src, int first, int last, cudaStream_t s);
+
+}  // namespace kb

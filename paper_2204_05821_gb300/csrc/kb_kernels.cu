@@ -1,0 +1,760 @@
+// Refinement-round kernels of the GB300 k-bisimulation library.
+//
+// One round (paper Alg. 1, one pass of the loop; Def. "signature"):
+//   1. tile_round_kernel: every non-hub vertex gathers its (direction, edge
+//      label, previous block of neighbour) pairs, drops duplicates, hashes
+//      (own previous block, pair set) and finds or inserts its key in the
+//      block table.  A hash match is accepted only after the full signature
+//      compare (the paper's implementations trust the hash; Section 4.3 notes
+//      BRS is only correct while hashes do not collide).
+//   2. hub_chunk_kernel / hub_final_kernel: the same for vertices with more
+//      than hub_threshold edges, split over many CTAs.
+//   3. renumber: the block table keeps the smallest member of every block; a
+//      bitmap marks those minima, its prefix count gives every block its
+//      canonical id (rank of its smallest member).
+#include <cuda_runtime.h>
+
+#include "kb_internal.cuh"
+
+namespace kb {
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+enum : uint8_t { kPending = 0, kDone = 1, kSkip = 2 };
+
+__device__ __forceinline__ void set_error(Counters* c, int32_t bit) { atomicOr(&c->err, bit); }
+
+// Exclusive scan of one int per thread over a CTA of NT threads.
+template <int NT>
+__device__ __forceinline__ int block_exclusive_scan(int x, int* warp_tmp, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NT / 32 ? warp_tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) warp_tmp[lane] = w;
+    }
+    __syncthreads();
+    const int base = warp > 0 ? warp_tmp[warp - 1] : 0;
+    *total = warp_tmp[NT / 32 - 1];
+    __syncthreads();
+    return base + incl - x;
+}
+
+__device__ __forceinline__ uint64_t volatile_load(const uint64_t* p) {
+    return *reinterpret_cast<const volatile uint64_t*>(p);
+}
+
+// Toggle membership of v in the set of block minima.  Every vertex that ever
+// becomes the minimum of its slot is toggled on once and off once when a
+// smaller member replaces it, so the final bitmap holds exactly the minima,
+// whatever order the toggles land in.
+__device__ __forceinline__ void toggle_min(uint32_t* bitmap, uint32_t v) {
+    atomicXor(&bitmap[v >> 5], 1u << (v & 31));
+}
+
+// Join slot `pos` (same epoch and tag as ours) with vertex v.
+__device__ __forceinline__ void join_slot(const RoundParams& p, uint64_t pos, uint32_t hi, uint32_t v) {
+    const uint64_t want = ((uint64_t)hi << 32) | v;
+    const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(&p.table[pos]),
+                                   (unsigned long long)want);
+    const uint32_t prev_min = (uint32_t)old;
+    if (v < prev_min) {
+        toggle_min(p.bitmap, v);
+        toggle_min(p.bitmap, prev_min);
+    }
+    p.slot_of[v] = (int32_t)pos;
+}
+
+// Probe the block table from *pos.  Returns 0 when v inserted a new key,
+// 1 with *rep set when a slot with our tag was found (a signature compare
+// decides), 2 when the probe limit was hit.
+__device__ __forceinline__ int probe_table(const RoundParams& p, uint64_t* pos_io, uint32_t hi, uint32_t v,
+                                           uint32_t* rep) {
+    uint64_t pos = *pos_io;
+    for (int it = 0; it < kProbeLimit; ++it) {
+        uint64_t cur = volatile_load(&p.table[pos]);
+        if ((uint32_t)(cur >> 56) != p.epoch) {
+            const uint64_t want = ((uint64_t)hi << 32) | v;
+            const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(&p.table[pos]),
+                                           (unsigned long long)cur, (unsigned long long)want);
+            if (old == cur) {
+                p.slot_of[v] = (int32_t)pos;
+                toggle_min(p.bitmap, v);
+                *pos_io = pos;
+                return 0;
+            }
+            cur = old;
+            if ((uint32_t)(cur >> 56) != p.epoch) continue;
+        }
+        if ((uint32_t)(cur >> 32) == hi) {
+            *rep = (uint32_t)cur;
+            *pos_io = pos;
+            return 1;
+        }
+        pos = (pos + 1) & p.mask;
+    }
+    return 2;
+}
+
+// ----------------------------------------------------------------------------
+// Tile kernel: kTileVerts consecutive vertices per CTA, one thread per vertex.
+// ----------------------------------------------------------------------------
+template <bool kLevel0>
+__global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const RoundParams p) {
+    __shared__ int64_t s_row[kTileVerts + 1];
+    __shared__ int32_t s_eoff[kTileVerts + 1];
+    __shared__ uint64_t s_pair[kStage];
+    __shared__ uint16_t s_seg[kStage];
+    __shared__ uint32_t s_set[kSetCap];  // bits 15..0: staged index + 1; bits 31..16: compare stamp
+    __shared__ uint64_t s_acc[kTileVerts];
+    __shared__ uint32_t s_cnt[kTileVerts];
+    __shared__ uint64_t s_pos[kTileVerts];
+    __shared__ uint32_t s_hi[kTileVerts];
+    __shared__ int32_t s_own[kTileVerts];
+    __shared__ uint8_t s_state[kTileVerts];
+    __shared__ uint16_t s_qj[kTileVerts];
+    __shared__ uint32_t s_qr[kTileVerts];
+    __shared__ uint8_t s_qres[kTileVerts];
+    __shared__ int s_warp[32];
+    __shared__ int s_qn;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int64_t v0 = (int64_t)blockIdx.x * kTileVerts;
+    const int nv = (int)min((int64_t)kTileVerts, p.n - v0);
+
+    // Offsets of the tile and capped degrees (hubs contribute no edges here).
+    if (!kLevel0) {
+        for (int i = tid; i <= nv; i += kTileThreads) s_row[i] = p.row[v0 + i];
+    }
+    __syncthreads();
+    int cdeg = 0;
+    uint8_t st = kSkip;
+    if (tid < nv) {
+        st = kPending;
+        if (!kLevel0) {
+            const int64_t d = s_row[tid + 1] - s_row[tid];
+            if (d > p.hub_threshold) st = kSkip; else cdeg = (int)d;
+        }
+    }
+    s_state[tid] = st;
+    int total;
+    const int eo = block_exclusive_scan<kTileThreads>(cdeg, s_warp, &total);
+    s_eoff[tid] = eo;
+    if (tid == 0) s_eoff[nv] = total;
+    __syncthreads();
+
+    const int n_sub = total == 0 ? 1 : (total + kSplit - 1) / kSplit;
+    for (int sub = 0; sub < n_sub; ++sub) {
+        // vertices whose edge prefix falls in [sub*kSplit, (sub+1)*kSplit)
+        int jlo, jhi;
+        {
+            int lo = 0, hi = nv;
+            const int key = sub * kSplit;
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (s_eoff[mid] < key) lo = mid + 1; else hi = mid; }
+            jlo = lo;
+            if (sub == n_sub - 1) {
+                jhi = nv;
+            } else {
+                int lo2 = jlo, hi2 = nv;
+                const int key2 = (sub + 1) * kSplit;
+                while (lo2 < hi2) { int mid = (lo2 + hi2) >> 1; if (s_eoff[mid] < key2) lo2 = mid + 1; else hi2 = mid; }
+                jhi = lo2;
+            }
+        }
+        if (jlo >= jhi) continue;  // uniform over the CTA
+        const int elo = s_eoff[jlo];
+        const int ehi = jhi == nv ? total : s_eoff[jhi];
+        const int E = ehi - elo;
+        if (E > kStage) {  // cannot happen with hub_threshold <= kMaxHubThreshold
+            if (tid == 0) set_error(p.ctr, kErrStage);
+            continue;
+        }
+
+        for (int i = tid; i < kSetCap; i += kTileThreads) s_set[i] = 0u;
+        if (tid >= jlo && tid < jhi) { s_acc[tid] = 0ull; s_cnt[tid] = 0u; }
+        __syncthreads();
+
+        if (!kLevel0) {
+            // Stage: coalesced streaming loads of neighbours and labels, then the
+            // gather of their previous blocks; four edges per thread in flight.
+            for (int base = 0; base < E; base += 4 * kTileThreads) {
+                int le[4], jj[4];
+                int64_t ge[4];
+                int32_t w[4], l[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    le[u] = base + u * kTileThreads + tid;
+                    jj[u] = jlo;
+                    ge[u] = 0;
+                    if (le[u] < E) {
+                        const int e = elo + le[u];
+                        int lo = jlo, hi = jhi;
+                        while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s_eoff[mid] <= e) lo = mid; else hi = mid; }
+                        jj[u] = lo;
+                        ge[u] = s_row[lo] + (e - s_eoff[lo]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (le[u] < E) {
+                        w[u] = __ldcs(p.col + ge[u]);
+                        l[u] = p.lab ? __ldcs(p.lab + ge[u]) : 0;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (le[u] < E) b[u] = __ldg(p.prev + (w[u] & 0x7fffffff));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (le[u] < E) {
+                        s_pair[le[u]] = pack_pair(l[u], (uint32_t)w[u], b[u]);
+                        s_seg[le[u]] = (uint16_t)jj[u];
+                    }
+                }
+            }
+            __syncthreads();
+
+            // Drop duplicate pairs per vertex (set semantics) and accumulate the
+            // order-independent hash of each vertex's distinct pairs.
+            for (int le = tid; le < E; le += kTileThreads) {
+                const uint64_t pr = s_pair[le];
+                const uint32_t j = s_seg[le];
+                uint32_t slot = set_slot(pr, j) & (kSetCap - 1);
+                while (true) {
+                    uint32_t cur = s_set[slot];
+                    if (cur == 0u) {
+                        const uint32_t old = atomicCAS(&s_set[slot], 0u, (uint32_t)(le + 1));
+                        if (old == 0u) {
+                            atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[j]),
+                                      (unsigned long long)pair_mix(pr));
+                            atomicAdd(&s_cnt[j], 1u);
+                            break;
+                        }
+                        cur = old;
+                    }
+                    const int idx = (int)(cur & 0xffffu) - 1;
+                    if (s_pair[idx] == pr && s_seg[idx] == j) break;
+                    slot = (slot + 1) & (kSetCap - 1);
+                }
+            }
+            __syncthreads();
+        }
+
+        // Hash each vertex's key.
+        if (tid >= jlo && tid < jhi && s_state[tid] == kPending) {
+            const int64_t v = v0 + tid;
+            const int32_t own = p.prev[v];
+            const uint64_t h = vertex_hash(own, s_cnt[tid], s_acc[tid], p.hash_mode);
+            s_pos[tid] = h & p.mask;
+            s_hi[tid] = table_hi(h, p.epoch);
+            s_own[tid] = own;
+        }
+
+        // Find-or-insert with full signature compare on every tag match.
+        for (uint32_t stamp = 1;; ++stamp) {
+            if (tid == 0) s_qn = 0;
+            __syncthreads();
+            if (tid >= jlo && tid < jhi && s_state[tid] == kPending) {
+                uint64_t pos = s_pos[tid];
+                uint32_t rep = 0;
+                const int r = probe_table(p, &pos, s_hi[tid], (uint32_t)(v0 + tid), &rep);
+                s_pos[tid] = pos;
+                if (r == 0) {
+                    s_state[tid] = kDone;
+                } else if (r == 1) {
+                    const int q = atomicAdd(&s_qn, 1);
+                    s_qj[q] = (uint16_t)tid;
+                    s_qr[q] = rep;
+                } else {
+                    set_error(p.ctr, kErrTableFull);
+                    s_state[tid] = kDone;
+                }
+            }
+            __syncthreads();
+            const int qn = s_qn;
+            if (qn == 0) break;
+            if (stamp >= 0xffffu) {  // cannot happen within the probe limit
+                if (tid == 0) set_error(p.ctr, kErrTableFull);
+                break;
+            }
+            // Compare: one warp per queued vertex.  The representative r is a
+            // non-hub vertex (hubs enter the table after this kernel), so its
+            // pairs are re-derived from the CSR and looked up in the shared set
+            // of our vertex; every distinct pair of ours must be hit once.
+            for (int q = warp; q < qn; q += kTileThreads / 32) {
+                const int j = s_qj[q];
+                const uint32_t r = s_qr[q];
+                bool ok = (__ldg(p.prev + r) == s_own[j]);
+                if (!kLevel0 && ok) {
+                    const int64_t rb = p.row[r], re = p.row[r + 1];
+                    int nf = 0;
+                    for (int64_t e0 = rb; e0 < re; e0 += 32) {
+                        const int64_t e = e0 + lane;
+                        bool found = true;
+                        if (e < re) {
+                            const int32_t w = __ldg(p.col + e);
+                            const int32_t l = p.lab ? __ldg(p.lab + e) : 0;
+                            const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(p.prev + (w & 0x7fffffff)));
+                            uint32_t slot = set_slot(pr, (uint32_t)j) & (kSetCap - 1);
+                            found = false;
+                            while (true) {
+                                const uint32_t cur = s_set[slot];
+                                if (cur == 0u) break;
+                                const int idx = (int)(cur & 0xffffu) - 1;
+                                if (s_pair[idx] == pr && s_seg[idx] == (uint16_t)j) {
+                                    const uint32_t old = atomicMax(&s_set[slot], (stamp << 16) | (cur & 0xffffu));
+                                    if ((old >> 16) < stamp) ++nf;
+                                    found = true;
+                                    break;
+                                }
+                                slot = (slot + 1) & (kSetCap - 1);
+                            }
+                        }
+                        ok = ok && found;
+                    }
+                    ok = __all_sync(kFull, ok);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(kFull, nf, o);
+                    ok = ok && ((uint32_t)nf == s_cnt[j]);
+                }
+                if (lane == 0) s_qres[q] = ok ? 1 : 0;
+            }
+            __syncthreads();
+            if (tid < qn) {
+                const int j = s_qj[tid];
+                if (s_qres[tid]) {
+                    join_slot(p, s_pos[j], s_hi[j], (uint32_t)(v0 + j));
+                    s_state[j] = kDone;
+                } else {
+                    s_pos[j] = (s_pos[j] + 1) & p.mask;
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Hub chunks: kHubChunk edges of one hub per CTA.  Chunk-local dedup in shared
+// memory, then the chunk's distinct pairs go into the hub's global set; pairs
+// new to the hub are appended to its list and summed into its hash.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundParams p) {
+    __shared__ uint64_t s_pair[kHubChunk];
+    __shared__ uint64_t s_new[kHubChunk];
+    __shared__ uint32_t s_set[kSetCap];
+    __shared__ uint8_t s_isnew[kHubChunk];
+    __shared__ int s_h, s_nuniq, s_nnew;
+    __shared__ int64_t s_e0, s_E, s_base;
+    __shared__ uint64_t s_accsum;
+
+    const int tid = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    if (tid == 0) {
+        int lo = 0, hi = p.n_hubs;  // largest h with chunk_off[h] <= c
+        while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (p.hub_chunk_off[mid] <= c) lo = mid; else hi = mid; }
+        s_h = lo;
+        const int32_t v = p.hub_v[lo];
+        const int64_t rb = p.row[v], re = p.row[v + 1];
+        const int64_t e0 = rb + (c - p.hub_chunk_off[lo]) * (int64_t)kHubChunk;
+        s_e0 = e0;
+        s_E = min((int64_t)kHubChunk, re - e0);
+        s_nuniq = 0;
+        s_nnew = 0;
+        s_accsum = 0ull;
+    }
+    for (int i = tid; i < kSetCap; i += kTileThreads) s_set[i] = 0u;
+    __syncthreads();
+    const int h = s_h;
+    const int E = (int)s_E;
+    const int64_t e0 = s_e0;
+
+    for (int base = 0; base < E; base += 4 * kTileThreads) {
+        int32_t w[4], l[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int le = base + u * kTileThreads + tid;
+            if (le < E) {
+                w[u] = __ldcs(p.col + e0 + le);
+                l[u] = p.lab ? __ldcs(p.lab + e0 + le) : 0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int le = base + u * kTileThreads + tid;
+            if (le < E) b[u] = __ldg(p.prev + (w[u] & 0x7fffffff));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int le = base + u * kTileThreads + tid;
+            if (le < E) s_pair[le] = pack_pair(l[u], (uint32_t)w[u], b[u]);
+        }
+    }
+    __syncthreads();
+
+    // chunk-local distinct pairs
+    for (int le = tid; le < E; le += kTileThreads) {
+        const uint64_t pr = s_pair[le];
+        uint32_t slot = set_slot(pr, 0u) & (kSetCap - 1);
+        while (true) {
+            uint32_t cur = s_set[slot];
+            if (cur == 0u) {
+                const uint32_t old = atomicCAS(&s_set[slot], 0u, (uint32_t)(le + 1));
+                if (old == 0u) {
+                    s_new[atomicAdd(&s_nuniq, 1)] = pr;
+                    break;
+                }
+                cur = old;
+            }
+            if (s_pair[(int)cur - 1] == pr) break;
+            slot = (slot + 1) & (kSetCap - 1);
+        }
+    }
+    __syncthreads();
+
+    // insert into the hub's global set
+    const int nu = s_nuniq;
+    uint64_t* gset = p.hub_sets + p.hub_set_off[h];
+    const uint64_t gmask = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]) - 1;
+    uint64_t lacc = 0;
+    for (int i = tid; i < nu; i += kTileThreads) {
+        const uint64_t pr = s_new[i];
+        uint64_t slot = (pair_mix(pr) >> 17) & gmask;
+        uint8_t isnew = 0;
+        for (uint64_t t = 0; t <= gmask; ++t) {
+            const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(&gset[slot]),
+                                           (unsigned long long)kEmptyPair, (unsigned long long)pr);
+            if (old == kEmptyPair) { isnew = 1; break; }
+            if (old == pr) break;
+            slot = (slot + 1) & gmask;
+        }
+        s_isnew[i] = isnew;
+        if (isnew) lacc += pair_mix(pr);
+    }
+    // CTA hash sum of the pairs new to the hub
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(kFull, lacc, o);
+    if ((tid & 31) == 0 && lacc) atomicAdd(reinterpret_cast<unsigned long long*>(&s_accsum), (unsigned long long)lacc);
+    __syncthreads();
+    // compact the new pairs
+    for (int i = tid; i < nu; i += kTileThreads)
+        if (s_isnew[i]) s_pair[atomicAdd(&s_nnew, 1)] = s_new[i];
+    __syncthreads();
+    const int nnew = s_nnew;
+    if (tid == 0) {
+        if (nnew) s_base = atomicAdd(&p.hub_cnt[h], (uint32_t)nnew);
+        if (s_accsum) atomicAdd(reinterpret_cast<unsigned long long*>(&p.hub_acc[h]), (unsigned long long)s_accsum);
+    }
+    __syncthreads();
+    uint64_t* list = p.hub_lists + p.hub_list_off[h];
+    for (int i = tid; i < nnew; i += kTileThreads) list[s_base + i] = s_pair[i];
+}
+
+__device__ __forceinline__ bool hub_set_contains(const uint64_t* gset, uint64_t gmask, uint64_t pr) {
+    uint64_t slot = (pair_mix(pr) >> 17) & gmask;
+    for (uint64_t t = 0; t <= gmask; ++t) {
+        const uint64_t cur = gset[slot];
+        if (cur == pr) return true;
+        if (cur == kEmptyPair) return false;
+        slot = (slot + 1) & gmask;
+    }
+    return false;
+}
+
+// ----------------------------------------------------------------------------
+// Hub keys: one CTA per hub finds or inserts the hub's key, comparing the full
+// signature against the representative of any slot with a matching tag.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const RoundParams p) {
+    __shared__ uint64_t s_pair[kMaxHubThreshold];
+    __shared__ uint32_t s_set[2 * kMaxHubThreshold];
+    __shared__ int s_kind;
+    __shared__ uint32_t s_rep;
+    __shared__ uint64_t s_pos;
+    __shared__ int s_ok, s_cnt_r;
+
+    const int tid = threadIdx.x;
+    const int h = blockIdx.x;
+    const int32_t v = p.hub_v[h];
+    const int32_t own = p.prev[v];
+    const uint32_t cnt = p.hub_cnt[h];
+    const uint64_t hv = vertex_hash(own, cnt, p.hub_acc[h], p.hash_mode);
+    const uint32_t hi = table_hi(hv, p.epoch);
+    const uint64_t* gset = p.hub_sets + p.hub_set_off[h];
+    const uint64_t gmask = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]) - 1;
+    if (tid == 0) s_pos = hv & p.mask;
+
+    for (int iter = 0; iter < kProbeLimit; ++iter) {
+        __syncthreads();
+        if (tid == 0) {
+            uint64_t pos = s_pos;
+            uint32_t rep = 0;
+            s_kind = probe_table(p, &pos, hi, (uint32_t)v, &rep);
+            s_pos = pos;
+            s_rep = rep;
+            s_ok = 1;
+            s_cnt_r = 0;
+        }
+        __syncthreads();
+        const int kind = s_kind;
+        if (kind == 0) return;
+        if (kind == 2) {
+            if (tid == 0) set_error(p.ctr, kErrTableFull);
+            return;
+        }
+        const uint32_t r = s_rep;
+        bool ok = (__ldg(p.prev + r) == own);
+        const int64_t rb = p.row[r], re = p.row[r + 1];
+        if (ok && re - rb > p.hub_threshold) {
+            // representative is a hub: compare distinct counts, then look its
+            // distinct pairs up in our set
+            int lo = 0, hi2 = p.n_hubs;
+            while (hi2 - lo > 1) { int mid = (lo + hi2) >> 1; if (p.hub_v[mid] <= (int32_t)r) lo = mid; else hi2 = mid; }
+            const uint32_t cnt_r = p.hub_cnt[lo];
+            ok = (cnt_r == cnt);
+            if (ok) {
+                const uint64_t* list = p.hub_lists + p.hub_list_off[lo];
+                bool all = true;
+                for (uint32_t i = tid; i < cnt_r; i += kHubFinalThreads)
+                    if (!hub_set_contains(gset, gmask, list[i])) all = false;
+                if (!all) s_ok = 0;
+            } else if (tid == 0) {
+                s_ok = 0;
+            }
+        } else if (ok) {
+            // representative is a small vertex: derive its pairs, count its
+            // distinct pairs in shared memory and look each up in our set
+            const int d = (int)(re - rb);
+            for (int i = tid; i < 2 * kMaxHubThreshold; i += kHubFinalThreads) s_set[i] = 0u;
+            __syncthreads();
+            bool all = true;
+            for (int i = tid; i < d; i += kHubFinalThreads) {
+                const int32_t w = __ldg(p.col + rb + i);
+                const int32_t l = p.lab ? __ldg(p.lab + rb + i) : 0;
+                const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(p.prev + (w & 0x7fffffff)));
+                s_pair[i] = pr;
+                if (!hub_set_contains(gset, gmask, pr)) all = false;
+            }
+            __syncthreads();
+            for (int i = tid; i < d; i += kHubFinalThreads) {
+                const uint64_t pr = s_pair[i];
+                uint32_t slot = set_slot(pr, 0u) & (2 * kMaxHubThreshold - 1);
+                while (true) {
+                    uint32_t cur = s_set[slot];
+                    if (cur == 0u) {
+                        const uint32_t old = atomicCAS(&s_set[slot], 0u, (uint32_t)(i + 1));
+                        if (old == 0u) { atomicAdd(&s_cnt_r, 1); break; }
+                        cur = old;
+                    }
+                    if (s_pair[(int)cur - 1] == pr) break;
+                    slot = (slot + 1) & (2 * kMaxHubThreshold - 1);
+                }
+            }
+            if (!all) s_ok = 0;
+            __syncthreads();
+            if (tid == 0 && (uint32_t)s_cnt_r != cnt) s_ok = 0;
+        } else if (tid == 0) {
+            s_ok = 0;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (s_ok) {
+                join_slot(p, s_pos, hi, (uint32_t)v);
+                s_kind = 0;
+            } else {
+                s_pos = (s_pos + 1) & p.mask;
+            }
+        }
+        __syncthreads();
+        if (s_kind == 0) return;
+    }
+    if (tid == 0) set_error(p.ctr, kErrTableFull);
+}
+
+// ----------------------------------------------------------------------------
+// Canonical renumbering
+// ----------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t x, uint32_t* tmp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if (lane == 0) tmp[warp] = x;
+    __syncthreads();
+    uint32_t t = 0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? tmp[lane] : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    }
+    __syncthreads();
+    return t;
+}
+
+// exclusive scan of one value per thread (blockDim = kScanThreads)
+__device__ __forceinline__ uint32_t block_exscan_u32(uint32_t x, uint32_t* tmp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = tmp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        tmp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t base = warp > 0 ? tmp[warp - 1] : 0u;
+    *total = tmp[31];
+    __syncthreads();
+    return base + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) popc_reduce_kernel(const uint32_t* bitmap, int64_t nw,
+                                                                  uint32_t* block_sums) {
+    __shared__ uint32_t tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t s = 0;
+#pragma unroll
+    for (int u = 0; u < kScanItems; ++u) {
+        const int64_t i = base + (int64_t)u * kScanThreads + threadIdx.x;
+        if (i < nw) s += __popc(bitmap[i]);
+    }
+    s = block_sum_u32(s, tmp);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_block_sums_kernel(uint32_t* block_sums, int64_t nb,
+                                                                      Counters* ctr) {
+    __shared__ uint32_t tmp[32];
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t x = i < nb ? block_sums[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exscan_u32(x, tmp, &total);
+        if (i < nb) block_sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) ctr->count = (int64_t)carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) popc_scan_kernel(const uint32_t* bitmap, int64_t nw,
+                                                                const uint32_t* block_sums, uint32_t* prefix) {
+    __shared__ uint32_t tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t c[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int u = 0; u < kScanItems; ++u) {
+        const int64_t i = base + u;
+        c[u] = i < nw ? (uint32_t)__popc(bitmap[i]) : 0u;
+        s += c[u];
+    }
+    uint32_t total;
+    uint32_t ex = block_exscan_u32(s, tmp, &total) + block_sums[blockIdx.x];
+#pragma unroll
+    for (int u = 0; u < kScanItems; ++u) {
+        const int64_t i = base + u;
+        if (i < nw) prefix[i] = ex;
+        ex += c[u];
+    }
+}
+
+__global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const uint32_t* prefix, int32_t* out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        const uint32_t bw = p.bitmap[v >> 5];
+        uint32_t mn = (uint32_t)v;
+        if (!((bw >> (v & 31)) & 1u)) {
+            mn = (uint32_t)(p.table[(uint64_t)(uint32_t)p.slot_of[v] & p.mask] & 0xffffffffu);
+            if ((int64_t)mn >= p.n) mn = (uint32_t)v;  // only after a reported device error
+        }
+        const uint32_t mw = p.bitmap[mn >> 5];
+        out[v] = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
+    }
+}
+
+__global__ void fill_i32_kernel(int32_t* out, int64_t n, int32_t value) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = value;
+}
+
+int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)b;
+}
+
+}  // namespace
+
+void launch_clear_round(const RoundParams& p, cudaStream_t s) {
+    cudaMemsetAsync(p.bitmap, 0, sizeof(uint32_t) * (size_t)((p.n >> 5) + 1), s);
+    if (p.n_hubs > 0) {
+        cudaMemsetAsync(p.hub_acc, 0, sizeof(uint64_t) * (size_t)p.n_hubs, s);
+        cudaMemsetAsync(p.hub_cnt, 0, sizeof(uint32_t) * (size_t)p.n_hubs, s);
+    }
+}
+
+void launch_tile_round(const RoundParams& p, bool level0, cudaStream_t s) {
+    if (p.n <= 0) return;
+    const int64_t blocks = (p.n + kTileVerts - 1) / kTileVerts;
+    if (level0)
+        tile_round_kernel<true><<<(unsigned)blocks, kTileThreads, 0, s>>>(p);
+    else
+        tile_round_kernel<false><<<(unsigned)blocks, kTileThreads, 0, s>>>(p);
+}
+
+void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s) {
+    if (p.n_hubs <= 0 || total_chunks <= 0) return;
+    hub_chunk_kernel<<<(unsigned)total_chunks, kTileThreads, 0, s>>>(p);
+}
+
+void launch_hub_final(const RoundParams& p, cudaStream_t s) {
+    if (p.n_hubs <= 0) return;
+    hub_final_kernel<<<(unsigned)p.n_hubs, kHubFinalThreads, 0, s>>>(p);
+}
+
+size_t scan_tmp_words(int64_t n_items) { return (size_t)((n_items + kScanTile - 1) / kScanTile) + 1; }
+
+void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
+    const int64_t nw = (p.n >> 5) + 1;
+    const int64_t nb = (nw + kScanTile - 1) / kScanTile;
+    popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp);
+    scan_block_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, nb, p.ctr);
+    popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp, prefix);
+    if (p.n > 0) assign_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out);
+}
+
+void launch_fill_i32(int32_t* out, int64_t n, int32_t value, cudaStream_t s) {
+    if (n <= 0) return;
+    fill_i32_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, n, value);
+}
+
+}  // namespace kb

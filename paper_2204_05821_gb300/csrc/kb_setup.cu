@@ -1,0 +1,216 @@
+// Per-call setup kernels: input validation, the in-edge / both-direction CSR
+// the backward and two-sided equivalences read (paper Defs. "bw-bisim" and
+// "vertex-labeled-bw-bisimulation" use in-neighbours, N^-(v) of Section 3.1),
+// hub discovery, an int64 prefix scan and level-row copies.
+#include <cuda_runtime.h>
+
+#include "kb_internal.cuh"
+
+namespace kb {
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+__global__ void validate_kernel(int64_t n, int64_t m, const int64_t* row, const int32_t* col, Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (t0 == 0 && (row[0] != 0 || row[n] != m)) bad = true;
+    for (int64_t v = t0; v < n; v += stride)
+        if (row[v + 1] < row[v]) bad = true;
+    for (int64_t e = t0; e < m; e += stride) {
+        const int32_t w = col[e];
+        if (w < 0 || (int64_t)w >= n) bad = true;
+    }
+    if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->err, kErrInvalid);
+}
+
+__global__ void in_degree_kernel(int64_t m, const int32_t* col, int64_t* deg) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&deg[col[e]]), 1ull);
+}
+
+// Source vertex of edge e: the largest v with row[v] <= e.
+__device__ __forceinline__ int64_t edge_source(const int64_t* row, int64_t n, int64_t e) {
+    int64_t lo = 0, hi = n;  // row[lo] <= e < row[hi]
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (row[mid] <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void rows_kernel(int64_t n, const int64_t* row, const int64_t* in_prefix, int include_out,
+                            int64_t* row_p, int64_t* cursor) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += stride) {
+        const int64_t r = (include_out ? row[v] : 0) + in_prefix[v];
+        row_p[v] = r;
+        if (v < n) cursor[v] = r + (include_out ? row[v + 1] - row[v] : 0);
+    }
+}
+
+__global__ void place_edges_kernel(int64_t n, int64_t m, const int64_t* row, const int32_t* col, const int32_t* lab,
+                                   int include_out, const int64_t* row_p, int32_t* col_p, int32_t* lab_p,
+                                   int64_t* cursor) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int64_t v = edge_source(row, n, e);
+        const int32_t w = col[e];
+        const int32_t l = lab ? lab[e] : 0;
+        if (include_out) {
+            const int64_t q = row_p[v] + (e - row[v]);
+            col_p[q] = w;
+            if (lab_p) lab_p[q] = l;
+        }
+        const int64_t q = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[w]), 1ull);
+        col_p[q] = (int32_t)((uint32_t)v | 0x80000000u);
+        if (lab_p) lab_p[q] = l;
+    }
+}
+
+__global__ void find_hubs_kernel(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v, int64_t* out_deg,
+                                 int32_t* n_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = row[v + 1] - row[v];
+        if (d > thr) {
+            const int32_t i = atomicAdd(n_out, 1);
+            out_v[i] = (int32_t)v;
+            out_deg[i] = d;
+        }
+    }
+}
+
+// ---- int64 exclusive scan (reduce, scan of block sums, down-sweep)
+constexpr int kT = 1024;
+constexpr int kItems = 4;
+constexpr int kTile = kT * kItems;
+
+__device__ __forceinline__ int64_t block_exscan_i64(int64_t x, int64_t* tmp, int64_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) tmp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = tmp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        tmp[lane] = w;
+    }
+    __syncthreads();
+    const int64_t base = warp > 0 ? tmp[warp - 1] : 0;
+    *total = tmp[31];
+    __syncthreads();
+    return base + incl - x;
+}
+
+__global__ void __launch_bounds__(kT) scan_reduce_kernel(const int64_t* in, int64_t n, int64_t* sums) {
+    __shared__ int64_t tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    int64_t s = 0;
+#pragma unroll
+    for (int u = 0; u < kItems; ++u)
+        if (base + u < n) s += in[base + u];
+    int64_t total;
+    block_exscan_i64(s, tmp, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kT) scan_sums_kernel(int64_t* sums, int64_t nb) {
+    __shared__ int64_t tmp[32];
+    int64_t carry = 0;
+    for (int64_t b = 0; b < nb; b += kT) {
+        const int64_t i = b + threadIdx.x;
+        const int64_t x = i < nb ? sums[i] : 0;
+        int64_t total;
+        const int64_t ex = block_exscan_i64(x, tmp, &total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void __launch_bounds__(kT) scan_down_kernel(const int64_t* in, int64_t n, const int64_t* sums,
+                                                        int64_t* out) {
+    __shared__ int64_t tmp[32];
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    int64_t c[kItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+        c[u] = base + u < n ? in[base + u] : 0;
+        s += c[u];
+    }
+    int64_t total;
+    int64_t ex = block_exscan_i64(s, tmp, &total) + sums[blockIdx.x];
+    __syncthreads();  // every thread has read its inputs before any output is written (in may alias out)
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+        if (base + u < n) out[base + u] = ex;
+        ex += c[u];
+    }
+}
+
+__global__ void write_total_kernel(const int64_t* sums, int64_t nb, int64_t* out, int64_t n) { out[n] = sums[nb]; }
+
+}  // namespace
+
+void launch_validate(int64_t n, int64_t m, const int64_t* row, const int32_t* col, Counters* ctr, cudaStream_t s) {
+    validate_kernel<<<grid_for(n > m ? n : m, 256), 256, 0, s>>>(n, m, row, col, ctr);
+}
+
+void launch_in_degree(int64_t m, const int32_t* col, int64_t* deg, cudaStream_t s) {
+    if (m <= 0) return;
+    in_degree_kernel<<<grid_for(m, 256), 256, 0, s>>>(m, col, deg);
+}
+
+size_t scan_i64_tmp(int64_t n) { return (size_t)((n + kTile - 1) / kTile) + 2; }
+
+void launch_scan_i64(const int64_t* in, int64_t n, int64_t* out, int64_t* tmp, cudaStream_t s) {
+    const int64_t nb = (n + kTile - 1) / kTile;
+    if (nb > 0) scan_reduce_kernel<<<(unsigned)nb, kT, 0, s>>>(in, n, tmp);
+    scan_sums_kernel<<<1, kT, 0, s>>>(tmp, nb);
+    if (nb > 0) scan_down_kernel<<<(unsigned)nb, kT, 0, s>>>(in, n, tmp, out);
+    write_total_kernel<<<1, 1, 0, s>>>(tmp, nb, out, n);
+}
+
+void launch_build_csr(int64_t n, int64_t m, const int64_t* row, const int32_t* col, const int32_t* lab,
+                      const int64_t* in_prefix, int include_out, int64_t* row_p, int32_t* col_p, int32_t* lab_p,
+                      int64_t* cursor, cudaStream_t s) {
+    rows_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(n, row, in_prefix, include_out, row_p, cursor);
+    if (m > 0)
+        place_edges_kernel<<<grid_for(m, 256), 256, 0, s>>>(n, m, row, col, lab, include_out, row_p, col_p, lab_p,
+                                                            cursor);
+}
+
+void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v, int64_t* out_deg, int32_t* n_out,
+                      cudaStream_t s) {
+    if (n <= 0) return;
+    find_hubs_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, row, thr, out_v, out_deg, n_out);
+}
+
+void launch_copy_rows(int32_t* levels, int64_t n, int src, int first, int last, cudaStream_t s) {
+    for (int r = first; r <= last; ++r)
+        if (r != src)
+            cudaMemcpyAsync(levels + (size_t)r * (size_t)n, levels + (size_t)src * (size_t)n,
+                            sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace kb

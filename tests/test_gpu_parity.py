@@ -1,0 +1,237 @@
+"""GPU path against the CPU oracle, element by element (exact integers).
+
+Every test calls the library through its C ABI (the ctypes binding) and
+compares all levels, block counts and the last refined level with the
+oracle on the same seeded graph.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from paper_fixture import load, partition
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2204_05821_gb300 as kb  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = kb.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_levels(ctx, g, d, vl, el, k, early_stop=True, **kw):
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    res = ctx.refine(dg, k, kb.Options(direction=d, use_vertex_labels=vl, use_edge_labels=el,
+                                       early_stop=early_stop, **kw))
+    torch.cuda.synchronize()
+    return res.levels.cpu().numpy(), res.counts, res.levels_computed
+
+
+def assert_same(ctx, g, d, vl, el, k, early_stop=True, **kw):
+    L, C, lc = oracle.refine_graph(g, d, vl, el, k=k, early_stop=early_stop)
+    got, gc, glc = gpu_levels(ctx, g, d, vl, el, k, early_stop, **kw)
+    for i in range(k + 1):
+        if not np.array_equal(got[i], L[i]):
+            bad = np.nonzero(got[i] != L[i])[0]
+            raise AssertionError("level %d differs at %d vertices, first %s: gpu %s oracle %s (dir %d vl %s el %s %s)"
+                                 % (i, bad.size, bad[:5], got[i][bad[:5]], L[i][bad[:5]], d, vl, el, kw))
+    assert np.array_equal(gc, C), (gc, C)
+    assert glc == lc
+    return L, C
+
+
+# ---------------------------------------------------------------- the paper's example
+
+
+@pytest.mark.parametrize("table", ["fw", "bw", "sch", "kau"])
+def test_paper_tables(ctx, table):
+    g, tables = load()
+    t = tables[table]
+    got, counts, _ = gpu_levels(ctx, g, t["direction"], t["use_vertex_labels"], t["use_edge_labels"], 2,
+                                early_stop=False)
+    for i, expected in t["levels"].items():
+        assert partition(got[i]) == expected
+        assert counts[i] == len(expected)
+
+
+def test_presets_match_definitions(ctx):
+    g, tables = load()
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    for name, opts in (("sch", kb.Options.schaetzle(early_stop=False)), ("kau", kb.Options.kaushik(early_stop=False))):
+        res = ctx.refine(dg, 2, opts)
+        got = res.levels.cpu().numpy()
+        for i, expected in tables[name]["levels"].items():
+            assert partition(got[i]) == expected
+
+
+# ---------------------------------------------------------------- configuration 1 (ER, 10k vertices, 50k edges)
+
+
+@pytest.fixture(scope="module")
+def er_tiny():
+    return graphgen.make(graphgen.CONFIG_TINY)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+@pytest.mark.parametrize("vl,el", [(True, True), (False, True), (True, False), (False, False)])
+def test_config_tiny_all_variants(ctx, er_tiny, d, vl, el):
+    assert_same(ctx, er_tiny, d, vl, el, 10, early_stop=False)
+    assert_same(ctx, er_tiny, d, vl, el, 10, early_stop=True)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_weak_hash_forces_compare_path(ctx, er_tiny, d):
+    # hash of the previous block only: every vertex of a block collides, so
+    # only the full signature compare separates them
+    assert_same(ctx, er_tiny, d, True, True, 6, hash_mode=1)
+
+
+@pytest.mark.parametrize("thr", [1, 3, 17, 64])
+def test_hub_path_equivalent(ctx, er_tiny, thr):
+    for d in (0, 1, 2):
+        assert_same(ctx, er_tiny, d, True, True, 6, hub_threshold=thr)
+
+
+@pytest.mark.parametrize("thr", [2, 8])
+def test_hub_path_weak_hash(ctx, er_tiny, thr):
+    assert_same(ctx, er_tiny, 2, True, True, 5, hub_threshold=thr, hash_mode=1)
+
+
+@pytest.mark.parametrize("lf", [0.05, 0.5, 0.9])
+def test_load_factor_invariance(ctx, er_tiny, lf):
+    assert_same(ctx, er_tiny, 0, True, True, 8, load_factor=lf)
+
+
+# ---------------------------------------------------------------- random small graphs and edge cases
+
+
+def test_random_tiny_graphs(ctx):
+    rng = np.random.Generator(np.random.PCG64(31))
+    for _ in range(150):
+        g = graphgen.tiny_random(rng, n_max=40, m_max=120, n_labels=int(rng.integers(1, 4)))
+        d = int(rng.integers(0, 3))
+        assert_same(ctx, g, d, bool(rng.integers(0, 2)), bool(rng.integers(0, 2)), int(rng.integers(0, 7)),
+                    hash_mode=int(rng.integers(0, 2)), hub_threshold=int(rng.choice([0, 1, 2, 5])))
+
+
+def test_edge_cases(ctx):
+    cases = [
+        graphgen.from_edges(1, [], [], [], [5]),
+        graphgen.from_edges(1, [0, 0, 0], [0, 0, 0], [1, 1, 2], [5]),  # self loops, parallel edges
+        graphgen.from_edges(5, [], [], [], [3, -7, 3, 2147483647, -2147483648]),
+        graphgen.path_graph(1000),
+        graphgen.cycle_graph(777),
+        graphgen.binary_tree(10),
+    ]
+    for g in cases:
+        for d in (0, 1, 2):
+            for k in (0, 1, 5):
+                assert_same(ctx, g, d, True, True, k)
+                assert_same(ctx, g, d, False, False, k, early_stop=False)
+
+
+def test_extreme_labels(ctx):
+    rng = np.random.Generator(np.random.PCG64(3))
+    g = graphgen.erdos_renyi(2000, 9000, 3, 3, seed=5)
+    g.elabel = rng.choice(np.array([-2147483648, -1, 0, 2147483647], dtype=np.int32), size=g.m)
+    g.vlabel = rng.choice(np.array([-2147483648, 7, 2147483647], dtype=np.int32), size=g.n)
+    for d in (0, 1, 2):
+        assert_same(ctx, g, d, True, True, 6)
+
+
+def test_hot_slot_and_hubs(ctx):
+    # one vertex receives every edge and one vertex sends 100k edges: a hot
+    # table slot, a multi-chunk hub with heavy duplicate pairs, and hubs in
+    # the in-direction
+    n = 50_000
+    rng = np.random.Generator(np.random.PCG64(8))
+    src = np.concatenate([np.arange(n), np.full(100_000, 17), rng.integers(0, n, 30_000)])
+    dst = np.concatenate([np.full(n, 3), rng.integers(0, n, 100_000), rng.integers(0, 100, 30_000)])
+    lab = rng.integers(0, 3, size=src.shape[0])
+    g = graphgen.from_edges(n, src, dst, lab, rng.integers(0, 4, size=n))
+    for d in (0, 1, 2):
+        assert_same(ctx, g, d, True, True, 6)
+        assert_same(ctx, g, d, False, True, 4, hash_mode=1)
+
+
+def test_subtile_boundaries(ctx):
+    # degrees around the sub-tile split and the hub threshold: 2047, 2048
+    # (largest non-hub), 2049 (hub), mixed with zero-degree runs, over several
+    # 512-vertex tiles with a ragged last tile
+    degs = []
+    rng = np.random.Generator(np.random.PCG64(12))
+    for t in range(7):
+        degs += [2047, 0, 0, 2048, 1, 2049, 0] + list(rng.integers(0, 9, size=505))
+    degs = np.array(degs[: 7 * 512 - 137])
+    n = degs.shape[0]
+    src = np.repeat(np.arange(n), degs)
+    dst = rng.integers(0, n, size=src.shape[0])
+    dst[::3] = rng.integers(0, 40, size=dst[::3].shape[0])  # many duplicate pairs
+    lab = rng.integers(0, 2, size=src.shape[0])
+    g = graphgen.from_edges(n, src, dst, lab, rng.integers(0, 3, size=n))
+    for d in (0, 1, 2):
+        assert_same(ctx, g, d, True, True, 5)
+    assert_same(ctx, g, 0, True, True, 4, hash_mode=1)
+
+
+# ---------------------------------------------------------------- resume, initial partition, host buffers
+
+
+def test_refine_from_matches_full_run(ctx, er_tiny):
+    for d in (0, 1, 2):
+        L, C, _ = oracle.refine_graph(er_tiny, d, True, True, k=8, early_stop=False)
+        dg = kb.DeviceGraph.from_numpy(er_tiny, "cuda:0")
+        for j in (0, 2, 5):
+            start = torch.from_numpy(L[j]).to("cuda:0")
+            res = ctx.refine_from(dg, start, j, 8, kb.Options(direction=d, early_stop=False))
+            got = res.levels.cpu().numpy()
+            assert np.array_equal(got[j:], L[j:])
+            assert np.array_equal(res.counts[j:], C[j:])
+
+
+def test_initial_partition(ctx, er_tiny):
+    init = (er_tiny.vlabel.astype(np.int64) * 1000003 % 7 - 3).astype(np.int32)
+    L, C, _ = oracle.refine_graph(er_tiny, 0, False, True, k=6, early_stop=False, initial=init)
+    dg = kb.DeviceGraph.from_numpy(er_tiny, "cuda:0")
+    res = ctx.refine_from(dg, torch.from_numpy(init).to("cuda:0"), 0, 6, kb.Options(early_stop=False))
+    assert np.array_equal(res.levels.cpu().numpy(), L) and np.array_equal(res.counts, C)
+
+
+def test_host_buffers(ctx, er_tiny):
+    for d in (0, 2):
+        L, C, lc = oracle.refine_graph(er_tiny, d, True, True, k=10)
+        res = ctx.refine_host(er_tiny.row_offsets, er_tiny.col, er_tiny.elabel, er_tiny.vlabel, 10,
+                              kb.Options(direction=d))
+        assert np.array_equal(res.levels, L) and np.array_equal(res.counts, C) and res.levels_computed == lc
+
+
+def test_torch_workspace(er_tiny):
+    with kb.Context(0, torch_workspace=True) as c:
+        assert_same(c, er_tiny, 1, True, True, 6)
+        dg = kb.DeviceGraph.from_numpy(er_tiny, "cuda:0")
+        need = c.workspace_size(dg, 6, kb.Options(direction=1))
+        assert need > 0
+
+
+def test_invalid_inputs_rejected(ctx):
+    g = graphgen.erdos_renyi(100, 300, 2, 2, seed=1)
+    bad = graphgen.Graph(n=g.n, m=g.m, row_offsets=g.row_offsets.copy(), col=g.col.copy(), elabel=g.elabel,
+                         vlabel=g.vlabel)
+    bad.col[5] = g.n + 3
+    with pytest.raises(kb.KbError) as e:
+        gpu_levels(ctx, bad, 0, True, True, 3)
+    assert e.value.status == 1
+    bad2 = graphgen.Graph(n=g.n, m=g.m, row_offsets=g.row_offsets.copy(), col=g.col, elabel=g.elabel,
+                          vlabel=g.vlabel)
+    bad2.row_offsets[10], bad2.row_offsets[11] = bad2.row_offsets[11] + 1, bad2.row_offsets[10]
+    with pytest.raises(kb.KbError):
+        gpu_levels(ctx, bad2, 0, True, True, 3)
+    with pytest.raises(kb.KbError):
+        gpu_levels(ctx, g, 0, True, True, 3, hub_threshold=5000)
+    # the context stays usable after errors
+    assert_same(ctx, g, 0, True, True, 3)
