@@ -33,6 +33,8 @@ import graphgen  # noqa: E402
 
 WORKLOADS = {
     "large": graphgen.CONFIG_LARGE,
+    # the same recipe at a tenth of the size: small enough for multi-pass profiling
+    "large_tenth": graphgen.scaled(graphgen.CONFIG_LARGE, 0.1),
     "rdf": graphgen.CONFIG_RDF,
     "tiny": graphgen.CONFIG_TINY,
 }
@@ -257,23 +259,29 @@ def run_ours(args, rank, world, local):
         total_edge_rounds = float(rounds) * m
     value = total_edge_rounds / elapsed
 
-    # roofline of the dominant kernel family
-    dom = max(fam_ms, key=lambda kname: fam_ms[kname])
-    hub_thr = 2048
+    # roofline of the dominant kernel family (algorithmic bytes per launch)
+    hub_thr, small_max = 2048, 32
     deg = (wl["row_offsets"][1:] - wl["row_offsets"][:-1])
-    tile_edges = int(deg[deg <= hub_thr].sum().item())
-    hub_edges = m - tile_edges
-    n_hubs = int((deg > hub_thr).sum().item())
+    small = deg <= small_max
+    hub = deg > hub_thr
+    med = ~small & ~hub
+    small_edges = int(deg[small].sum().item())
+    med_edges = int(deg[med].sum().item())
+    hub_edges = m - small_edges - med_edges
+    n_small, n_med, n_hubs = int(small.sum().item()), int(med.sum().item()), int(hub.sum().item())
+    del deg, small, hub, med
     algo_bytes = {
-        # 12 B per staged edge (neighbour id, edge label, gathered block) plus
-        # per vertex: row offset 8, own block 4, slot write 4, table entry 8
-        "signature": 12 * tile_edges + 24 * n,
+        # 12 B per edge (neighbour id 4, edge label 4, gathered block 4) and per
+        # vertex 24 B (row offset 8, own block 4, slot write 4, table entry 8)
+        "small": 12 * small_edges + 24 * n_small,
+        "medium": 12 * med_edges + 28 * n_med,
         "hub_chunk": 12 * hub_edges,
         "hub_final": 24 * n_hubs,
-        # bitmap scan + per vertex: slot 4, table entry 8, level write 4
-        "renumber": 16 * n + n // 8,
+        # per vertex: slot 4, table entry 8, level write 4; bitmap read twice
+        "renumber": 16 * n + n // 4,
         "other": n // 8,
     }
+    dom = max(fam_ms, key=lambda kname: fam_ms[kname])
     peak, peak_kind = peaks()
     per_launch_ms = fam_ms[dom] / max(1, fam_n[dom])
     achieved = algo_bytes.get(dom, 0) / (per_launch_ms / 1000.0) / 1e9
@@ -316,6 +324,9 @@ def run_ours(args, rank, world, local):
                 "warmup": args.warmup, "ms_per_step": 1000 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": dict(describe(args.workload, cfg, k, "out"),
+                               vertex_classes={"small_le32": [n_small, small_edges], "medium": [n_med, med_edges],
+                                               "hub_gt2048": [n_hubs, hub_edges]},
+                               counts_last_step=[int(x) for x in r.counts],
                                l2="inputs larger than L2 (CSR %.1f GB); no flush" % ((8 * (n + 1) + 8 * m) / 1e9),
                                parallelism="replicas" if world > 1 else "single GPU",
                                rounds_per_step=rounds / args.steps),

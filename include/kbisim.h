@@ -161,12 +161,13 @@ kb_status kb_refine_host(kb_context* ctx, const kb_graph* g, const kb_options* o
  *   kernel_ms[j] / kernel_launches[j] for j < KB_KERNEL_COUNT: summed device time
  *   and launches of each kernel family inside the rounds. */
 enum {
-    KB_KERNEL_SIGNATURE = 0,   /* tile signature + dedup + hash + block-table insert */
-    KB_KERNEL_HUB_CHUNK = 1,   /* hub pairs: chunk dedup + global set insert */
-    KB_KERNEL_HUB_FINAL = 2,   /* hub hash + block-table insert */
-    KB_KERNEL_RENUMBER = 3,    /* prefix scan of block minima + canonical assignment */
-    KB_KERNEL_OTHER = 4,       /* clears, copies */
-    KB_KERNEL_COUNT = 5
+    KB_KERNEL_SMALL = 0,       /* warp kernel: vertices with <= 32 edges (signature, dedup, hash, insert) */
+    KB_KERNEL_MEDIUM = 1,      /* tile kernel: vertices with 33..hub_threshold edges */
+    KB_KERNEL_HUB_CHUNK = 2,   /* hub pairs: chunk dedup + global set insert */
+    KB_KERNEL_HUB_FINAL = 3,   /* hub hash + block-table insert */
+    KB_KERNEL_RENUMBER = 4,    /* prefix scan of block minima + canonical assignment */
+    KB_KERNEL_OTHER = 5,       /* clears, copies */
+    KB_KERNEL_COUNT = 6
 };
 kb_status kb_set_timing(kb_context* ctx, int enable);
 kb_status kb_get_timing(const kb_context* ctx, float* round_ms, int max_rounds, int* n_rounds,

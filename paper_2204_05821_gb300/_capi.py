@@ -21,8 +21,8 @@ KB_ERR_DEVICE_CHECK = 6
 KB_ERR_NOT_FOUND = 7
 
 KB_DIR_OUT, KB_DIR_IN, KB_DIR_BOTH = 0, 1, 2
-KB_KERNEL_COUNT = 5
-KERNEL_NAMES = ("signature", "hub_chunk", "hub_final", "renumber", "other")
+KB_KERNEL_COUNT = 6
+KERNEL_NAMES = ("small", "medium", "hub_chunk", "hub_final", "renumber", "other")
 
 
 class KbGraph(ctypes.Structure):

@@ -26,6 +26,8 @@ struct kb_context {
     kb::Counters* h_ctr = nullptr;  // pinned
     int32_t* d_hub_n = nullptr;
     int32_t* h_hub_n = nullptr;  // pinned
+    int64_t* d_med_n = nullptr;
+    int64_t* h_med_n = nullptr;  // pinned
     void* hub_tmp = nullptr;     // unordered hub list during planning
     size_t hub_tmp_bytes = 0;
     void* plan_tmp = nullptr;    // in-degree scratch used by kb_workspace_size
@@ -41,7 +43,7 @@ struct kb_context {
     std::vector<float> round_ms;
     float kernel_ms[KB_KERNEL_COUNT] = {};
     int64_t kernel_launches[KB_KERNEL_COUNT] = {};
-    cudaEvent_t ev[2 * 8] = {};
+    cudaEvent_t ev[2 * 10] = {};
 };
 
 namespace {
@@ -91,11 +93,12 @@ struct Plan {
     // hubs (host copies, ascending vertex id)
     std::vector<int32_t> hub_v;
     std::vector<int64_t> chunk_off, set_off, list_off;
+    std::vector<int32_t> chunk_hub;
     // layout
     size_t o_rowp = 0, o_colp = 0, o_labp = 0, o_cursor = 0, o_inpref = 0, o_i64tmp = 0;
     size_t csr_bytes = 0;
-    size_t o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
-           o_listoff = 0, o_acc = 0, o_cnt = 0, o_sets = 0, o_lists = 0;
+    size_t o_emin = 0, o_med = 0, o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
+           o_listoff = 0, o_chunkhub = 0, o_acc = 0, o_cnt = 0, o_sets = 0, o_lists = 0;
     size_t total = 0;
 };
 
@@ -120,6 +123,8 @@ void layout_round(Plan& P) {
     auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
     const int64_t nw = (P.n >> 5) + 1;
     const size_t H = P.hub_v.size();
+    P.o_med = take(sizeof(int32_t) * (size_t)(std::min<int64_t>(P.n, P.m_proc / 2 + 1) + 1));
+    P.o_emin = take(sizeof(uint64_t) * (size_t)std::max<int64_t>(P.n, 1));
     P.o_slot = take(sizeof(int32_t) * (size_t)std::max<int64_t>(P.n, 1));
     P.o_table = take(sizeof(uint64_t) * (size_t)P.cap);
     P.o_bitmap = take(sizeof(uint32_t) * (size_t)nw);
@@ -129,6 +134,7 @@ void layout_round(Plan& P) {
     P.o_chunk = take(sizeof(int64_t) * (H + 1));
     P.o_setoff = take(sizeof(int64_t) * (H + 1));
     P.o_listoff = take(sizeof(int64_t) * (H + 1));
+    P.o_chunkhub = take(sizeof(int32_t) * P.chunk_hub.size());
     P.o_acc = take(sizeof(uint64_t) * H);
     P.o_cnt = take(sizeof(uint32_t) * H);
     P.o_sets = take(sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0));
@@ -242,6 +248,9 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
         P.set_off[(size_t)i + 1] = P.set_off[(size_t)i] + (int64_t)next_pow2((uint64_t)(2 * d));
         P.list_off[(size_t)i + 1] = P.list_off[(size_t)i] + d;
     }
+    P.chunk_hub.resize((size_t)P.chunk_off[(size_t)H]);
+    for (int32_t i = 0; i < H; ++i)
+        for (int64_t c = P.chunk_off[(size_t)i]; c < P.chunk_off[(size_t)i + 1]; ++c) P.chunk_hub[(size_t)c] = i;
     return KB_OK;
 }
 
@@ -295,15 +304,15 @@ kb_status acquire_workspace(kb_context* ctx, size_t bytes, char** base) {
 struct Timer {
     kb_context* ctx;
     int used = 0;
-    int fam[8];
+    int fam[10];
     explicit Timer(kb_context* c) : ctx(c) {}
     void begin(int family) {
-        if (!ctx->timing || used >= 8) return;
+        if (!ctx->timing || used >= 10) return;
         fam[used] = family;
         cudaEventRecord(ctx->ev[2 * used], ctx->stream);
     }
     void end() {
-        if (!ctx->timing || used >= 8) return;
+        if (!ctx->timing || used >= 10) return;
         cudaEventRecord(ctx->ev[2 * used + 1], ctx->stream);
         ++used;
     }
@@ -389,6 +398,8 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
             R.csr_bytes = 0;
             layout_round(R);
             KB_TRY(ensure_buffer(ctx, &ctx->own_ws, &ctx->own_ws_bytes, std::max<size_t>(R.total, 256)));
+            P.o_med = R.o_med;
+            P.o_emin = R.o_emin;
             P.o_slot = R.o_slot;
             P.o_table = R.o_table;
             P.o_bitmap = R.o_bitmap;
@@ -398,6 +409,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
             P.o_chunk = R.o_chunk;
             P.o_setoff = R.o_setoff;
             P.o_listoff = R.o_listoff;
+            P.o_chunkhub = R.o_chunkhub;
             P.o_acc = R.o_acc;
             P.o_cnt = R.o_cnt;
             P.o_sets = R.o_sets;
@@ -418,10 +430,13 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
             p.lab = P.labels ? g->edge_labels : nullptr;
         }
         p.hub_threshold = P.thr;
+        p.small_max = std::min(kb::kSmallDegree, P.thr);
         p.hash_mode = opt->hash_mode;
         p.table = reinterpret_cast<uint64_t*>(ws + P.o_table);
         p.mask = P.cap - 1;
         p.slot_of = reinterpret_cast<int32_t*>(ws + P.o_slot);
+        p.emin = reinterpret_cast<uint64_t*>(ws + P.o_emin);
+        KB_CUDA(ctx, cudaMemsetAsync(p.emin, 0xff, sizeof(uint64_t) * (size_t)n, s));
         p.bitmap = reinterpret_cast<uint32_t*>(ws + P.o_bitmap);
         p.ctr = ctx->d_ctr;
         const size_t H = P.hub_v.size();
@@ -430,6 +445,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         p.hub_chunk_off = reinterpret_cast<const int64_t*>(ws + P.o_chunk);
         p.hub_set_off = reinterpret_cast<const int64_t*>(ws + P.o_setoff);
         p.hub_list_off = reinterpret_cast<const int64_t*>(ws + P.o_listoff);
+        p.chunk_hub = reinterpret_cast<const int32_t*>(ws + P.o_chunkhub);
         p.hub_sets = reinterpret_cast<uint64_t*>(ws + P.o_sets);
         p.hub_lists = reinterpret_cast<uint64_t*>(ws + P.o_lists);
         p.hub_acc = reinterpret_cast<uint64_t*>(ws + P.o_acc);
@@ -444,6 +460,20 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
                                          cudaMemcpyHostToDevice, s));
             KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_listoff, P.list_off.data(), sizeof(int64_t) * (H + 1),
                                          cudaMemcpyHostToDevice, s));
+            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunkhub, P.chunk_hub.data(), sizeof(int32_t) * P.chunk_hub.size(),
+                                         cudaMemcpyHostToDevice, s));
+        }
+        // medium vertices, once per call
+        int32_t* med = reinterpret_cast<int32_t*>(ws + P.o_med);
+        p.med_v = med;
+        p.n_med = 0;
+        if (g->m > 0) {
+            KB_CUDA(ctx, cudaMemsetAsync(ctx->d_med_n, 0, sizeof(int64_t), s));
+            kb::launch_classify(n, p.row, p.small_max, P.thr, med, ctx->d_med_n, s);
+            KB_CUDA(ctx, cudaGetLastError());
+            KB_CUDA(ctx, cudaMemcpyAsync(ctx->h_med_n, ctx->d_med_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            KB_CUDA(ctx, cudaStreamSynchronize(s));
+            p.n_med = *ctx->h_med_n;
         }
         const int64_t total_chunks = H ? P.chunk_off[H] : 0;
         const size_t set_bytes = sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0);
@@ -466,7 +496,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
             KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
             KB_CUDA(ctx, cudaMemsetAsync(p.bitmap, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
             p.prev = init_key;
-            kb::launch_tile_round(p, true, s);
+            kb::launch_small_round(p, true, s);
             kb::launch_renumber(p, prefix, scan_tmp, row0, s);
             KB_CUDA(ctx, cudaGetLastError());
             KB_TRY(read_counters(ctx));
@@ -481,6 +511,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         for (int i = i_start + 1; i <= k; ++i) {
             Timer T(ctx);
             KB_TRY(next_epoch());
+            p.ehigh = 0xffffffffu - (uint32_t)(i - i_start);
             p.prev = levels + (size_t)(i - 1) * (size_t)n;
             int32_t* out = levels + (size_t)i * (size_t)n;
             T.begin(KB_KERNEL_OTHER);
@@ -488,9 +519,14 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
             kb::launch_clear_round(p, s);
             if (set_bytes) KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, set_bytes, s));
             T.end();
-            T.begin(KB_KERNEL_SIGNATURE);
-            kb::launch_tile_round(p, false, s);
+            T.begin(KB_KERNEL_SMALL);
+            kb::launch_small_round(p, false, s);
             T.end();
+            if (p.n_med) {
+                T.begin(KB_KERNEL_MEDIUM);
+                kb::launch_tile_round(p, s);
+                T.end();
+            }
             if (H) {
                 T.begin(KB_KERNEL_HUB_CHUNK);
                 kb::launch_hub_chunk(p, total_chunks, s);
@@ -574,6 +610,8 @@ kb_status kb_create(kb_context** out, int device, void* stream) {
     ctx->stream = reinterpret_cast<cudaStream_t>(stream);
     if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&ctx->d_ctr, sizeof(Counters)) != cudaSuccess ||
         cudaMalloc(&ctx->d_hub_n, sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_med_n, sizeof(int64_t)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_med_n, sizeof(int64_t)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_ctr, sizeof(Counters)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_hub_n, sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -591,6 +629,8 @@ kb_status kb_destroy(kb_context* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
     cudaFree(ctx->d_ctr);
     cudaFree(ctx->d_hub_n);
+    cudaFree(ctx->d_med_n);
+    cudaFreeHost(ctx->h_med_n);
     cudaFreeHost(ctx->h_ctr);
     cudaFreeHost(ctx->h_hub_n);
     cudaFree(ctx->own_ws);

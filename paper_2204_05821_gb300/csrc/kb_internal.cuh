@@ -25,6 +25,7 @@ constexpr int kDefaultHubThreshold = 2048;
 constexpr int kHubChunk = 4096;  // edges per hub-chunk CTA (== kStage)
 constexpr int kHubFinalThreads = 256;
 constexpr int kProbeLimit = 1 << 22;  // bound on block-table probes per vertex
+constexpr int kSmallDegree = 32;      // vertices with at most this many edges take the warp kernel
 
 constexpr uint64_t kEmptyPair = ~0ull;  // block field 0x7fffffff never occurs (n <= 2^31-2)
 
@@ -45,17 +46,25 @@ struct RoundParams {
     const int32_t* lab;   // [m_proc] edge label or nullptr (all labels 0)
     const int32_t* prev;  // [n] previous level (vertex labels at level 0)
     int32_t hub_threshold;
+    int32_t small_max;    // min(kSmallDegree, hub_threshold)
     int32_t hash_mode;
     uint32_t epoch;       // 1..255, tags this round's table entries
     uint64_t* table;      // [mask+1] block table
     uint64_t mask;
-    int32_t* slot_of;     // [n] table slot of every vertex
+    int32_t* slot_of;     // [n] table slot of every vertex; 0x80000000|own for an empty signature
+    uint64_t* emin;       // [n] smallest vertex with an empty signature per own block:
+                          //     (ehigh << 32) | vertex, ehigh decreasing from round to round
+    uint32_t ehigh;
     uint32_t* bitmap;     // [n/32+1] bit v set iff v is the smallest member of its block
     Counters* ctr;
+    // medium vertices (small_max < degree <= hub_threshold), processed by the tile kernel
+    const int32_t* med_v;
+    int64_t n_med;
     // hubs (vertices with more than hub_threshold edges)
     int32_t n_hubs;
     const int32_t* hub_v;          // [n_hubs] ascending
     const int64_t* hub_chunk_off;  // [n_hubs+1]
+    const int32_t* chunk_hub;      // [total chunks] hub index of every chunk
     const int64_t* hub_set_off;    // [n_hubs+1] power-of-two set per hub
     const int64_t* hub_list_off;   // [n_hubs+1] unique-pair list per hub
     uint64_t* hub_sets;
@@ -105,7 +114,8 @@ __device__ __forceinline__ uint32_t table_hi(uint64_t h, uint32_t epoch) {
 // ---------------------------------------------------------------- launchers
 // Signature rounds (kb_kernels.cu)
 void launch_clear_round(const RoundParams& p, cudaStream_t s);
-void launch_tile_round(const RoundParams& p, bool level0, cudaStream_t s);
+void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s);
+void launch_tile_round(const RoundParams& p, cudaStream_t s);
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s);
 void launch_hub_final(const RoundParams& p, cudaStream_t s);
 // Canonical renumbering: prefix of block minima, then ids.
@@ -131,6 +141,10 @@ void launch_build_csr(int64_t n, int64_t m, const int64_t* row, const int32_t* c
 // their degrees in out_deg; count in *n_out.
 void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v, int64_t* out_deg,
                       int32_t* n_out, cudaStream_t s);
+// Append the vertices with lo < degree <= hi to out (order within a warp
+// preserved); count in *n_out.
+void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,
+                     cudaStream_t s);
 // Copy row src of the level store to the rows [first, last] of levels.
 void launch_copy_rows(int32_t* levels, int64_t n, int src, int first, int last, cudaStream_t s);
 

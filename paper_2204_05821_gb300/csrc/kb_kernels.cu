@@ -14,15 +14,13 @@
 //      canonical id (rank of its smallest member).
 #include <cuda_runtime.h>
 
+#include "kb_device.cuh"
 #include "kb_internal.cuh"
 
 namespace kb {
 namespace {
 
-constexpr uint32_t kFull = 0xffffffffu;
 enum : uint8_t { kPending = 0, kDone = 1, kSkip = 2 };
-
-__device__ __forceinline__ void set_error(Counters* c, int32_t bit) { atomicOr(&c->err, bit); }
 
 // Exclusive scan of one int per thread over a CTA of NT threads.
 template <int NT>
@@ -52,69 +50,17 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* warp_tmp, int* t
     return base + incl - x;
 }
 
-__device__ __forceinline__ uint64_t volatile_load(const uint64_t* p) {
-    return *reinterpret_cast<const volatile uint64_t*>(p);
-}
-
-// Toggle membership of v in the set of block minima.  Every vertex that ever
-// becomes the minimum of its slot is toggled on once and off once when a
-// smaller member replaces it, so the final bitmap holds exactly the minima,
-// whatever order the toggles land in.
-__device__ __forceinline__ void toggle_min(uint32_t* bitmap, uint32_t v) {
-    atomicXor(&bitmap[v >> 5], 1u << (v & 31));
-}
-
-// Join slot `pos` (same epoch and tag as ours) with vertex v.
-__device__ __forceinline__ void join_slot(const RoundParams& p, uint64_t pos, uint32_t hi, uint32_t v) {
-    const uint64_t want = ((uint64_t)hi << 32) | v;
-    const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(&p.table[pos]),
-                                   (unsigned long long)want);
-    const uint32_t prev_min = (uint32_t)old;
-    if (v < prev_min) {
-        toggle_min(p.bitmap, v);
-        toggle_min(p.bitmap, prev_min);
-    }
-    p.slot_of[v] = (int32_t)pos;
-}
-
-// Probe the block table from *pos.  Returns 0 when v inserted a new key,
-// 1 with *rep set when a slot with our tag was found (a signature compare
-// decides), 2 when the probe limit was hit.
-__device__ __forceinline__ int probe_table(const RoundParams& p, uint64_t* pos_io, uint32_t hi, uint32_t v,
-                                           uint32_t* rep) {
-    uint64_t pos = *pos_io;
-    for (int it = 0; it < kProbeLimit; ++it) {
-        uint64_t cur = volatile_load(&p.table[pos]);
-        if ((uint32_t)(cur >> 56) != p.epoch) {
-            const uint64_t want = ((uint64_t)hi << 32) | v;
-            const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(&p.table[pos]),
-                                           (unsigned long long)cur, (unsigned long long)want);
-            if (old == cur) {
-                p.slot_of[v] = (int32_t)pos;
-                toggle_min(p.bitmap, v);
-                *pos_io = pos;
-                return 0;
-            }
-            cur = old;
-            if ((uint32_t)(cur >> 56) != p.epoch) continue;
-        }
-        if ((uint32_t)(cur >> 32) == hi) {
-            *rep = (uint32_t)cur;
-            *pos_io = pos;
-            return 1;
-        }
-        pos = (pos + 1) & p.mask;
-    }
-    return 2;
-}
-
 // ----------------------------------------------------------------------------
-// Tile kernel: kTileVerts consecutive vertices per CTA, one thread per vertex.
+// Tile kernel: kTileVerts medium vertices (small_max < degree <= hub_threshold)
+// per CTA, taken from the medium-vertex list; one thread per vertex.  Their
+// edges are staged in shared memory, deduplicated per vertex with a shared
+// hash set, hashed, and inserted in the block table with a full signature
+// compare on every tag match.
 // ----------------------------------------------------------------------------
-template <bool kLevel0>
 __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const RoundParams p) {
     __shared__ int64_t s_row[kTileVerts + 1];
     __shared__ int32_t s_eoff[kTileVerts + 1];
+    __shared__ int32_t s_vid[kTileVerts];
     __shared__ uint64_t s_pair[kStage];
     __shared__ uint16_t s_seg[kStage];
     __shared__ uint32_t s_set[kSetCap];  // bits 15..0: staged index + 1; bits 31..16: compare stamp
@@ -132,23 +78,24 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int64_t v0 = (int64_t)blockIdx.x * kTileVerts;
-    const int nv = (int)min((int64_t)kTileVerts, p.n - v0);
+    const int64_t base = (int64_t)blockIdx.x * kTileVerts;
+    const int nv = (int)min((int64_t)kTileVerts, p.n_med - base);
 
-    // Offsets of the tile and capped degrees (hubs contribute no edges here).
-    if (!kLevel0) {
-        for (int i = tid; i <= nv; i += kTileThreads) s_row[i] = p.row[v0 + i];
-    }
-    __syncthreads();
     int cdeg = 0;
     uint8_t st = kSkip;
+    int32_t vid = 0;
+    int64_t rs = 0;
     if (tid < nv) {
-        st = kPending;
-        if (!kLevel0) {
-            const int64_t d = s_row[tid + 1] - s_row[tid];
-            if (d > p.hub_threshold) st = kSkip; else cdeg = (int)d;
+        vid = p.med_v[base + tid];
+        rs = p.row[vid];
+        const int64_t d = p.row[(int64_t)vid + 1] - rs;
+        if (d > p.small_max && d <= p.hub_threshold) {
+            st = kPending;
+            cdeg = (int)d;
         }
     }
+    s_vid[tid] = vid;
+    s_row[tid] = rs;
     s_state[tid] = st;
     int total;
     const int eo = block_exclusive_scan<kTileThreads>(cdeg, s_warp, &total);
@@ -187,7 +134,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
         if (tid >= jlo && tid < jhi) { s_acc[tid] = 0ull; s_cnt[tid] = 0u; }
         __syncthreads();
 
-        if (!kLevel0) {
+        {
             // Stage: coalesced streaming loads of neighbours and labels, then the
             // gather of their previous blocks; four edges per thread in flight.
             for (int base = 0; base < E; base += 4 * kTileThreads) {
@@ -227,8 +174,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
             }
             __syncthreads();
 
-            // Drop duplicate pairs per vertex (set semantics) and accumulate the
-            // order-independent hash of each vertex's distinct pairs.
+            // Drop duplicate pairs per vertex (set semantics): the first copy of
+            // each pair gets bit 15 of its segment word.
             for (int le = tid; le < E; le += kTileThreads) {
                 const uint64_t pr = s_pair[le];
                 const uint32_t j = s_seg[le];
@@ -238,16 +185,38 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
                     if (cur == 0u) {
                         const uint32_t old = atomicCAS(&s_set[slot], 0u, (uint32_t)(le + 1));
                         if (old == 0u) {
-                            atomicAdd(reinterpret_cast<unsigned long long*>(&s_acc[j]),
-                                      (unsigned long long)pair_mix(pr));
-                            atomicAdd(&s_cnt[j], 1u);
+                            s_seg[le] = (uint16_t)(j | 0x8000u);
                             break;
                         }
                         cur = old;
                     }
                     const int idx = (int)(cur & 0xffffu) - 1;
-                    if (s_pair[idx] == pr && s_seg[idx] == j) break;
+                    if (s_pair[idx] == pr && (s_seg[idx] & 0x7fffu) == j) break;
                     slot = (slot + 1) & (kSetCap - 1);
+                }
+            }
+            __syncthreads();
+            // Order-independent hash of each vertex's distinct pairs: one warp
+            // per vertex sums the pair mixes of its flagged edges.
+            for (int j = jlo + warp; j < jhi; j += kTileThreads / 32) {
+                const int a = s_eoff[j] - elo;
+                const int b = (j + 1 == jhi ? ehi : s_eoff[j + 1]) - elo;
+                uint64_t acc = 0;
+                uint32_t cnt = 0;
+                for (int le = a + lane; le < b; le += 32) {
+                    if (s_seg[le] & 0x8000u) {
+                        acc += pair_mix(s_pair[le]);
+                        ++cnt;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc += __shfl_xor_sync(kFull, (unsigned long long)acc, o);
+                    cnt += __shfl_xor_sync(kFull, cnt, o);
+                }
+                if (lane == 0) {
+                    s_acc[j] = acc;
+                    s_cnt[j] = cnt;
                 }
             }
             __syncthreads();
@@ -255,8 +224,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
 
         // Hash each vertex's key.
         if (tid >= jlo && tid < jhi && s_state[tid] == kPending) {
-            const int64_t v = v0 + tid;
-            const int32_t own = p.prev[v];
+            const int32_t own = p.prev[s_vid[tid]];
             const uint64_t h = vertex_hash(own, s_cnt[tid], s_acc[tid], p.hash_mode);
             s_pos[tid] = h & p.mask;
             s_hi[tid] = table_hi(h, p.epoch);
@@ -270,12 +238,17 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
             if (tid >= jlo && tid < jhi && s_state[tid] == kPending) {
                 uint64_t pos = s_pos[tid];
                 uint32_t rep = 0;
-                const int r = probe_table(p, &pos, s_hi[tid], (uint32_t)(v0 + tid), &rep);
+                const int r = probe_table(p, &pos, s_hi[tid], (uint32_t)s_vid[tid], &rep);
                 s_pos[tid] = pos;
                 if (r == 0) {
                     s_state[tid] = kDone;
                 } else if (r == 1) {
-                    const int q = atomicAdd(&s_qn, 1);
+                    const unsigned b = __activemask();
+                    const int leader = __ffs(b) - 1;
+                    int q0 = 0;
+                    if (lane == leader) q0 = atomicAdd(&s_qn, __popc(b));
+                    q0 = __shfl_sync(b, q0, leader);
+                    const int q = q0 + __popc(b & ((1u << lane) - 1u));
                     s_qj[q] = (uint16_t)tid;
                     s_qr[q] = rep;
                 } else {
@@ -291,14 +264,14 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
                 break;
             }
             // Compare: one warp per queued vertex.  The representative r is a
-            // non-hub vertex (hubs enter the table after this kernel), so its
-            // pairs are re-derived from the CSR and looked up in the shared set
-            // of our vertex; every distinct pair of ours must be hit once.
+            // small or medium vertex (hubs enter the table after this kernel), so
+            // its pairs are re-derived from the CSR and looked up in the shared
+            // set of our vertex; every distinct pair of ours must be hit once.
             for (int q = warp; q < qn; q += kTileThreads / 32) {
                 const int j = s_qj[q];
                 const uint32_t r = s_qr[q];
                 bool ok = (__ldg(p.prev + r) == s_own[j]);
-                if (!kLevel0 && ok) {
+                if (ok) {
                     const int64_t rb = p.row[r], re = p.row[r + 1];
                     int nf = 0;
                     for (int64_t e0 = rb; e0 < re; e0 += 32) {
@@ -314,7 +287,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
                                 const uint32_t cur = s_set[slot];
                                 if (cur == 0u) break;
                                 const int idx = (int)(cur & 0xffffu) - 1;
-                                if (s_pair[idx] == pr && s_seg[idx] == (uint16_t)j) {
+                                if (s_pair[idx] == pr && (s_seg[idx] & 0x7fffu) == (uint32_t)j) {
                                     const uint32_t old = atomicMax(&s_set[slot], (stamp << 16) | (cur & 0xffffu));
                                     if ((old >> 16) < stamp) ++nf;
                                     found = true;
@@ -336,7 +309,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
             if (tid < qn) {
                 const int j = s_qj[tid];
                 if (s_qres[tid]) {
-                    join_slot(p, s_pos[j], s_hi[j], (uint32_t)(v0 + j));
+                    join_slot(p, s_pos[j], s_hi[j], (uint32_t)s_vid[j]);
                     s_state[j] = kDone;
                 } else {
                     s_pos[j] = (s_pos[j] + 1) & p.mask;
@@ -365,8 +338,7 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     const int tid = threadIdx.x;
     const int64_t c = blockIdx.x;
     if (tid == 0) {
-        int lo = 0, hi = p.n_hubs;  // largest h with chunk_off[h] <= c
-        while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (p.hub_chunk_off[mid] <= c) lo = mid; else hi = mid; }
+        const int lo = p.chunk_hub[c];
         s_h = lo;
         const int32_t v = p.hub_v[lo];
         const int64_t rb = p.row[v], re = p.row[v + 1];
@@ -406,23 +378,33 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     }
     __syncthreads();
 
-    // chunk-local distinct pairs
-    for (int le = tid; le < E; le += kTileThreads) {
-        const uint64_t pr = s_pair[le];
-        uint32_t slot = set_slot(pr, 0u) & (kSetCap - 1);
-        while (true) {
-            uint32_t cur = s_set[slot];
-            if (cur == 0u) {
-                const uint32_t old = atomicCAS(&s_set[slot], 0u, (uint32_t)(le + 1));
-                if (old == 0u) {
-                    s_new[atomicAdd(&s_nuniq, 1)] = pr;
-                    break;
+    // chunk-local distinct pairs, compacted into s_new with one shared atomic per warp
+    for (int base = 0; base < E; base += kTileThreads) {
+        const int le = base + tid;
+        bool isu = false;
+        uint64_t pr = 0;
+        if (le < E) {
+            pr = s_pair[le];
+            uint32_t slot = set_slot(pr, 0u) & (kSetCap - 1);
+            while (true) {
+                uint32_t cur = s_set[slot];
+                if (cur == 0u) {
+                    const uint32_t old = atomicCAS(&s_set[slot], 0u, (uint32_t)(le + 1));
+                    if (old == 0u) {
+                        isu = true;
+                        break;
+                    }
+                    cur = old;
                 }
-                cur = old;
+                if (s_pair[(int)cur - 1] == pr) break;
+                slot = (slot + 1) & (kSetCap - 1);
             }
-            if (s_pair[(int)cur - 1] == pr) break;
-            slot = (slot + 1) & (kSetCap - 1);
         }
+        const unsigned b = __ballot_sync(kFull, isu);
+        int wbase = 0;
+        if ((tid & 31) == 0 && b) wbase = atomicAdd(&s_nuniq, __popc(b));
+        wbase = __shfl_sync(kFull, wbase, 0);
+        if (isu) s_new[wbase + __popc(b & ((1u << (tid & 31)) - 1u))] = pr;
     }
     __syncthreads();
 
@@ -431,16 +413,33 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     uint64_t* gset = p.hub_sets + p.hub_set_off[h];
     const uint64_t gmask = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]) - 1;
     uint64_t lacc = 0;
-    for (int i = tid; i < nu; i += kTileThreads) {
-        const uint64_t pr = s_new[i];
-        uint64_t slot = (pair_mix(pr) >> 17) & gmask;
+    // Up to kHubChunk / kTileThreads pairs per thread: issue the first probe of
+    // every pair before waiting on any, then finish the rare collisions.
+    constexpr int kPer = kHubChunk / kTileThreads;
+    uint64_t prs[kPer], slots[kPer], olds[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = tid + u * kTileThreads;
+        if (i < nu) {
+            prs[u] = s_new[i];
+            slots[u] = (pair_mix(prs[u]) >> 17) & gmask;
+            olds[u] = atomicCAS(reinterpret_cast<unsigned long long*>(&gset[slots[u]]),
+                                (unsigned long long)kEmptyPair, (unsigned long long)prs[u]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int i = tid + u * kTileThreads;
+        if (i >= nu) continue;
+        const uint64_t pr = prs[u];
+        uint64_t slot = slots[u], old = olds[u];
         uint8_t isnew = 0;
         for (uint64_t t = 0; t <= gmask; ++t) {
-            const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(&gset[slot]),
-                                           (unsigned long long)kEmptyPair, (unsigned long long)pr);
             if (old == kEmptyPair) { isnew = 1; break; }
             if (old == pr) break;
             slot = (slot + 1) & gmask;
+            old = atomicCAS(reinterpret_cast<unsigned long long*>(&gset[slot]), (unsigned long long)kEmptyPair,
+                            (unsigned long long)pr);
         }
         s_isnew[i] = isnew;
         if (isnew) lacc += pair_mix(pr);
@@ -450,9 +449,16 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(kFull, lacc, o);
     if ((tid & 31) == 0 && lacc) atomicAdd(reinterpret_cast<unsigned long long*>(&s_accsum), (unsigned long long)lacc);
     __syncthreads();
-    // compact the new pairs
-    for (int i = tid; i < nu; i += kTileThreads)
-        if (s_isnew[i]) s_pair[atomicAdd(&s_nnew, 1)] = s_new[i];
+    // compact the new pairs (one shared atomic per warp)
+    for (int base = 0; base < nu; base += kTileThreads) {
+        const int i = base + tid;
+        const bool keep = i < nu && s_isnew[i];
+        const unsigned b = __ballot_sync(kFull, keep);
+        int wbase = 0;
+        if ((tid & 31) == 0 && b) wbase = atomicAdd(&s_nnew, __popc(b));
+        wbase = __shfl_sync(kFull, wbase, 0);
+        if (keep) s_pair[wbase + __popc(b & ((1u << (tid & 31)) - 1u))] = s_new[i];
+    }
     __syncthreads();
     const int nnew = s_nnew;
     if (tid == 0) {
@@ -692,7 +698,11 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
         const uint32_t bw = p.bitmap[v >> 5];
         uint32_t mn = (uint32_t)v;
         if (!((bw >> (v & 31)) & 1u)) {
-            mn = (uint32_t)(p.table[(uint64_t)(uint32_t)p.slot_of[v] & p.mask] & 0xffffffffu);
+            const uint32_t sl = (uint32_t)p.slot_of[v];
+            if (sl & 0x80000000u)
+                mn = (uint32_t)p.emin[(sl & 0x7fffffffu) % (uint32_t)p.n];
+            else
+                mn = (uint32_t)(p.table[(uint64_t)sl & p.mask] & 0xffffffffu);
             if ((int64_t)mn >= p.n) mn = (uint32_t)v;  // only after a reported device error
         }
         const uint32_t mw = p.bitmap[mn >> 5];
@@ -722,13 +732,10 @@ void launch_clear_round(const RoundParams& p, cudaStream_t s) {
     }
 }
 
-void launch_tile_round(const RoundParams& p, bool level0, cudaStream_t s) {
-    if (p.n <= 0) return;
-    const int64_t blocks = (p.n + kTileVerts - 1) / kTileVerts;
-    if (level0)
-        tile_round_kernel<true><<<(unsigned)blocks, kTileThreads, 0, s>>>(p);
-    else
-        tile_round_kernel<false><<<(unsigned)blocks, kTileThreads, 0, s>>>(p);
+void launch_tile_round(const RoundParams& p, cudaStream_t s) {
+    if (p.n_med <= 0) return;
+    const int64_t blocks = (p.n_med + kTileVerts - 1) / kTileVerts;
+    tile_round_kernel<<<(unsigned)blocks, kTileThreads, 0, s>>>(p);
 }
 
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s) {

@@ -90,6 +90,26 @@ __global__ void find_hubs_kernel(int64_t n, const int64_t* row, int32_t thr, int
     }
 }
 
+__global__ void classify_kernel(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out,
+                                unsigned long long* n_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        bool take = false;
+        if (v < n) {
+            const int64_t d = row[v + 1] - row[v];
+            take = d > lo && d <= hi;
+        }
+        const unsigned b = __ballot_sync(kFull, take);
+        if (!b) continue;
+        unsigned long long pos = 0;
+        if (lane == 0) pos = atomicAdd(n_out, (unsigned long long)__popc(b));
+        pos = __shfl_sync(kFull, pos, 0);
+        if (take) out[pos + __popc(b & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+}
+
 // ---- int64 exclusive scan (reduce, scan of block sums, down-sweep)
 constexpr int kT = 1024;
 constexpr int kItems = 4;
@@ -204,6 +224,13 @@ void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v
                       cudaStream_t s) {
     if (n <= 0) return;
     find_hubs_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, row, thr, out_v, out_deg, n_out);
+}
+
+void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,
+                     cudaStream_t s) {
+    if (n <= 0) return;
+    classify_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, row, lo, hi, out,
+                                                     reinterpret_cast<unsigned long long*>(n_out));
 }
 
 void launch_copy_rows(int32_t* levels, int64_t n, int src, int first, int last, cudaStream_t s) {
