@@ -197,6 +197,37 @@ kb_status kb_refine_batch(kb_context* ctx, const kb_graph* union_graph,
 kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt, int rounds,
                       float* best_load_factor, int32_t* best_hub_threshold, float* best_ms);
 
+/* ---- One refinement round without device allocation -----------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * must not allocate device memory, themselves or through the library: an
+ * application that reserves all device memory in its own pool at start-up, or
+ * a latency-critical thread for which the device-wide synchronisation that
+ * cudaMalloc / cudaFree may cause is not acceptable.  It needs no context.
+ *
+ * Computes level i from level i-1 (one round of the refinement, out-edges):
+ *   stream   cudaStream_t to run on (NULL = legacy default stream); the call
+ *            synchronises it before returning
+ *   g        DEVICE CSR as for kb_refine, with n <= KB_NOALLOC_MAX_VERTICES and
+ *            no vertex with more than hub_threshold (default 2048) edges
+ *   opt      direction must be KB_DIR_OUT; use_edge_labels, hash_mode,
+ *            hub_threshold and validate are honoured
+ *   prev     DEVICE int32[n], canonical ids of level i-1, each in [0, n)
+ *   out      DEVICE int32[n], receives the canonical ids of level i
+ *   count    HOST, receives the number of blocks of level i
+ * Its scratch is one static device array of about 33 MB inside the library,
+ * which every device that loads the library keeps until the process exits.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Every call shares the array, which
+ * keeps the previous call's contents (each call resets what it uses), so calls
+ * that overlap on the GPU -- from several streams or threads -- race; the
+ * caller must serialise them.
+ * Errors: KB_ERR_INVALID_ARG for n above the limit, another direction, a
+ * vertex above the hub threshold, an id of prev outside [0, n) or (with
+ * validate) malformed CSR; KB_ERR_CUDA when a runtime call fails. */
+#define KB_NOALLOC_MAX_VERTICES 1048576
+kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, const kb_options* opt,
+                                  const int32_t* prev, int32_t* out, int64_t* count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ from ._capi import KbError
 
 __all__ = [
     "DIR_OUT", "DIR_IN", "DIR_BOTH", "Options", "DeviceGraph", "Context", "Result", "KbError", "refine",
-    "library_path",
+    "refine_round_noalloc", "library_path",
 ]
 
 
@@ -282,6 +282,28 @@ class Context:
         self._check(self._lib.kb_get_timing(self._h, _np_ptr(rm), 4096, ctypes.byref(nr), _np_ptr(km), _np_ptr(kl)))
         fam = {name: (float(km[i]), int(kl[i])) for i, name in enumerate(_capi.KERNEL_NAMES)}
         return rm[: nr.value].tolist(), fam
+
+
+def refine_round_noalloc(graph: DeviceGraph, prev, out, options: Options = None, stream=None) -> int:
+    """One refinement round (level i from level i-1, out-edges) through
+    ``kb_refine_round_noalloc``: the library allocates no device memory for
+    it, using a fixed static scratch array instead (n <= 2^20, no vertex above
+    the hub threshold).  ``prev`` and ``out`` are int32 CUDA tensors of length
+    n.  Returns the number of blocks of the new level."""
+    import torch
+
+    options = options or Options()
+    if stream is None:
+        stream = torch.cuda.current_stream(graph.device)
+    lib = _capi.load()
+    cnt = ctypes.c_int64(0)
+    g, o = graph.to_c(), options.to_c()
+    st = lib.kb_refine_round_noalloc(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(g), ctypes.byref(o),
+                                     ctypes.c_void_p(prev.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.byref(cnt))
+    if st != _capi.KB_OK:
+        raise KbError(st, "kb_refine_round_noalloc")
+    return int(cnt.value)
 
 
 _default = {}

@@ -73,7 +73,10 @@ SIGNATURES = [
     ("kb_get_timing", _I, [_P, _P, _I, _P, _P, _P]),
     ("kb_refine_batch", _I, [_P, ctypes.POINTER(KbGraph), _P, _I64, _P, ctypes.POINTER(KbOptions), _P, _P, _P]),
     ("kb_autotune", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
+    ("kb_refine_round_noalloc", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _P, _P,
+                                     ctypes.POINTER(ctypes.c_int64)]),
 ]
+NOALLOC_MAX_VERTICES = 1 << 20
 
 _lib = None
 _lock = threading.Lock()
