@@ -476,3 +476,41 @@ def serve_graph(m: int, seed: int) -> Graph:
     64 vertex labels Zipf(1.5), 32 edge labels Zipf(1.2)."""
     n = max(1, m // 5)
     return chung_lu(n, m, 2.1, 2.1, max(1.0, m / 10), max(1.0, m / 10), 64, 1.5, 32, 1.2, seed)
+
+
+def batch_union_torch(G: int = 4096, seed: int = 3, median_m: float = 5e4, sigma: float = 1.25,
+                      m_lo: int = 1000, m_hi: int = 2_000_000, k_max: int = 10, n_vlabels: int = 16,
+                      n_elabels: int = 8, device="cuda"):
+    """The batching workload drawn with torch on ``device``: G Erdos-Renyi
+    graphs with lognormal edge counts (clipped to [m_lo, m_hi]), n = m/5,
+    uniform labels and k uniform on 1..k_max, laid out as one disjoint union.
+    Returns (union dict of tensors, vertex offsets int64[G+1] numpy, ks int32[G]
+    numpy)."""
+    import torch
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ms = np.clip(np.exp(rng.normal(np.log(median_m), sigma, size=G)), m_lo, m_hi).astype(np.int64)
+    ns = np.maximum(1, ms // 5)
+    ks = rng.integers(1, k_max + 1, size=G).astype(np.int32)
+    voff = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(ns, out=voff[1:])
+    eoff = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum(ms, out=eoff[1:])
+    n, m = int(voff[-1]), int(eoff[-1])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    gid = torch.repeat_interleave(torch.arange(G, device=device), torch.from_numpy(ms).to(device))
+    base = torch.from_numpy(voff[:-1]).to(device)[gid]
+    size = torch.from_numpy(ns).to(device)[gid]
+    src = base + (torch.rand(m, generator=gen, device=device, dtype=torch.float64) * size).long().clamp_(max=size - 1)
+    dst = base + (torch.rand(m, generator=gen, device=device, dtype=torch.float64) * size).long().clamp_(max=size - 1)
+    del gid, base, size
+    order = torch.argsort(src, stable=True)
+    col = dst[order].to(torch.int32)
+    deg = torch.bincount(src, minlength=n)
+    del src, dst, order
+    row = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(deg, 0, out=row[1:])
+    el = torch.randint(0, max(1, n_elabels), (m,), generator=gen, device=device, dtype=torch.int32)
+    vl = torch.randint(0, max(1, n_vlabels), (n,), generator=gen, device=device, dtype=torch.int32)
+    return ({"n": n, "m": m, "row_offsets": row, "col": col, "elabel": el, "vlabel": vl}, voff, ks)

@@ -86,7 +86,9 @@ typedef struct {
  *   hash_mode          0: full 64-bit signature hash.  1: weak hash of the previous
  *                      block only, which forces collisions (tests the full
  *                      signature compare); results are identical in both modes
- *   validate           1: check offsets and ids on the device before refining */
+ *   validate           1: check offsets and ids on the device before refining
+ *   small_task_vertices vertices each warp of the small-vertex kernel takes per task
+ *                      (tile size); 0 -> default 256, else 32..65536 */
 typedef struct {
     int32_t direction;
     int32_t use_vertex_labels;
@@ -96,7 +98,8 @@ typedef struct {
     int32_t hub_threshold;
     int32_t hash_mode;
     int32_t validate;
-    int32_t reserved[8];
+    int32_t small_task_vertices;
+    int32_t reserved[7];
 } kb_options;
 
 typedef struct kb_context kb_context;

@@ -44,6 +44,7 @@ class Options:
     hub_threshold: int = 0
     hash_mode: int = 0
     validate: bool = True
+    small_task_vertices: int = 0
 
     @classmethod
     def schaetzle(cls, **kw) -> "Options":
@@ -65,6 +66,7 @@ class Options:
         o.hub_threshold = int(self.hub_threshold)
         o.hash_mode = int(self.hash_mode)
         o.validate = int(bool(self.validate))
+        o.small_task_vertices = int(self.small_task_vertices)
         return o
 
 

@@ -46,7 +46,8 @@ class KbOptions(ctypes.Structure):
         ("hub_threshold", ctypes.c_int32),
         ("hash_mode", ctypes.c_int32),
         ("validate", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("small_task_vertices", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
     ]
 
 

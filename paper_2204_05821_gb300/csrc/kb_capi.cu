@@ -38,12 +38,19 @@ struct kb_context {
     // autotuned defaults
     float tuned_load_factor = 0.f;
     int32_t tuned_hub_threshold = 0;
+    int32_t tuned_warp_verts = 0;
+    // batched refinement
+    void* batch_ws = nullptr;
+    size_t batch_ws_bytes = 0;
+    void* tune_buf = nullptr;
+    size_t tune_buf_bytes = 0;
+    cudaStream_t cap_stream = nullptr;  // non-default stream used only to capture CUDA graphs
     // timing
     bool timing = false;
     std::vector<float> round_ms;
     float kernel_ms[KB_KERNEL_COUNT] = {};
     int64_t kernel_launches[KB_KERNEL_COUNT] = {};
-    cudaEvent_t ev[2 * 10] = {};
+    cudaEvent_t ev[2 * 10 + 2] = {};  // pairs for the round timer; the last two time whole calls
 };
 
 namespace {
@@ -156,6 +163,8 @@ kb_status check_graph(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     if (opt->hub_threshold < 0 || opt->hub_threshold > kb::kMaxHubThreshold)
         return fail(ctx, KB_ERR_INVALID_ARG, "hub_threshold must be in [0, %d]", kb::kMaxHubThreshold);
     if (opt->hash_mode < 0 || opt->hash_mode > 1) return fail(ctx, KB_ERR_INVALID_ARG, "bad hash_mode");
+    if (opt->small_task_vertices != 0 && (opt->small_task_vertices < 32 || opt->small_task_vertices > 65536))
+        return fail(ctx, KB_ERR_INVALID_ARG, "small_task_vertices must be 0 or in [32, 65536]");
     if (opt->direction == KB_DIR_BOTH && g->m > (int64_t)1 << 62)
         return fail(ctx, KB_ERR_INVALID_ARG, "too many edges");
     return KB_OK;
@@ -337,6 +346,192 @@ struct Timer {
     }
 };
 
+// Everything one refine call needs on the device: the plan, the bound round
+// parameters and the table epoch.
+struct Prepared {
+    Plan P;
+    kb::RoundParams p{};
+    uint32_t* prefix = nullptr;
+    uint32_t* scan_tmp = nullptr;
+    int64_t total_chunks = 0;
+    size_t set_bytes = 0;
+    uint32_t epoch = 0;
+};
+
+// Validate, plan, acquire the workspace, bind the round parameters, list the
+// medium vertices and reset the per-call state (block table, empty-signature
+// minima).  Synchronises.
+kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Prepared& R) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = g->n;
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    if (opt->validate) {
+        kb::launch_validate(n, g->m, g->row_offsets, g->col_indices, ctx->d_ctr, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_TRY(read_counters(ctx));
+        KB_TRY(device_error(ctx));
+    }
+    // The processed CSR sits at the head of the workspace, so its size is known
+    // before the hub layout.
+    Plan& P = R.P;
+    Plan probe;
+    probe.n = n;
+    probe.m = g->m;
+    probe.dir = opt->direction;
+    probe.m_proc = probe.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
+    probe.labels = opt->use_edge_labels && g->edge_labels != nullptr;
+    layout_csr(probe);
+    char* base = nullptr;
+    if (probe.csr_bytes) {
+        // The hub layout is not known yet: reserve the CSR part first.  A
+        // library-owned workspace keeps its contents when it does not grow.
+        if (ctx->user_ws) {
+            KB_TRY(acquire_workspace(ctx, probe.csr_bytes, &base));
+        } else {
+            KB_TRY(ensure_buffer(ctx, &ctx->plan_tmp, &ctx->plan_tmp_bytes, probe.csr_bytes));
+            base = reinterpret_cast<char*>(ctx->plan_tmp);
+        }
+    }
+    KB_TRY(make_plan(ctx, g, opt, P, &base, false));
+    char* ws = nullptr;
+    if (ctx->user_ws) {
+        KB_TRY(acquire_workspace(ctx, P.total, &ws));
+    } else {
+        // round buffers live in the owned workspace; the CSR stays in plan_tmp
+        const size_t csr_bytes = P.csr_bytes;
+        P.csr_bytes = 0;
+        layout_round(P);
+        P.csr_bytes = csr_bytes;
+        KB_TRY(ensure_buffer(ctx, &ctx->own_ws, &ctx->own_ws_bytes, std::max<size_t>(P.total, 256)));
+        ws = reinterpret_cast<char*>(ctx->own_ws);
+    }
+    char* csr = base;
+    kb::RoundParams& p = R.p;
+    p = kb::RoundParams{};
+    p.n = n;
+    if (needs_in_csr(P.dir)) {
+        p.row = reinterpret_cast<const int64_t*>(csr + P.o_rowp);
+        p.col = reinterpret_cast<const int32_t*>(csr + P.o_colp);
+        p.lab = P.labels ? reinterpret_cast<const int32_t*>(csr + P.o_labp) : nullptr;
+    } else {
+        p.row = g->row_offsets;
+        p.col = g->col_indices;
+        p.lab = P.labels ? g->edge_labels : nullptr;
+    }
+    p.hub_threshold = P.thr;
+    p.small_max = std::min(kb::kSmallDegree, P.thr);
+    p.warp_verts = opt->small_task_vertices ? opt->small_task_vertices : ctx->tuned_warp_verts;
+    p.hash_mode = opt->hash_mode;
+    p.table = reinterpret_cast<uint64_t*>(ws + P.o_table);
+    p.mask = P.cap - 1;
+    p.slot_of = reinterpret_cast<int32_t*>(ws + P.o_slot);
+    p.emin = reinterpret_cast<uint64_t*>(ws + P.o_emin);
+    KB_CUDA(ctx, cudaMemsetAsync(p.emin, 0xff, sizeof(uint64_t) * (size_t)n, s));
+    p.bitmap = reinterpret_cast<uint32_t*>(ws + P.o_bitmap);
+    p.ctr = ctx->d_ctr;
+    const size_t H = P.hub_v.size();
+    p.n_hubs = (int32_t)H;
+    p.hub_v = reinterpret_cast<const int32_t*>(ws + P.o_hubv);
+    p.hub_chunk_off = reinterpret_cast<const int64_t*>(ws + P.o_chunk);
+    p.hub_set_off = reinterpret_cast<const int64_t*>(ws + P.o_setoff);
+    p.hub_list_off = reinterpret_cast<const int64_t*>(ws + P.o_listoff);
+    p.chunk_hub = reinterpret_cast<const int32_t*>(ws + P.o_chunkhub);
+    p.hub_sets = reinterpret_cast<uint64_t*>(ws + P.o_sets);
+    p.hub_lists = reinterpret_cast<uint64_t*>(ws + P.o_lists);
+    p.hub_acc = reinterpret_cast<uint64_t*>(ws + P.o_acc);
+    p.hub_cnt = reinterpret_cast<uint32_t*>(ws + P.o_cnt);
+    R.prefix = reinterpret_cast<uint32_t*>(ws + P.o_prefix);
+    R.scan_tmp = reinterpret_cast<uint32_t*>(ws + P.o_scan);
+    if (H) {
+        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_hubv, P.hub_v.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice, s));
+        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunk, P.chunk_off.data(), sizeof(int64_t) * (H + 1),
+                                     cudaMemcpyHostToDevice, s));
+        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_setoff, P.set_off.data(), sizeof(int64_t) * (H + 1),
+                                     cudaMemcpyHostToDevice, s));
+        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_listoff, P.list_off.data(), sizeof(int64_t) * (H + 1),
+                                     cudaMemcpyHostToDevice, s));
+        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunkhub, P.chunk_hub.data(), sizeof(int32_t) * P.chunk_hub.size(),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    // medium vertices, once per call
+    int32_t* med = reinterpret_cast<int32_t*>(ws + P.o_med);
+    p.med_v = med;
+    p.n_med = 0;
+    if (g->m > 0) {
+        KB_CUDA(ctx, cudaMemsetAsync(ctx->d_med_n, 0, sizeof(int64_t), s));
+        kb::launch_classify(n, p.row, p.small_max, P.thr, med, ctx->d_med_n, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_CUDA(ctx, cudaMemcpyAsync(ctx->h_med_n, ctx->d_med_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        KB_CUDA(ctx, cudaStreamSynchronize(s));
+        p.n_med = *ctx->h_med_n;
+    }
+    R.total_chunks = H ? P.chunk_off[H] : 0;
+    R.set_bytes = sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0);
+    KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
+    R.epoch = 0;
+    return KB_OK;
+}
+
+// Advance the table epoch (entries of other epochs read as empty); the table
+// is cleared once every 255 rounds.
+kb_status next_epoch(kb_context* ctx, Prepared& R, cudaStream_t s) {
+    if (R.epoch == 255) {
+        KB_CUDA(ctx, cudaMemsetAsync(R.p.table, 0, sizeof(uint64_t) * (size_t)R.P.cap, s));
+        R.epoch = 0;
+    }
+    R.p.epoch = ++R.epoch;
+    return KB_OK;
+}
+
+// Starting level: canonical renumbering of `key` (labels or a given
+// partition; all-zero partition when key is NULL in a batched run).
+kb_status launch_level0(kb_context* ctx, Prepared& R, const int32_t* key, int32_t* out, cudaStream_t s) {
+    KB_TRY(next_epoch(ctx, R, s));
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    KB_CUDA(ctx, cudaMemsetAsync(R.p.bitmap, 0, sizeof(uint32_t) * (size_t)((R.p.n >> 5) + 1), s));
+    R.p.prev = key;
+    kb::launch_small_round(R.p, true, s);
+    kb::launch_renumber(R.p, R.prefix, R.scan_tmp, out, s);
+    KB_CUDA(ctx, cudaGetLastError());
+    return KB_OK;
+}
+
+// One refinement round up to (not including) the renumbering.
+kb_status launch_round_body(kb_context* ctx, Prepared& R, cudaStream_t s, Timer* T) {
+    kb::RoundParams& p = R.p;
+    if (T) T->begin(KB_KERNEL_OTHER);
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    kb::launch_clear_round(p, s);
+    if (R.set_bytes) KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, R.set_bytes, s));
+    if (T) T->end();
+    if (T) T->begin(KB_KERNEL_SMALL);
+    kb::launch_small_round(p, false, s);
+    if (T) T->end();
+    if (p.n_med) {
+        if (T) T->begin(KB_KERNEL_MEDIUM);
+        kb::launch_tile_round(p, s);
+        if (T) T->end();
+    }
+    if (p.n_hubs) {
+        if (T) T->begin(KB_KERNEL_HUB_CHUNK);
+        kb::launch_hub_chunk(p, R.total_chunks, s);
+        if (T) T->end();
+        if (T) T->begin(KB_KERNEL_HUB_FINAL);
+        kb::launch_hub_final(p, s);
+        if (T) T->end();
+    }
+    KB_CUDA(ctx, cudaGetLastError());
+    return KB_OK;
+}
+
+void reset_timing(kb_context* ctx) {
+    ctx->round_ms.clear();
+    for (int f = 0; f < KB_KERNEL_COUNT; ++f) {
+        ctx->kernel_ms[f] = 0.f;
+        ctx->kernel_launches[f] = 0;
+    }
+}
+
 // The refinement driver shared by kb_refine and kb_refine_from.
 kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
                       int k, int32_t* levels, int64_t* counts, int* levels_computed) {
@@ -345,11 +540,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
     if (g->n > 0 && !levels) return fail(ctx, KB_ERR_INVALID_ARG, "levels is NULL");
     KB_CUDA(ctx, cudaSetDevice(ctx->device));
-    ctx->round_ms.clear();
-    for (int f = 0; f < KB_KERNEL_COUNT; ++f) {
-        ctx->kernel_ms[f] = 0.f;
-        ctx->kernel_launches[f] = 0;
-    }
+    reset_timing(ctx);
     const int64_t n = g->n;
     if (levels_computed) *levels_computed = i_start;
     if (n == 0) {
@@ -357,202 +548,197 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         return KB_OK;
     }
     cudaStream_t s = ctx->stream;
+    Prepared R;
+    KB_TRY(prepare(ctx, g, opt, R));
+    kb::RoundParams& p = R.p;
 
-    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
-    if (opt->validate) {
-        kb::launch_validate(n, g->m, g->row_offsets, g->col_indices, ctx->d_ctr, s);
-        KB_CUDA(ctx, cudaGetLastError());
+    // ---- the starting level
+    int32_t* row0 = levels + (size_t)i_start * (size_t)n;
+    const int32_t* init_key = start ? start : (opt->use_vertex_labels ? g->vertex_labels : nullptr);
+    if (init_key) {
+        KB_TRY(launch_level0(ctx, R, init_key, row0, s));
         KB_TRY(read_counters(ctx));
         KB_TRY(device_error(ctx));
+        counts[i_start] = ctx->h_ctr->count;
+    } else {
+        kb::launch_fill_i32(row0, n, 0, s);
+        counts[i_start] = 1;
     }
 
-    // Plan: the processed CSR sits at the head of the workspace, so its size
-    // is known before the hub layout.
-    Plan P;
-    {
-        Plan probe;
-        probe.n = n;
-        probe.m = g->m;
-        probe.dir = opt->direction;
-        probe.m_proc = probe.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
-        probe.labels = opt->use_edge_labels && g->edge_labels != nullptr;
-        layout_csr(probe);
-        char* base = nullptr;
-        if (probe.csr_bytes) {
-            // The hub layout is not known yet: reserve the CSR part first.  A
-            // library-owned workspace keeps its contents when it does not grow.
-            if (ctx->user_ws) {
-                KB_TRY(acquire_workspace(ctx, probe.csr_bytes, &base));
-            } else {
-                KB_TRY(ensure_buffer(ctx, &ctx->plan_tmp, &ctx->plan_tmp_bytes, probe.csr_bytes));
-                base = reinterpret_cast<char*>(ctx->plan_tmp);
-            }
-        }
-        KB_TRY(make_plan(ctx, g, opt, P, &base, false));
-        char* ws = nullptr;
-        if (ctx->user_ws) {
-            KB_TRY(acquire_workspace(ctx, P.total, &ws));
-        } else {
-            // round buffers live in the owned workspace; the CSR stays in plan_tmp
-            Plan R = P;
-            R.csr_bytes = 0;
-            layout_round(R);
-            KB_TRY(ensure_buffer(ctx, &ctx->own_ws, &ctx->own_ws_bytes, std::max<size_t>(R.total, 256)));
-            P.o_med = R.o_med;
-            P.o_emin = R.o_emin;
-            P.o_slot = R.o_slot;
-            P.o_table = R.o_table;
-            P.o_bitmap = R.o_bitmap;
-            P.o_prefix = R.o_prefix;
-            P.o_scan = R.o_scan;
-            P.o_hubv = R.o_hubv;
-            P.o_chunk = R.o_chunk;
-            P.o_setoff = R.o_setoff;
-            P.o_listoff = R.o_listoff;
-            P.o_chunkhub = R.o_chunkhub;
-            P.o_acc = R.o_acc;
-            P.o_cnt = R.o_cnt;
-            P.o_sets = R.o_sets;
-            P.o_lists = R.o_lists;
-            ws = reinterpret_cast<char*>(ctx->own_ws);
-        }
-        char* csr = base;
-        // assemble round parameters
-        kb::RoundParams p{};
-        p.n = n;
-        if (needs_in_csr(P.dir)) {
-            p.row = reinterpret_cast<const int64_t*>(csr + P.o_rowp);
-            p.col = reinterpret_cast<const int32_t*>(csr + P.o_colp);
-            p.lab = P.labels ? reinterpret_cast<const int32_t*>(csr + P.o_labp) : nullptr;
-        } else {
-            p.row = g->row_offsets;
-            p.col = g->col_indices;
-            p.lab = P.labels ? g->edge_labels : nullptr;
-        }
-        p.hub_threshold = P.thr;
-        p.small_max = std::min(kb::kSmallDegree, P.thr);
-        p.hash_mode = opt->hash_mode;
-        p.table = reinterpret_cast<uint64_t*>(ws + P.o_table);
-        p.mask = P.cap - 1;
-        p.slot_of = reinterpret_cast<int32_t*>(ws + P.o_slot);
-        p.emin = reinterpret_cast<uint64_t*>(ws + P.o_emin);
-        KB_CUDA(ctx, cudaMemsetAsync(p.emin, 0xff, sizeof(uint64_t) * (size_t)n, s));
-        p.bitmap = reinterpret_cast<uint32_t*>(ws + P.o_bitmap);
-        p.ctr = ctx->d_ctr;
-        const size_t H = P.hub_v.size();
-        p.n_hubs = (int32_t)H;
-        p.hub_v = reinterpret_cast<const int32_t*>(ws + P.o_hubv);
-        p.hub_chunk_off = reinterpret_cast<const int64_t*>(ws + P.o_chunk);
-        p.hub_set_off = reinterpret_cast<const int64_t*>(ws + P.o_setoff);
-        p.hub_list_off = reinterpret_cast<const int64_t*>(ws + P.o_listoff);
-        p.chunk_hub = reinterpret_cast<const int32_t*>(ws + P.o_chunkhub);
-        p.hub_sets = reinterpret_cast<uint64_t*>(ws + P.o_sets);
-        p.hub_lists = reinterpret_cast<uint64_t*>(ws + P.o_lists);
-        p.hub_acc = reinterpret_cast<uint64_t*>(ws + P.o_acc);
-        p.hub_cnt = reinterpret_cast<uint32_t*>(ws + P.o_cnt);
-        uint32_t* prefix = reinterpret_cast<uint32_t*>(ws + P.o_prefix);
-        uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(ws + P.o_scan);
-        if (H) {
-            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_hubv, P.hub_v.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice, s));
-            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunk, P.chunk_off.data(), sizeof(int64_t) * (H + 1),
-                                         cudaMemcpyHostToDevice, s));
-            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_setoff, P.set_off.data(), sizeof(int64_t) * (H + 1),
-                                         cudaMemcpyHostToDevice, s));
-            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_listoff, P.list_off.data(), sizeof(int64_t) * (H + 1),
-                                         cudaMemcpyHostToDevice, s));
-            KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunkhub, P.chunk_hub.data(), sizeof(int32_t) * P.chunk_hub.size(),
-                                         cudaMemcpyHostToDevice, s));
-        }
-        // medium vertices, once per call
-        int32_t* med = reinterpret_cast<int32_t*>(ws + P.o_med);
-        p.med_v = med;
-        p.n_med = 0;
-        if (g->m > 0) {
-            KB_CUDA(ctx, cudaMemsetAsync(ctx->d_med_n, 0, sizeof(int64_t), s));
-            kb::launch_classify(n, p.row, p.small_max, P.thr, med, ctx->d_med_n, s);
+    // ---- refinement rounds
+    for (int i = i_start + 1; i <= k; ++i) {
+        Timer T(ctx);
+        KB_TRY(next_epoch(ctx, R, s));
+        p.ehigh = 0xffffffffu - (uint32_t)(i - i_start);
+        p.prev = levels + (size_t)(i - 1) * (size_t)n;
+        int32_t* out = levels + (size_t)i * (size_t)n;
+        KB_TRY(launch_round_body(ctx, R, s, &T));
+        T.begin(KB_KERNEL_RENUMBER);
+        kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
+        T.end();
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_TRY(read_counters(ctx));
+        ctx->round_ms.push_back(T.collect());
+        KB_TRY(device_error(ctx));
+        counts[i] = ctx->h_ctr->count;
+        if (levels_computed) *levels_computed = i;
+        if (opt->early_stop && counts[i] == counts[i - 1]) {
+            if (i < k) kb::launch_copy_rows(levels, n, i, i + 1, k, s);
+            for (int j = i + 1; j <= k; ++j) counts[j] = counts[i];
             KB_CUDA(ctx, cudaGetLastError());
-            KB_CUDA(ctx, cudaMemcpyAsync(ctx->h_med_n, ctx->d_med_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-            KB_CUDA(ctx, cudaStreamSynchronize(s));
-            p.n_med = *ctx->h_med_n;
-        }
-        const int64_t total_chunks = H ? P.chunk_off[H] : 0;
-        const size_t set_bytes = sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0);
-        KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
-        uint32_t epoch = 0;
-        auto next_epoch = [&]() -> kb_status {
-            if (epoch == 255) {
-                KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
-                epoch = 0;
-            }
-            p.epoch = ++epoch;
-            return KB_OK;
-        };
-
-        // ---- the starting level
-        int32_t* row0 = levels + (size_t)i_start * (size_t)n;
-        const int32_t* init_key = start ? start : (opt->use_vertex_labels ? g->vertex_labels : nullptr);
-        if (init_key) {
-            KB_TRY(next_epoch());
-            KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
-            KB_CUDA(ctx, cudaMemsetAsync(p.bitmap, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
-            p.prev = init_key;
-            kb::launch_small_round(p, true, s);
-            kb::launch_renumber(p, prefix, scan_tmp, row0, s);
-            KB_CUDA(ctx, cudaGetLastError());
-            KB_TRY(read_counters(ctx));
-            KB_TRY(device_error(ctx));
-            counts[i_start] = ctx->h_ctr->count;
-        } else {
-            kb::launch_fill_i32(row0, n, 0, s);
-            counts[i_start] = 1;
-        }
-
-        // ---- refinement rounds
-        for (int i = i_start + 1; i <= k; ++i) {
-            Timer T(ctx);
-            KB_TRY(next_epoch());
-            p.ehigh = 0xffffffffu - (uint32_t)(i - i_start);
-            p.prev = levels + (size_t)(i - 1) * (size_t)n;
-            int32_t* out = levels + (size_t)i * (size_t)n;
-            T.begin(KB_KERNEL_OTHER);
-            KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
-            kb::launch_clear_round(p, s);
-            if (set_bytes) KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, set_bytes, s));
-            T.end();
-            T.begin(KB_KERNEL_SMALL);
-            kb::launch_small_round(p, false, s);
-            T.end();
-            if (p.n_med) {
-                T.begin(KB_KERNEL_MEDIUM);
-                kb::launch_tile_round(p, s);
-                T.end();
-            }
-            if (H) {
-                T.begin(KB_KERNEL_HUB_CHUNK);
-                kb::launch_hub_chunk(p, total_chunks, s);
-                T.end();
-                T.begin(KB_KERNEL_HUB_FINAL);
-                kb::launch_hub_final(p, s);
-                T.end();
-            }
-            T.begin(KB_KERNEL_RENUMBER);
-            kb::launch_renumber(p, prefix, scan_tmp, out, s);
-            T.end();
-            KB_CUDA(ctx, cudaGetLastError());
-            KB_TRY(read_counters(ctx));
-            ctx->round_ms.push_back(T.collect());
-            KB_TRY(device_error(ctx));
-            counts[i] = ctx->h_ctr->count;
-            if (levels_computed) *levels_computed = i;
-            if (opt->early_stop && counts[i] == counts[i - 1]) {
-                if (i < k) kb::launch_copy_rows(levels, n, i, i + 1, k, s);
-                for (int j = i + 1; j <= k; ++j) counts[j] = counts[i];
-                KB_CUDA(ctx, cudaGetLastError());
-                break;
-            }
+            break;
         }
     }
     KB_CUDA(ctx, cudaStreamSynchronize(s));
+    return KB_OK;
+}
+
+// Batched refinement of G graphs held as one disjoint union (see
+// kb_refine_batch in kbisim.h).  Block ids are union-global while the rounds
+// run: the own previous block is part of every key, so vertices of different
+// graphs never share a block, and level 0 hashes the graph id into the key.
+// Rounds 1..k_max are captured once into a CUDA graph; per-graph stopping is
+// decided on the device, so the loop needs no host synchronisation.
+kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, int64_t G, const int32_t* k_h,
+                     const kb_options* opt, int32_t* levels, int64_t* counts, int32_t* lc_out) {
+    if (!g || !opt) return fail(ctx, KB_ERR_INVALID_ARG, "graph and options must not be NULL");
+    if (G < 0 || G > (int64_t)1 << 30) return fail(ctx, KB_ERR_INVALID_ARG, "bad graph count");
+    if (G > 0 && (!voff_h || !k_h || !counts)) return fail(ctx, KB_ERR_INVALID_ARG, "NULL batch arrays");
+    int kmax = 0;
+    for (int64_t j = 0; j < G; ++j) {
+        if (k_h[j] < 0) return fail(ctx, KB_ERR_INVALID_ARG, "k of graph %lld is negative", (long long)j);
+        kmax = std::max(kmax, (int)k_h[j]);
+        if (voff_h[j + 1] < voff_h[j]) return fail(ctx, KB_ERR_INVALID_ARG, "graph_vertex_offsets not monotone");
+    }
+    if (G > 0 && (voff_h[0] != 0 || voff_h[G] != g->n))
+        return fail(ctx, KB_ERR_INVALID_ARG, "graph_vertex_offsets must run from 0 to n");
+    KB_TRY(check_graph(ctx, g, opt, kmax));
+    const int64_t n = g->n;
+    if (G == 0) return KB_OK;
+    for (int64_t j = 0; j < G * (kmax + 1); ++j) counts[j] = 0;
+    if (lc_out)
+        for (int64_t j = 0; j < G; ++j) lc_out[j] = 0;
+    if (n == 0) return KB_OK;
+    if (!levels) return fail(ctx, KB_ERR_INVALID_ARG, "levels is NULL");
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    reset_timing(ctx);
+    cudaStream_t s = ctx->stream;
+    Prepared R;
+    KB_TRY(prepare(ctx, g, opt, R));
+    kb::RoundParams& p = R.p;
+
+    // batch scratch
+    const int64_t nw = (n >> 5) + 1;
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += align_up(b); return o; };
+    const size_t o_vgraph = take(sizeof(int32_t) * (size_t)n);
+    const size_t o_voff = take(sizeof(int64_t) * (size_t)(G + 1));
+    const size_t o_k = take(sizeof(int32_t) * (size_t)G);
+    const size_t o_act = take((size_t)G);
+    const size_t o_early = take((size_t)G);
+    const size_t o_last = take(sizeof(int32_t) * (size_t)G);
+    const size_t o_sticky = take(sizeof(int32_t));
+    const size_t o_bases = take(sizeof(uint32_t) * (size_t)(G + 1) * (size_t)(kmax + 1));
+    const size_t o_bm2 = take(sizeof(uint32_t) * (size_t)nw);
+    KB_TRY(ensure_buffer(ctx, &ctx->batch_ws, &ctx->batch_ws_bytes, off));
+    char* b = reinterpret_cast<char*>(ctx->batch_ws);
+    int32_t* vgraph = reinterpret_cast<int32_t*>(b + o_vgraph);
+    int64_t* voff = reinterpret_cast<int64_t*>(b + o_voff);
+    int32_t* kd = reinterpret_cast<int32_t*>(b + o_k);
+    uint8_t* gact = reinterpret_cast<uint8_t*>(b + o_act);
+    uint8_t* early = reinterpret_cast<uint8_t*>(b + o_early);
+    int32_t* glast = reinterpret_cast<int32_t*>(b + o_last);
+    int32_t* sticky = reinterpret_cast<int32_t*>(b + o_sticky);
+    uint32_t* bases = reinterpret_cast<uint32_t*>(b + o_bases);
+    uint32_t* bm_a = p.bitmap;
+    uint32_t* bm_b = reinterpret_cast<uint32_t*>(b + o_bm2);
+    std::vector<uint8_t> act_h((size_t)G), early_h((size_t)G, (uint8_t)(opt->early_stop ? 1 : 0));
+    for (int64_t j = 0; j < G; ++j) act_h[(size_t)j] = k_h[j] > 0 ? 1 : 0;
+    KB_CUDA(ctx, cudaMemcpyAsync(voff, voff_h, sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, s));
+    KB_CUDA(ctx, cudaMemcpyAsync(kd, k_h, sizeof(int32_t) * (size_t)G, cudaMemcpyHostToDevice, s));
+    KB_CUDA(ctx, cudaMemcpyAsync(gact, act_h.data(), (size_t)G, cudaMemcpyHostToDevice, s));
+    KB_CUDA(ctx, cudaMemcpyAsync(early, early_h.data(), (size_t)G, cudaMemcpyHostToDevice, s));
+    KB_CUDA(ctx, cudaMemsetAsync(glast, 0, sizeof(int32_t) * (size_t)G, s));
+    KB_CUDA(ctx, cudaMemsetAsync(sticky, 0, sizeof(int32_t), s));
+    kb::launch_vertex_graph(voff, (int32_t)G, n, vgraph, s);
+    p.vgraph = vgraph;
+    p.voff = voff;
+    p.n_graphs = (int32_t)G;
+
+    // level 0 for every graph: key (graph, label) or (graph) without labels
+    p.gactive = nullptr;
+    p.gbase_cur = bases;
+    KB_TRY(launch_level0(ctx, R, opt->use_vertex_labels ? g->vertex_labels : nullptr, levels, s));
+    KB_TRY(read_counters(ctx));
+    KB_TRY(device_error(ctx));
+
+    // rounds 1..kmax, captured once
+    p.gactive = gact;
+    if (kmax > 0) {
+        if (!ctx->cap_stream) KB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = ctx->cap_stream;
+        KB_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        kb_status st = KB_OK;
+        for (int i = 1; i <= kmax && st == KB_OK; ++i) {
+            st = next_epoch(ctx, R, cs);
+            if (st != KB_OK) break;
+            p.ehigh = 0xffffffffu - (uint32_t)i;
+            p.prev = levels + (size_t)(i - 1) * (size_t)n;
+            p.bitmap = (i & 1) ? bm_b : bm_a;
+            p.bitmap_prev = (i & 1) ? bm_a : bm_b;
+            p.gbase_prev = bases + (size_t)(i - 1) * (size_t)(G + 1);
+            p.gbase_cur = bases + (size_t)i * (size_t)(G + 1);
+            st = launch_round_body(ctx, R, cs, nullptr);
+            if (st != KB_OK) break;
+            kb::launch_carry_minima(p, cs);
+            kb::launch_renumber(p, R.prefix, R.scan_tmp, levels + (size_t)i * (size_t)n, cs);
+            kb::launch_graph_stop(p, i, kd, early, gact, glast, sticky, cs);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (st != KB_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return fail(ctx, KB_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(ctx, KB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+        cudaEvent_t e0 = ctx->ev[20], e1 = ctx->ev[21];
+        cudaEventRecord(e0, s);
+        const cudaError_t le = cudaGraphLaunch(exec, s);
+        cudaEventRecord(e1, s);
+        if (le != cudaSuccess) {
+            cudaGraphExecDestroy(exec);
+            return fail(ctx, KB_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(le));
+        }
+        const cudaError_t se = cudaStreamSynchronize(s);
+        cudaGraphExecDestroy(exec);
+        if (se != cudaSuccess) return fail(ctx, KB_ERR_CUDA, "batched rounds failed: %s", cudaGetErrorString(se));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ctx->round_ms.push_back(ms);
+    }
+    p.bitmap = bm_a;
+
+    // results: graph-local ids, per-graph counts, last refined level
+    std::vector<uint32_t> bases_h((size_t)(G + 1) * (size_t)(kmax + 1));
+    int32_t sticky_h = 0;
+    KB_CUDA(ctx, cudaMemcpyAsync(bases_h.data(), bases, sizeof(uint32_t) * bases_h.size(), cudaMemcpyDeviceToHost, s));
+    KB_CUDA(ctx, cudaMemcpyAsync(&sticky_h, sticky, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (lc_out) KB_CUDA(ctx, cudaMemcpyAsync(lc_out, glast, sizeof(int32_t) * (size_t)G, cudaMemcpyDeviceToHost, s));
+    for (int i = 0; i <= kmax; ++i)
+        kb::launch_localize(levels + (size_t)i * (size_t)n, n, vgraph, bases + (size_t)i * (size_t)(G + 1), s);
+    KB_CUDA(ctx, cudaGetLastError());
+    KB_CUDA(ctx, cudaStreamSynchronize(s));
+    if (sticky_h & kb::kErrTableFull) return fail(ctx, KB_ERR_TABLE_FULL, "block table probe limit reached");
+    if (sticky_h) return fail(ctx, KB_ERR_DEVICE_CHECK, "device consistency check failed (%d)", sticky_h);
+    for (int64_t j = 0; j < G; ++j)
+        for (int i = 0; i <= kmax; ++i) {
+            const uint32_t* bi = bases_h.data() + (size_t)i * (size_t)(G + 1);
+            counts[j * (kmax + 1) + i] = (int64_t)(bi[j + 1] - bi[j]);
+        }
     return KB_OK;
 }
 
@@ -637,6 +823,9 @@ kb_status kb_destroy(kb_context* ctx) {
     cudaFree(ctx->hub_tmp);
     cudaFree(ctx->plan_tmp);
     cudaFree(ctx->stage);
+    cudaFree(ctx->batch_ws);
+    cudaFree(ctx->tune_buf);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     delete ctx;
@@ -740,13 +929,63 @@ kb_status kb_get_timing(const kb_context* ctx, float* round_ms, int max_rounds, 
     return KB_OK;
 }
 
-kb_status kb_refine_batch(kb_context* ctx, const kb_graph*, const int64_t*, int64_t, const int32_t*,
-                          const kb_options*, int32_t*, int64_t*, int32_t*) {
-    return fail(ctx, KB_ERR_INVALID_ARG, "kb_refine_batch: not available in this build");
+kb_status kb_refine_batch(kb_context* ctx, const kb_graph* union_graph, const int64_t* graph_vertex_offsets,
+                          int64_t G, const int32_t* k_per_graph, const kb_options* opt, int32_t* levels,
+                          int64_t* counts, int32_t* levels_computed) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    return batch_impl(ctx, union_graph, graph_vertex_offsets, G, k_per_graph, opt, levels, counts, levels_computed);
 }
 
-kb_status kb_autotune(kb_context* ctx, const kb_graph*, const kb_options*, int, float*, int32_t*, float*) {
-    return fail(ctx, KB_ERR_INVALID_ARG, "kb_autotune: not available in this build");
+kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt, int rounds, float* best_lf,
+                      int32_t* best_thr, float* best_ms) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    if (rounds < 1) return fail(ctx, KB_ERR_INVALID_ARG, "rounds must be >= 1");
+    KB_TRY(check_graph(ctx, g, opt, rounds));
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int64_t n = g->n;
+    KB_TRY(ensure_buffer(ctx, &ctx->tune_buf, &ctx->tune_buf_bytes,
+                         std::max<size_t>(256, sizeof(int32_t) * (size_t)n * (size_t)(rounds + 1))));
+    int32_t* lev = reinterpret_cast<int32_t*>(ctx->tune_buf);
+    std::vector<int64_t> counts((size_t)rounds + 1);
+    const float lfs[] = {0.35f, 0.5f, 0.7f};
+    const int32_t thrs[] = {512, 1024, 2048};
+    const int32_t wvs[] = {64, 256, 1024};
+    float best = 1e30f;
+    kb_options o = *opt;
+    o.early_stop = 0;
+    o.validate = 0;
+    kb_options win = o;
+    // coordinate search: load factor, then hub threshold, then warp task size
+    for (int axis = 0; axis < 3; ++axis) {
+        for (int c = 0; c < 3; ++c) {
+            kb_options t = win;
+            if (axis == 0) t.load_factor = lfs[c];
+            if (axis == 1) t.hub_threshold = thrs[c];
+            if (axis == 2) t.small_task_vertices = wvs[c];
+            float total = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEvent_t e0 = ctx->ev[20], e1 = ctx->ev[21];
+                cudaEventRecord(e0, ctx->stream);
+                KB_TRY(refine_impl(ctx, g, &t, nullptr, 0, rounds, lev, counts.data(), nullptr));
+                cudaEventRecord(e1, ctx->stream);
+                KB_CUDA(ctx, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1) total = ms;  // the first run warms caches and scratch
+            }
+            if (total < best) {
+                best = total;
+                win = t;
+            }
+        }
+    }
+    ctx->tuned_load_factor = win.load_factor;
+    ctx->tuned_hub_threshold = win.hub_threshold;
+    ctx->tuned_warp_verts = win.small_task_vertices;
+    if (best_lf) *best_lf = win.load_factor;
+    if (best_thr) *best_thr = win.hub_threshold;
+    if (best_ms) *best_ms = best;
+    return KB_OK;
 }
 
 }  // extern "C"

@@ -35,6 +35,10 @@ __device__ __forceinline__ void join_slot(const RoundParams& p, uint64_t pos, ui
     p.slot_of[v] = (int32_t)pos;
 }
 
+__device__ __forceinline__ bool vertex_active(const RoundParams& p, int64_t v) {
+    return !p.gactive || p.gactive[p.vgraph[v]];
+}
+
 // A vertex without edges in the processed direction has the key (own block,
 // empty set): it is grouped by its own block exactly, without hashing or a
 // signature compare.  emin[own] keeps the smallest such vertex of this round;

@@ -26,6 +26,7 @@ constexpr int kHubChunk = 4096;  // edges per hub-chunk CTA (== kStage)
 constexpr int kHubFinalThreads = 256;
 constexpr int kProbeLimit = 1 << 22;  // bound on block-table probes per vertex
 constexpr int kSmallDegree = 32;      // vertices with at most this many edges take the warp kernel
+constexpr int kDefaultWarpVerts = 256;
 
 constexpr uint64_t kEmptyPair = ~0ull;  // block field 0x7fffffff never occurs (n <= 2^31-2)
 
@@ -47,6 +48,7 @@ struct RoundParams {
     const int32_t* prev;  // [n] previous level (vertex labels at level 0)
     int32_t hub_threshold;
     int32_t small_max;    // min(kSmallDegree, hub_threshold)
+    int32_t warp_verts;   // vertices per warp task of the small-vertex kernel
     int32_t hash_mode;
     uint32_t epoch;       // 1..255, tags this round's table entries
     uint64_t* table;      // [mask+1] block table
@@ -71,7 +73,17 @@ struct RoundParams {
     uint64_t* hub_lists;
     uint64_t* hub_acc;  // [n_hubs] sum of pair mixes over unique pairs
     uint32_t* hub_cnt;  // [n_hubs] unique pairs
+    // several graphs at once (batched refinement, serving); all null for one graph
+    const int32_t* vgraph;     // [n] graph of every vertex
+    const uint8_t* gactive;    // [G] the graph refines this round (else it keeps its partition)
+    const int64_t* voff;       // [G+1] first vertex of every graph
+    int32_t n_graphs;
+    const uint32_t* bitmap_prev;  // block minima of the previous level (kept by inactive graphs)
+    const uint32_t* gbase_prev;   // [G+1] rank of every graph's first vertex at the previous level
+    uint32_t* gbase_cur;          // [G+1] the same at this level (written by the renumbering)
 };
+
+__host__ __device__ __forceinline__ bool batched(const RoundParams& p) { return p.vgraph != nullptr; }
 
 // ---------------------------------------------------------------- hashing
 // SplitMix64 output function (Steele, Lea & Flood, "Fast splittable
@@ -123,6 +135,16 @@ void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp,
                      cudaStream_t s);
 size_t scan_tmp_words(int64_t n_items);
 void launch_fill_i32(int32_t* out, int64_t n, int32_t value, cudaStream_t s);
+// Batched runs: inactive graphs keep the block minima of the previous level.
+void launch_carry_minima(const RoundParams& p, cudaStream_t s);
+// Batched runs: per-graph stop test after round `round` (count unchanged with
+// early stop, or the graph's own k reached) -> gactive cleared, glast set.
+void launch_graph_stop(const RoundParams& p, int round, const int32_t* k_per_graph, const uint8_t* early,
+                       uint8_t* gactive, int32_t* glast, int32_t* sticky_err, cudaStream_t s);
+// Batched runs: row -= gbase[graph of v] (union-global ids to graph-local ids).
+void launch_localize(int32_t* row, int64_t n, const int32_t* vgraph, const uint32_t* gbase, cudaStream_t s);
+// vgraph[v] = graph owning v
+void launch_vertex_graph(const int64_t* voff, int32_t G, int64_t n, int32_t* vgraph, cudaStream_t s);
 
 // Setup (kb_setup.cu)
 void launch_validate(int64_t n, int64_t m, const int64_t* row, const int32_t* col, Counters* ctr,

@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
         vid = p.med_v[base + tid];
         rs = p.row[vid];
         const int64_t d = p.row[(int64_t)vid + 1] - rs;
-        if (d > p.small_max && d <= p.hub_threshold) {
+        if (d > p.small_max && d <= p.hub_threshold && vertex_active(p, vid)) {
             st = kPending;
             cdeg = (int)d;
         }
@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     const int h = s_h;
     const int E = (int)s_E;
     const int64_t e0 = s_e0;
+    if (!vertex_active(p, p.hub_v[h])) return;  // uniform over the CTA
 
     for (int base = 0; base < E; base += 4 * kTileThreads) {
         int32_t w[4], l[4], b[4];
@@ -496,6 +497,7 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
     const int tid = threadIdx.x;
     const int h = blockIdx.x;
     const int32_t v = p.hub_v[h];
+    if (!vertex_active(p, v)) return;
     const int32_t own = p.prev[v];
     const uint32_t cnt = p.hub_cnt[h];
     const uint64_t hv = vertex_hash(own, cnt, p.hub_acc[h], p.hash_mode);
@@ -695,6 +697,11 @@ __global__ void __launch_bounds__(kScanThreads) popc_scan_kernel(const uint32_t*
 __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const uint32_t* prefix, int32_t* out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        if (!vertex_active(p, v)) {
+            const int32_t g = p.vgraph[v];
+            out[v] = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
+            continue;
+        }
         const uint32_t bw = p.bitmap[v >> 5];
         uint32_t mn = (uint32_t)v;
         if (!((bw >> (v & 31)) & 1u)) {
@@ -708,6 +715,58 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
         const uint32_t mw = p.bitmap[mn >> 5];
         out[v] = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
     }
+}
+
+// rank of every graph's first vertex (the first vertex of a graph is always
+// the smallest member of its block)
+__global__ void graph_base_kernel(const RoundParams p, const uint32_t* prefix) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g > p.n_graphs) return;
+    const int64_t x = p.voff[g];
+    uint32_t r;
+    if (x >= p.n) {
+        r = prefix[(p.n >> 5) + 1];
+    } else {
+        r = prefix[x >> 5] + __popc(p.bitmap[x >> 5] & ((1u << (x & 31)) - 1u));
+    }
+    p.gbase_cur[g] = r;
+}
+
+__global__ void carry_minima_kernel(const RoundParams p) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < p.n; base += stride) {
+        const int64_t v = base + threadIdx.x;  // blockDim is a multiple of 32: a warp covers one bitmap word
+        const bool keep = v < p.n && !vertex_active(p, v) && ((p.bitmap_prev[v >> 5] >> (v & 31)) & 1u);
+        const unsigned b = __ballot_sync(kFull, keep);
+        if ((threadIdx.x & 31) == 0 && b) atomicOr(&p.bitmap[v >> 5], b);
+    }
+}
+
+__global__ void graph_stop_kernel(const RoundParams p, int round, const int32_t* k_per_graph, const uint8_t* early,
+                                  uint8_t* gactive, int32_t* glast, int32_t* sticky_err) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0 && p.ctr->err) atomicOr(sticky_err, p.ctr->err);
+    if (g >= p.n_graphs || !gactive[g]) return;
+    const uint32_t cur = p.gbase_cur[g + 1] - p.gbase_cur[g];
+    const uint32_t prv = p.gbase_prev[g + 1] - p.gbase_prev[g];
+    glast[g] = round;
+    if ((early[g] && cur == prv) || round >= k_per_graph[g]) gactive[g] = 0;
+}
+
+__global__ void localize_kernel(int32_t* row, int64_t n, const int32_t* vgraph, const uint32_t* gbase) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        row[v] = (int32_t)((uint32_t)row[v] - gbase[vgraph[v]]);
+}
+
+__global__ void vertex_graph_kernel(const int64_t* voff, int32_t G, int64_t n, int32_t* vgraph) {
+    const int g = blockIdx.x;
+    if (g >= G) return;
+    for (int64_t v = voff[g] + threadIdx.x; v < voff[g + 1]; v += blockDim.x) vgraph[v] = g;
+}
+
+__global__ void write_total_kernel(uint32_t* prefix, int64_t nw, const Counters* ctr) {
+    prefix[nw] = (uint32_t)ctr->count;
 }
 
 __global__ void fill_i32_kernel(int32_t* out, int64_t n, int32_t value) {
@@ -756,7 +815,36 @@ void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp,
     popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp);
     scan_block_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, nb, p.ctr);
     popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp, prefix);
+    if (batched(p)) {
+        // prefix[nw] (one past the last word) is not written by the scan: the
+        // total sits in the counters; graph_base_kernel reads prefix only for
+        // x < n, and takes the total from gbase of the last graph otherwise.
+        write_total_kernel<<<1, 1, 0, s>>>(prefix, nw, p.ctr);
+        graph_base_kernel<<<(p.n_graphs + 1 + 255) / 256, 256, 0, s>>>(p, prefix);
+    }
     if (p.n > 0) assign_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out);
+}
+
+void launch_carry_minima(const RoundParams& p, cudaStream_t s) {
+    if (p.n <= 0) return;
+    carry_minima_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p);
+}
+
+void launch_graph_stop(const RoundParams& p, int round, const int32_t* k_per_graph, const uint8_t* early,
+                       uint8_t* gactive, int32_t* glast, int32_t* sticky_err, cudaStream_t s) {
+    if (p.n_graphs <= 0) return;
+    graph_stop_kernel<<<(p.n_graphs + 255) / 256, 256, 0, s>>>(p, round, k_per_graph, early, gactive, glast,
+                                                                sticky_err);
+}
+
+void launch_localize(int32_t* row, int64_t n, const int32_t* vgraph, const uint32_t* gbase, cudaStream_t s) {
+    if (n <= 0) return;
+    localize_kernel<<<grid_for(n, 256), 256, 0, s>>>(row, n, vgraph, gbase);
+}
+
+void launch_vertex_graph(const int64_t* voff, int32_t G, int64_t n, int32_t* vgraph, cudaStream_t s) {
+    if (G <= 0) return;
+    vertex_graph_kernel<<<(unsigned)G, 256, 0, s>>>(voff, G, n, vgraph);
 }
 
 void launch_fill_i32(int32_t* out, int64_t n, int32_t value, cudaStream_t s) {

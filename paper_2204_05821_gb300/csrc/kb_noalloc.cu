@@ -113,6 +113,7 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     p.prev = prev;
     p.hub_threshold = thr;
     p.small_max = std::min(kb::kSmallDegree, thr);
+    p.warp_verts = opt->small_task_vertices;
     p.hash_mode = opt->hash_mode;
     p.epoch = 1;
     p.table = reinterpret_cast<uint64_t*>(base + kOffTable);

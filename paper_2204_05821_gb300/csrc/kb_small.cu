@@ -25,7 +25,6 @@ namespace kb {
 namespace {
 
 constexpr int kSmallThreads = 256;
-constexpr int kWarpVerts = 256;  // vertices per warp task
 
 __device__ __forceinline__ uint64_t shfl64(uint64_t x, int src) {
     return __shfl_sync(kFull, (unsigned long long)x, src);
@@ -37,9 +36,9 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
     const int lane = threadIdx.x & 31;
     uint64_t* wpairs = s_pairs + (threadIdx.x & ~31);
     const int64_t warp = ((int64_t)blockIdx.x * kSmallThreads + threadIdx.x) >> 5;
-    const int64_t vb = warp * kWarpVerts;
+    const int64_t vb = warp * p.warp_verts;
     if (vb >= p.n) return;
-    const int64_t ve = min(p.n, vb + kWarpVerts);
+    const int64_t ve = min(p.n, vb + p.warp_verts);
 
     for (int64_t v0 = vb; v0 < ve;) {
         const int nvw = (int)min((int64_t)32, ve - v0);
@@ -48,8 +47,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
         bool small = false;
         int64_t a = 0;
         int32_t own = 0;
-        if (lane < nvw) {
-            own = p.prev[v];
+        if (lane < nvw && vertex_active(p, v)) {
+            own = p.prev ? p.prev[v] : 0;
             if (kLevel0) {
                 small = true;
             } else {
@@ -125,7 +124,9 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
                 join_empty(p, own, (uint32_t)v);
                 pending = false;
             } else {
-                const uint64_t h = vertex_hash(own, cnt, acc, p.hash_mode);
+                // at level 0 of a batched run the key is (graph, label)
+                const uint32_t c2 = (kLevel0 && batched(p)) ? (uint32_t)p.vgraph[v] : cnt;
+                const uint64_t h = vertex_hash(own, c2, acc, p.hash_mode);
                 pos = h & p.mask;
                 hi = table_hi(h, p.epoch);
             }
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
                 continue;
             }
             // full signature compare with the representative, on this lane
-            bool eq = __ldg(p.prev + rep) == own;
+            bool eq = (p.prev ? __ldg(p.prev + rep) : 0) == own;
+            if (kLevel0 && batched(p)) eq = eq && p.vgraph[rep] == p.vgraph[v];
             if (!kLevel0 && eq) {
                 const int64_t rb = p.row[rep], re = p.row[(int64_t)rep + 1];
                 unsigned vfound = 0;
@@ -194,12 +196,15 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
 
 void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s) {
     if (p.n <= 0) return;
-    const int64_t warps = (p.n + kWarpVerts - 1) / kWarpVerts;
+    const int64_t wv = p.warp_verts > 0 ? p.warp_verts : kDefaultWarpVerts;
+    const int64_t warps = (p.n + wv - 1) / wv;
     const int64_t blocks = (warps * 32 + kSmallThreads - 1) / kSmallThreads;
+    RoundParams q = p;
+    q.warp_verts = (int32_t)wv;
     if (level0)
-        small_round_kernel<true><<<(unsigned)blocks, kSmallThreads, 0, s>>>(p);
+        small_round_kernel<true><<<(unsigned)blocks, kSmallThreads, 0, s>>>(q);
     else
-        small_round_kernel<false><<<(unsigned)blocks, kSmallThreads, 0, s>>>(p);
+        small_round_kernel<false><<<(unsigned)blocks, kSmallThreads, 0, s>>>(q);
 }
 
 }  // namespace kb

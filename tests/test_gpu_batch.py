@@ -1,0 +1,94 @@
+"""Batched refinement (kb_refine_batch): every graph's levels, counts and last
+refined level in the batch equal its solo result from the oracle, exactly."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2204_05821_gb300 as kb  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = kb.Context(0)
+    yield c
+    c.close()
+
+
+def mixed_graphs(seed, count):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gs = []
+    for i in range(count):
+        kind = i % 4
+        if kind == 0:
+            gs.append(graphgen.erdos_renyi(int(rng.integers(1, 400)), int(rng.integers(0, 2000)), 3, 3,
+                                           int(rng.integers(0, 1 << 30))))
+        elif kind == 1:
+            gs.append(graphgen.tiny_random(rng, n_max=30, m_max=80, n_labels=3))
+        elif kind == 2:
+            n = int(rng.integers(50, 3000))
+            gs.append(graphgen.chung_lu(n, 6 * n, 2.1, 2.1, n, n, 5, 1.5, 4, 1.2, int(rng.integers(0, 1 << 30))))
+        else:
+            gs.append(graphgen.from_edges(int(rng.integers(1, 20)), [], [], [], rng.integers(0, 2, size=0)))
+            gs[-1].vlabel = rng.integers(0, 3, size=gs[-1].n).astype(np.int32)
+    ks = rng.integers(0, 7, size=count).astype(np.int32)
+    return gs, ks
+
+
+def check_batch(ctx, graphs, ks, d, vl, el, early=True, **kw):
+    union, voff = graphgen.disjoint_union(graphs)
+    dg = kb.DeviceGraph.from_numpy(union, "cuda:0")
+    levels, counts, lc = ctx.refine_batch(dg, voff, ks, kb.Options(direction=d, use_vertex_labels=vl,
+                                                                    use_edge_labels=el, early_stop=early, **kw))
+    levels = levels.cpu().numpy()
+    kmax = int(ks.max())
+    for j, g in enumerate(graphs):
+        L, C, lcj = oracle.refine_graph(g, d, vl, el, k=int(ks[j]), early_stop=early)
+        a, b = int(voff[j]), int(voff[j + 1])
+        for i in range(kmax + 1):
+            src = min(i, int(ks[j]))
+            assert np.array_equal(levels[i, a:b], L[src]), (j, i, d, vl, el, kw)
+            assert counts[j, i] == C[src], (j, i)
+        assert lc[j] == lcj, (j, lc[j], lcj)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_batch_equals_solo(ctx, d):
+    graphs, ks = mixed_graphs(10 + d, 60)
+    check_batch(ctx, graphs, ks, d, True, True)
+
+
+@pytest.mark.parametrize("vl,el", [(False, True), (True, False), (False, False)])
+def test_batch_label_variants(ctx, vl, el):
+    graphs, ks = mixed_graphs(20, 40)
+    check_batch(ctx, graphs, ks, 0, vl, el)
+    check_batch(ctx, graphs, ks, 2, vl, el, early=False)
+
+
+def test_batch_weak_hash_and_hubs(ctx):
+    graphs, ks = mixed_graphs(30, 40)
+    check_batch(ctx, graphs, ks, 0, True, True, hash_mode=1)
+    check_batch(ctx, graphs, ks, 1, True, True, hub_threshold=4)
+    check_batch(ctx, graphs, ks, 2, True, True, hub_threshold=2, hash_mode=1)
+
+
+def test_batch_single_and_degenerate(ctx):
+    g = graphgen.make(graphgen.CONFIG_TINY)
+    check_batch(ctx, [g], np.array([10], dtype=np.int32), 0, True, True)
+    check_batch(ctx, [g, g, g], np.array([0, 3, 10], dtype=np.int32), 1, True, True)
+    empty = graphgen.from_edges(1, [], [], [], [4])
+    check_batch(ctx, [empty, g, empty], np.array([2, 2, 0], dtype=np.int32), 2, True, True)
+
+
+def test_autotune_keeps_results(ctx):
+    g = graphgen.make(graphgen.CONFIG_TINY)
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    lf, thr, ms = ctx.autotune(dg, kb.Options(), rounds=2)
+    assert 0 < lf <= 0.9 and thr in (512, 1024, 2048) and ms > 0
+    L, C, lc = oracle.refine_graph(g, 0, True, True, k=10)
+    res = ctx.refine(dg, 10, kb.Options())
+    assert np.array_equal(res.levels.cpu().numpy(), L) and np.array_equal(res.counts, C)
