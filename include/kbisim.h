@@ -200,6 +200,62 @@ kb_status kb_refine_batch(kb_context* ctx, const kb_graph* union_graph,
 kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt, int rounds,
                       float* best_load_factor, int32_t* best_hub_threshold, float* best_ms);
 
+/* ---- Serving: continuous batching of summarisation requests ----------------
+ * A server keeps every admitted request's graph and partitions on the device
+ * and advances all of them by one refinement round per kb_server_step: one
+ * set of kernel launches covers every in-flight request, whatever its size,
+ * direction or k.  Requests that arrive while others run wait until arena
+ * space, a request slot and device memory for their level store are free,
+ * and are then admitted at the next step (their level 0 is computed in that
+ * step alongside the others' rounds).  Results are identical to a solo
+ * kb_refine of the same graph and options.
+ *   max_vertices / max_edges   arena capacity; a graph's processed edges count
+ *                              (2m for KB_DIR_BOTH) must fit max_edges
+ *   max_requests               requests in flight at most
+ *   memory_budget              device bytes for the per-request level stores
+ *                              ((k+1)*n*4 each); 0 = free device memory minus a
+ *                              1 GiB reserve, checked at every admission
+ *   load_factor, hub_threshold, hash_mode   as in kb_options */
+typedef struct {
+    int64_t max_vertices;
+    int64_t max_edges;
+    int32_t max_requests;
+    int32_t hub_threshold;
+    size_t memory_budget;
+    float load_factor;
+    int32_t hash_mode;
+    int32_t reserved[6];
+} kb_server_config;
+
+typedef struct {
+    int64_t submitted, completed, running, waiting;
+    int64_t steps, compactions;
+    double p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency of completed requests */
+    double requests_per_s;            /* completed requests / time since the first submit */
+    double edge_rounds_per_s;         /* processed edges x rounds of completed requests / same time */
+} kb_server_stats;
+
+typedef struct kb_server kb_server;
+
+kb_server_config kb_server_config_default(void);
+kb_status kb_server_create(kb_server** server, int device, void* stream, const kb_server_config* cfg);
+kb_status kb_server_destroy(kb_server* server);
+const char* kb_server_last_error(const kb_server* server);
+/* Queue a request.  g holds HOST arrays, copied before the call returns;
+ * ticket receives its id.  Thread-safe with respect to kb_server_step. */
+kb_status kb_server_submit(kb_server* server, const kb_graph* g, const kb_options* opt, int k, int64_t* ticket);
+/* Admit what fits, then run one round for every in-flight request and retire
+ * finished ones (their levels are copied to host memory).  running / waiting
+ * (may be NULL) receive the request counts after the step. */
+kb_status kb_server_step(kb_server* server, int32_t* running, int32_t* waiting);
+/* state: 0 waiting, 1 running, 2 done (fetchable); KB_ERR_NOT_FOUND if unknown. */
+kb_status kb_server_poll(kb_server* server, int64_t ticket, int32_t* state);
+/* Copy a finished request's results to HOST buffers (levels int32[(k+1)*n],
+ * counts int64[k+1]) and forget it. */
+kb_status kb_server_fetch(kb_server* server, int64_t ticket, int32_t* levels, int64_t* counts,
+                          int32_t* levels_computed);
+kb_status kb_server_get_stats(kb_server* server, kb_server_stats* stats);
+
 /* ---- One refinement round without device allocation -----------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * must not allocate device memory, themselves or through the library: an

@@ -24,7 +24,7 @@ from ._capi import KbError
 
 __all__ = [
     "DIR_OUT", "DIR_IN", "DIR_BOTH", "Options", "DeviceGraph", "Context", "Result", "KbError", "refine",
-    "refine_round_noalloc", "library_path",
+    "refine_round_noalloc", "library_path", "Server",
 ]
 
 
@@ -284,6 +284,97 @@ class Context:
         self._check(self._lib.kb_get_timing(self._h, _np_ptr(rm), 4096, ctypes.byref(nr), _np_ptr(km), _np_ptr(kl)))
         fam = {name: (float(km[i]), int(kl[i])) for i, name in enumerate(_capi.KERNEL_NAMES)}
         return rm[: nr.value].tolist(), fam
+
+
+class Server:
+    """Continuous-batching summarisation server (``kb_server_*`` in the C ABI).
+
+    ``submit`` copies a host graph (numpy CSR) and queues it; every ``step``
+    admits what fits (arena space, request slots, device memory), runs one
+    refinement round for all in-flight requests at once and retires finished
+    ones.  ``fetch`` returns (levels [k+1, n], counts, levels_computed)."""
+
+    WAITING, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, device: int = 0, stream=None, max_vertices: int = 1 << 26, max_edges: int = 1 << 28,
+                 max_requests: int = 256, memory_budget: int = 0, load_factor: float = 0.0,
+                 hub_threshold: int = 0, hash_mode: int = 0):
+        import torch
+
+        self._lib = _capi.load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        cfg = self._lib.kb_server_config_default()
+        cfg.max_vertices, cfg.max_edges, cfg.max_requests = int(max_vertices), int(max_edges), int(max_requests)
+        cfg.memory_budget, cfg.load_factor = int(memory_budget), float(load_factor)
+        cfg.hub_threshold, cfg.hash_mode = int(hub_threshold), int(hash_mode)
+        h = ctypes.c_void_p()
+        _capi.check(self._lib.kb_server_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream.cuda_stream),
+                                                ctypes.byref(cfg)))
+        self._h = h
+        self._meta = {}
+
+    def _check(self, st):
+        if st != _capi.KB_OK:
+            raise KbError(st, self._lib.kb_server_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.kb_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, row_offsets, col, elabel, vlabel, k: int, options: Options = None) -> int:
+        options = options or Options()
+        row = np.ascontiguousarray(row_offsets, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        el = None if elabel is None else np.ascontiguousarray(elabel, dtype=np.int32)
+        vl = None if vlabel is None else np.ascontiguousarray(vlabel, dtype=np.int32)
+        g = _capi.KbGraph(row.shape[0] - 1, col.shape[0], _np_ptr(row), _np_ptr(col), _np_ptr(el), _np_ptr(vl))
+        o = options.to_c()
+        t = ctypes.c_int64(0)
+        self._check(self._lib.kb_server_submit(self._h, ctypes.byref(g), ctypes.byref(o), int(k), ctypes.byref(t)))
+        self._meta[t.value] = (row.shape[0] - 1, int(k))
+        return int(t.value)
+
+    def submit_graph(self, g, k: int, options: Options = None) -> int:
+        return self.submit(g.row_offsets, g.col, g.elabel, g.vlabel, k, options)
+
+    def step(self):
+        """One scheduling step; returns (running, waiting)."""
+        r, w = ctypes.c_int32(0), ctypes.c_int32(0)
+        self._check(self._lib.kb_server_step(self._h, ctypes.byref(r), ctypes.byref(w)))
+        return int(r.value), int(w.value)
+
+    def poll(self, ticket: int) -> int:
+        st = ctypes.c_int32(0)
+        self._check(self._lib.kb_server_poll(self._h, int(ticket), ctypes.byref(st)))
+        return int(st.value)
+
+    def fetch(self, ticket: int):
+        n, k = self._meta.pop(ticket)
+        levels = np.empty((k + 1, n), dtype=np.int32)
+        counts = np.zeros(k + 1, dtype=np.int64)
+        lc = ctypes.c_int32(0)
+        self._check(self._lib.kb_server_fetch(self._h, int(ticket), _np_ptr(levels), _np_ptr(counts), ctypes.byref(lc)))
+        return levels, counts, int(lc.value)
+
+    def stats(self) -> dict:
+        st = _capi.KbServerStats()
+        self._check(self._lib.kb_server_get_stats(self._h, ctypes.byref(st)))
+        return {name: getattr(st, name) for name, _ in _capi.KbServerStats._fields_}
 
 
 def refine_round_noalloc(graph: DeviceGraph, prev, out, options: Options = None, stream=None) -> int:

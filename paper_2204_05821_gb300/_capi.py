@@ -51,6 +51,35 @@ class KbOptions(ctypes.Structure):
     ]
 
 
+class KbServerConfig(ctypes.Structure):
+    _fields_ = [
+        ("max_vertices", ctypes.c_int64),
+        ("max_edges", ctypes.c_int64),
+        ("max_requests", ctypes.c_int32),
+        ("hub_threshold", ctypes.c_int32),
+        ("memory_budget", ctypes.c_size_t),
+        ("load_factor", ctypes.c_float),
+        ("hash_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
+    ]
+
+
+class KbServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("running", ctypes.c_int64),
+        ("waiting", ctypes.c_int64),
+        ("steps", ctypes.c_int64),
+        ("compactions", ctypes.c_int64),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("mean_ms", ctypes.c_double),
+        ("requests_per_s", ctypes.c_double),
+        ("edge_rounds_per_s", ctypes.c_double),
+    ]
+
+
 # (name, restype, argtypes) for every symbol the header declares
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -74,6 +103,16 @@ SIGNATURES = [
     ("kb_get_timing", _I, [_P, _P, _I, _P, _P, _P]),
     ("kb_refine_batch", _I, [_P, ctypes.POINTER(KbGraph), _P, _I64, _P, ctypes.POINTER(KbOptions), _P, _P, _P]),
     ("kb_autotune", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
+    ("kb_server_config_default", KbServerConfig, []),
+    ("kb_server_create", _I, [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(KbServerConfig)]),
+    ("kb_server_destroy", _I, [_P]),
+    ("kb_server_last_error", ctypes.c_char_p, [_P]),
+    ("kb_server_submit", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I,
+                              ctypes.POINTER(ctypes.c_int64)]),
+    ("kb_server_step", _I, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
+    ("kb_server_poll", _I, [_P, _I64, ctypes.POINTER(_I32)]),
+    ("kb_server_fetch", _I, [_P, _I64, _P, _P, ctypes.POINTER(_I32)]),
+    ("kb_server_get_stats", _I, [_P, ctypes.POINTER(KbServerStats)]),
     ("kb_refine_round_noalloc", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _P, _P,
                                      ctypes.POINTER(ctypes.c_int64)]),
 ]

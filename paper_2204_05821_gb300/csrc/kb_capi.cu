@@ -4,7 +4,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <cstdarg>
+#include <deque>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -742,6 +747,445 @@ kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, 
     return KB_OK;
 }
 
+
+// ============================================================================
+// Serving: continuous batching over a device arena (see kb_server_* in
+// kbisim.h).  Every admitted request owns one graph slot of the arena, in
+// arena order; retired slots stay as dead ranges until a compaction packs the
+// live ones into the other arena buffer.
+// ============================================================================
+struct Arena {
+    int64_t* row = nullptr;   // [Ncap+1]
+    int32_t* col = nullptr;   // [Mcap]
+    int32_t* lab = nullptr;   // [Mcap]
+    int32_t* vlab = nullptr;  // [Ncap]
+    int32_t* B[2] = {nullptr, nullptr};  // [Ncap] current / next level, union-global ids
+};
+
+struct ServeRequest {
+    int64_t ticket = 0;
+    int state = 0;  // 0 waiting, 1 running, 2 done
+    int64_t n = 0, m = 0, m_proc = 0;
+    std::vector<int64_t> row;
+    std::vector<int32_t> col, lab, vlab;
+    kb_options opt;
+    int k = 0;
+    int slot = -1;
+    int round = 0;  // next level to compute (0 = level 0)
+    int32_t* d_levels = nullptr;
+    size_t level_bytes = 0;
+    std::vector<int32_t> levels;  // host copy after completion
+    std::vector<int64_t> counts;
+    int32_t levels_computed = 0;
+    double t_submit = 0, t_done = 0;
+};
+
+struct Slot {
+    int64_t ticket = -1;  // -1: dead
+    int64_t vbase = 0, n = 0, ebase = 0, m = 0;
+};
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct kb_server {
+    kb_context* ctx = nullptr;
+    kb_server_config cfg{};
+    std::string last_error;
+    std::mutex mu;  // guards queue, requests, stats (submit vs step)
+    Arena arena[2];
+    int cur = 0;  // active arena buffer
+    int bsel = 0;  // which B buffer of the arena holds the current level
+    int64_t n_used = 0, m_used = 0;
+    std::vector<Slot> slots;
+    std::deque<int64_t> waiting;
+    std::map<int64_t, ServeRequest> reqs;
+    int64_t next_ticket = 1;
+    size_t level_bytes_in_use = 0;
+    // per-slot device arrays (capacity max_requests + dead slots: sized by max_slots)
+    int32_t max_slots = 0;
+    int32_t* vgraph = nullptr;
+    int64_t* voff = nullptr;
+    uint8_t* gactive = nullptr;
+    uint8_t* gmode = nullptr;
+    uint32_t* bases[2] = {nullptr, nullptr};
+    uint32_t* bitmap2 = nullptr;
+    int32_t** slot_levels = nullptr;
+    int32_t* slot_row = nullptr;
+    int64_t* slot_n = nullptr;
+    std::vector<uint32_t> gbase_host;
+    // staging for admission (raw graph, processed CSR for IN / BOTH)
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+    // round state
+    Prepared R;
+    bool dirty = true;
+    uint32_t rounds_since_prepare = 0;
+    int bmsel = 0;
+    uint32_t* bm_ws = nullptr;
+    // stats
+    double t_first = -1;
+    int64_t submitted = 0, completed = 0, steps = 0, compactions = 0;
+    double edge_rounds = 0;
+    std::vector<double> latencies_ms;
+};
+
+namespace {
+
+kb_status sfail(kb_server* sv, kb_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    sv->last_error = buf;
+    return st;
+}
+
+#define SV_CUDA(sv, call)                                                                            \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return sfail((sv), KB_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define SV_TRY(sv, expr)                                                     \
+    do {                                                                     \
+        kb_status s_ = (expr);                                               \
+        if (s_ != KB_OK) {                                                   \
+            if ((sv)->last_error.empty()) (sv)->last_error = (sv)->ctx->last_error; \
+            return s_;                                                       \
+        }                                                                    \
+    } while (0)
+
+int64_t processed_edges(const ServeRequest& r) { return r.opt.direction == KB_DIR_BOTH ? 2 * r.m : r.m; }
+
+// Copy request r's graph into the arena at the tail as slot `slot`.
+kb_status place_request(kb_server* sv, ServeRequest& r, int slot) {
+    kb_context* ctx = sv->ctx;
+    cudaStream_t s = ctx->stream;
+    Arena& A = sv->arena[sv->cur];
+    const int64_t n = r.n, m = r.m, mp = r.m_proc;
+    // staging: raw CSR (+ processed CSR for IN / BOTH)
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += align_up(b); return o; };
+    const size_t o_row = take(sizeof(int64_t) * (size_t)(n + 1));
+    const size_t o_col = take(sizeof(int32_t) * (size_t)m);
+    const size_t o_lab = take(sizeof(int32_t) * (size_t)m);
+    const size_t o_vlab = take(sizeof(int32_t) * (size_t)n);
+    Plan P;
+    P.n = n;
+    P.m = m;
+    P.dir = r.opt.direction;
+    P.m_proc = mp;
+    P.labels = !r.lab.empty();
+    layout_csr(P);
+    const size_t o_csr = take(P.csr_bytes);
+    if (off > sv->stage_bytes) {
+        if (sv->stage) cudaFree(sv->stage);
+        sv->stage = nullptr;
+        sv->stage_bytes = 0;
+        if (cudaMalloc(&sv->stage, off) != cudaSuccess) {
+            cudaGetLastError();
+            return sfail(sv, KB_ERR_OOM, "cannot allocate %zu bytes of staging", off);
+        }
+        sv->stage_bytes = off;
+    }
+    char* b = reinterpret_cast<char*>(sv->stage);
+    SV_CUDA(sv, cudaMemcpyAsync(b + o_row, r.row.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
+    if (m) SV_CUDA(sv, cudaMemcpyAsync(b + o_col, r.col.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+    if (m && P.labels)
+        SV_CUDA(sv, cudaMemcpyAsync(b + o_lab, r.lab.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+    if (!r.vlab.empty())
+        SV_CUDA(sv, cudaMemcpyAsync(b + o_vlab, r.vlab.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    kb::PlaceArgs a{};
+    a.srow = reinterpret_cast<const int64_t*>(b + o_row);
+    a.scol = reinterpret_cast<const int32_t*>(b + o_col);
+    a.slab = P.labels ? reinterpret_cast<const int32_t*>(b + o_lab) : nullptr;
+    if (needs_in_csr(P.dir)) {
+        kb_graph g{n, m, a.srow, a.scol, a.slab, nullptr};
+        char* csr = b + o_csr;
+        SV_TRY(sv, build_processed_csr(ctx, &g, P, csr));
+        a.srow = reinterpret_cast<const int64_t*>(csr + P.o_rowp);
+        a.scol = reinterpret_cast<const int32_t*>(csr + P.o_colp);
+        a.slab = P.labels ? reinterpret_cast<const int32_t*>(csr + P.o_labp) : nullptr;
+    }
+    a.svlab = r.vlab.empty() ? nullptr : reinterpret_cast<const int32_t*>(b + o_vlab);
+    a.drow = A.row;
+    a.dcol = A.col;
+    a.dlab = A.lab;
+    a.dvlab = A.vlab;
+    a.n = n;
+    a.m = mp;
+    a.src_vbase = 0;
+    a.src_ebase = 0;
+    a.dst_vbase = sv->n_used;
+    a.dst_ebase = sv->m_used;
+    kb::launch_place(a, s);
+    SV_CUDA(sv, cudaGetLastError());
+    Slot sl;
+    sl.ticket = r.ticket;
+    sl.vbase = sv->n_used;
+    sl.n = n;
+    sl.ebase = sv->m_used;
+    sl.m = mp;
+    if ((int)sv->slots.size() != slot) return sfail(sv, KB_ERR_DEVICE_CHECK, "slot order broken");
+    sv->slots.push_back(sl);
+    sv->n_used += n;
+    sv->m_used += mp;
+    r.slot = slot;
+    return KB_OK;
+}
+
+// Pack the live slots into the other arena buffer.
+kb_status compact(kb_server* sv) {
+    kb_context* ctx = sv->ctx;
+    cudaStream_t s = ctx->stream;
+    Arena& S = sv->arena[sv->cur];
+    Arena& D = sv->arena[1 - sv->cur];
+    std::vector<Slot> live;
+    int64_t nv = 0, ne = 0;
+    SV_CUDA(sv, cudaMemsetAsync(D.row, 0, sizeof(int64_t), s));
+    for (size_t j = 0; j < sv->slots.size(); ++j) {
+        const Slot& o = sv->slots[j];
+        if (o.ticket < 0) continue;
+        kb::PlaceArgs a{};
+        a.srow = S.row;
+        a.scol = S.col;
+        a.slab = S.lab;
+        a.svlab = S.vlab;
+        a.sB = S.B[sv->bsel];
+        a.drow = D.row;
+        a.dcol = D.col;
+        a.dlab = D.lab;
+        a.dvlab = D.vlab;
+        a.dB = D.B[0];
+        a.n = o.n;
+        a.m = o.m;
+        a.src_vbase = o.vbase;
+        a.src_ebase = o.ebase;
+        a.dst_vbase = nv;
+        a.dst_ebase = ne;
+        a.b_sub = sv->gbase_host.size() > j ? sv->gbase_host[j] : 0u;
+        a.b_add = (uint32_t)nv;
+        kb::launch_place(a, s);
+        Slot ns = o;
+        ns.vbase = nv;
+        ns.ebase = ne;
+        sv->reqs[o.ticket].slot = (int)live.size();
+        live.push_back(ns);
+        nv += o.n;
+        ne += o.m;
+    }
+    SV_CUDA(sv, cudaGetLastError());
+    sv->slots = live;
+    sv->n_used = nv;
+    sv->m_used = ne;
+    sv->cur = 1 - sv->cur;
+    sv->bsel = 0;
+    sv->gbase_host.clear();
+    sv->dirty = true;
+    ++sv->compactions;
+    return KB_OK;
+}
+
+size_t free_device_bytes() {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return fr;
+}
+
+// Admit waiting requests in arrival order while they fit.
+kb_status admit(kb_server* sv, bool* changed) {
+    std::vector<int64_t> admitted;
+    while (true) {
+        int64_t t;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (sv->waiting.empty()) break;
+            t = sv->waiting.front();
+        }
+        ServeRequest& r = sv->reqs[t];
+        int live = 0;
+        for (const Slot& sl : sv->slots) live += sl.ticket >= 0;
+        if (live >= sv->cfg.max_requests) break;
+        const size_t lb = sizeof(int32_t) * (size_t)r.n * (size_t)(r.k + 1);
+        const size_t budget = sv->cfg.memory_budget;
+        if (budget) {
+            if (sv->level_bytes_in_use + lb > budget) break;
+        } else {
+            const size_t fr = free_device_bytes();
+            if (fr < lb + ((size_t)1 << 30)) break;
+        }
+        const bool fits_tail = sv->n_used + r.n <= sv->cfg.max_vertices && sv->m_used + r.m_proc <= sv->cfg.max_edges &&
+                               (int)sv->slots.size() < sv->max_slots;
+        if (!fits_tail) {
+            int64_t ln = 0, lm = 0;
+            for (const Slot& sl : sv->slots)
+                if (sl.ticket >= 0) {
+                    ln += sl.n;
+                    lm += sl.m;
+                }
+            if (ln + r.n > sv->cfg.max_vertices || lm + r.m_proc > sv->cfg.max_edges) break;
+            SV_TRY(sv, compact(sv));
+        }
+        if (cudaMalloc(&r.d_levels, std::max<size_t>(lb, 4)) != cudaSuccess) {
+            cudaGetLastError();
+            r.d_levels = nullptr;
+            break;
+        }
+        r.level_bytes = lb;
+        sv->level_bytes_in_use += lb;
+        SV_TRY(sv, place_request(sv, r, (int)sv->slots.size()));
+        r.state = 1;
+        r.round = 0;
+        r.counts.assign((size_t)r.k + 1, 0);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->waiting.pop_front();
+        }
+        *changed = true;
+    }
+    return KB_OK;
+}
+
+// Finish request r after its last round: copy its levels to the host.
+kb_status retire(kb_server* sv, ServeRequest& r, int last) {
+    cudaStream_t s = sv->ctx->stream;
+    r.levels.assign((size_t)r.n * (size_t)(r.k + 1), 0);
+    if (r.n)
+        SV_CUDA(sv, cudaMemcpyAsync(r.levels.data(), r.d_levels, sizeof(int32_t) * (size_t)r.n * (size_t)(last + 1),
+                                    cudaMemcpyDeviceToHost, s));
+    SV_CUDA(sv, cudaStreamSynchronize(s));
+    for (int j = last + 1; j <= r.k; ++j) {
+        std::copy(r.levels.begin() + (size_t)last * (size_t)r.n, r.levels.begin() + (size_t)(last + 1) * (size_t)r.n,
+                  r.levels.begin() + (size_t)j * (size_t)r.n);
+        r.counts[(size_t)j] = r.counts[(size_t)last];
+    }
+    r.levels_computed = last;
+    cudaFree(r.d_levels);
+    r.d_levels = nullptr;
+    sv->level_bytes_in_use -= r.level_bytes;
+    sv->slots[(size_t)r.slot].ticket = -1;
+    r.slot = -1;
+    r.t_done = now_s();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r.state = 2;
+    ++sv->completed;
+    sv->latencies_ms.push_back(1000.0 * (r.t_done - r.t_submit));
+    sv->edge_rounds += (double)r.m_proc * (double)last;
+    return KB_OK;
+}
+
+kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
+    kb_context* ctx = sv->ctx;
+    cudaStream_t s = ctx->stream;
+    SV_CUDA(sv, cudaSetDevice(ctx->device));
+    bool changed = false;
+    SV_TRY(sv, admit(sv, &changed));
+    if (changed) sv->dirty = true;
+    int live = 0;
+    for (const Slot& sl : sv->slots) live += sl.ticket >= 0;
+    if (live > 0) {
+        const int G = (int)sv->slots.size();
+        Arena& A = sv->arena[sv->cur];
+        kb::RoundParams& p = sv->R.p;
+        if (sv->dirty) {
+            // re-plan the arena: medium / hub lists, block table, minima
+            kb_graph view{sv->n_used, sv->m_used, A.row, A.col, A.lab, nullptr};
+            kb_options o = kb_options_default();
+            o.validate = 0;
+            o.load_factor = sv->cfg.load_factor;
+            o.hub_threshold = sv->cfg.hub_threshold;
+            o.hash_mode = sv->cfg.hash_mode;
+            SV_TRY(sv, prepare(ctx, &view, &o, sv->R));
+            sv->bm_ws = sv->R.p.bitmap;
+            std::vector<int64_t> voff((size_t)G + 1);
+            for (int j = 0; j < G; ++j) voff[(size_t)j] = sv->slots[(size_t)j].vbase;
+            voff[(size_t)G] = sv->n_used;
+            SV_CUDA(sv, cudaMemcpyAsync(sv->voff, voff.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, s));
+            kb::launch_vertex_graph(sv->voff, G, sv->n_used, sv->vgraph, s);
+            sv->rounds_since_prepare = 0;
+            sv->dirty = false;
+        }
+        // per-slot flags for this step
+        std::vector<uint8_t> act((size_t)G), mode((size_t)G);
+        std::vector<int32_t*> lev((size_t)G, nullptr);
+        std::vector<int32_t> row((size_t)G, -1);
+        std::vector<int64_t> sn((size_t)G, 0);
+        for (int j = 0; j < G; ++j) {
+            const Slot& sl = sv->slots[(size_t)j];
+            sn[(size_t)j] = sl.n;
+            if (sl.ticket < 0) continue;
+            ServeRequest& r = sv->reqs[sl.ticket];
+            act[(size_t)j] = 1;
+            mode[(size_t)j] = r.round == 0 ? 1 : 0;
+            lev[(size_t)j] = r.d_levels;
+            row[(size_t)j] = r.round;
+        }
+        SV_CUDA(sv, cudaMemcpyAsync(sv->gactive, act.data(), (size_t)G, cudaMemcpyHostToDevice, s));
+        SV_CUDA(sv, cudaMemcpyAsync(sv->gmode, mode.data(), (size_t)G, cudaMemcpyHostToDevice, s));
+        SV_CUDA(sv, cudaMemcpyAsync(sv->slot_levels, lev.data(), sizeof(int32_t*) * (size_t)G, cudaMemcpyHostToDevice, s));
+        SV_CUDA(sv, cudaMemcpyAsync(sv->slot_row, row.data(), sizeof(int32_t) * (size_t)G, cudaMemcpyHostToDevice, s));
+        SV_CUDA(sv, cudaMemcpyAsync(sv->slot_n, sn.data(), sizeof(int64_t) * (size_t)G, cudaMemcpyHostToDevice, s));
+        // one round for everything in flight
+        SV_TRY(sv, next_epoch(ctx, sv->R, s));
+        p.ehigh = 0xffffffffu - (++sv->rounds_since_prepare);
+        p.vgraph = sv->vgraph;
+        p.voff = sv->voff;
+        p.n_graphs = G;
+        p.gactive = sv->gactive;
+        p.gmode = sv->gmode;
+        p.vlab = A.vlab;
+        p.prev = A.B[sv->bsel];
+        // block-minima bitmaps alternate between the prepared one and the server's own
+        p.bitmap = sv->bmsel ? sv->bitmap2 : sv->bm_ws;
+        p.bitmap_prev = sv->bmsel ? sv->bm_ws : sv->bitmap2;
+        p.gbase_prev = sv->bases[1 - (sv->steps & 1)];
+        p.gbase_cur = sv->bases[sv->steps & 1];
+        int32_t* out = A.B[1 - sv->bsel];
+        SV_TRY(sv, launch_round_body(ctx, sv->R, s, nullptr));
+        kb::launch_carry_minima(p, s);
+        kb::launch_renumber(p, sv->R.prefix, sv->R.scan_tmp, out, s);
+        kb::launch_emit(sv->n_used, sv->vgraph, out, p.gbase_cur, sv->slot_levels, sv->slot_row, sv->slot_n, sv->voff, s);
+        SV_CUDA(sv, cudaGetLastError());
+        sv->gbase_host.assign((size_t)G + 1, 0);
+        SV_CUDA(sv, cudaMemcpyAsync(sv->gbase_host.data(), p.gbase_cur, sizeof(uint32_t) * (size_t)(G + 1),
+                                    cudaMemcpyDeviceToHost, s));
+        SV_CUDA(sv, cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        SV_CUDA(sv, cudaStreamSynchronize(s));
+        if (ctx->h_ctr->err) {
+            SV_TRY(sv, device_error(ctx));
+        }
+        sv->bsel = 1 - sv->bsel;
+        sv->bmsel = 1 - sv->bmsel;
+        // bookkeeping and retirement
+        for (int j = 0; j < G; ++j) {
+            const Slot sl = sv->slots[(size_t)j];
+            if (sl.ticket < 0) continue;
+            ServeRequest& r = sv->reqs[sl.ticket];
+            const int64_t cnt = (int64_t)(sv->gbase_host[(size_t)j + 1] - sv->gbase_host[(size_t)j]);
+            r.counts[(size_t)r.round] = cnt;
+            const int done_round = r.round;
+            bool done = done_round >= r.k;
+            if (done_round > 0 && r.opt.early_stop && cnt == r.counts[(size_t)done_round - 1]) done = true;
+            ++r.round;
+            if (done) SV_TRY(sv, retire(sv, r, done_round));
+        }
+        ++sv->steps;
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    int run = 0;
+    for (const Slot& sl : sv->slots) run += sl.ticket >= 0;
+    if (running) *running = run;
+    if (waiting_out) *waiting_out = (int32_t)sv->waiting.size();
+    return KB_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -954,6 +1398,9 @@ kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     kb_options o = *opt;
     o.early_stop = 0;
     o.validate = 0;
+    if (!(o.load_factor > 0.f)) o.load_factor = 0.5f;
+    if (o.hub_threshold == 0) o.hub_threshold = kb::kDefaultHubThreshold;
+    if (o.small_task_vertices == 0) o.small_task_vertices = kb::kDefaultWarpVerts;
     kb_options win = o;
     // coordinate search: load factor, then hub threshold, then warp task size
     for (int axis = 0; axis < 3; ++axis) {
@@ -985,6 +1432,211 @@ kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     if (best_lf) *best_lf = win.load_factor;
     if (best_thr) *best_thr = win.hub_threshold;
     if (best_ms) *best_ms = best;
+    return KB_OK;
+}
+
+
+kb_server_config kb_server_config_default(void) {
+    kb_server_config c;
+    std::memset(&c, 0, sizeof(c));
+    c.max_vertices = (int64_t)1 << 26;
+    c.max_edges = (int64_t)1 << 28;
+    c.max_requests = 256;
+    return c;
+}
+
+kb_status kb_server_create(kb_server** out, int device, void* stream, const kb_server_config* cfg) {
+    if (!out || !cfg) return KB_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (cfg->max_vertices < 1 || cfg->max_vertices > 2147483646LL || cfg->max_edges < 0 || cfg->max_requests < 1)
+        return KB_ERR_INVALID_ARG;
+    if (cfg->load_factor < 0.f || cfg->load_factor > 0.9f) return KB_ERR_INVALID_ARG;
+    if (cfg->hub_threshold < 0 || cfg->hub_threshold > kb::kMaxHubThreshold) return KB_ERR_INVALID_ARG;
+    if (cfg->hash_mode < 0 || cfg->hash_mode > 1) return KB_ERR_INVALID_ARG;
+    kb_server* sv = new (std::nothrow) kb_server();
+    if (!sv) return KB_ERR_OOM;
+    sv->cfg = *cfg;
+    sv->max_slots = 4 * cfg->max_requests;
+    kb_status st = kb_create(&sv->ctx, device, stream);
+    if (st != KB_OK) {
+        delete sv;
+        return st;
+    }
+    const int64_t N = cfg->max_vertices, M = std::max<int64_t>(cfg->max_edges, 1), S = sv->max_slots;
+    bool ok = true;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (ok && cudaMalloc(ptr, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+    };
+    for (int a = 0; a < 2; ++a) {
+        Arena& A = sv->arena[a];
+        alloc((void**)&A.row, sizeof(int64_t) * (size_t)(N + 1));
+        alloc((void**)&A.col, sizeof(int32_t) * (size_t)M);
+        alloc((void**)&A.lab, sizeof(int32_t) * (size_t)M);
+        alloc((void**)&A.vlab, sizeof(int32_t) * (size_t)N);
+        alloc((void**)&A.B[0], sizeof(int32_t) * (size_t)N);
+        alloc((void**)&A.B[1], sizeof(int32_t) * (size_t)N);
+    }
+    alloc((void**)&sv->vgraph, sizeof(int32_t) * (size_t)N);
+    alloc((void**)&sv->voff, sizeof(int64_t) * (size_t)(S + 1));
+    alloc((void**)&sv->gactive, (size_t)S);
+    alloc((void**)&sv->gmode, (size_t)S);
+    alloc((void**)&sv->bases[0], sizeof(uint32_t) * (size_t)(S + 1));
+    alloc((void**)&sv->bases[1], sizeof(uint32_t) * (size_t)(S + 1));
+    alloc((void**)&sv->bitmap2, sizeof(uint32_t) * (size_t)((N >> 5) + 1));
+    alloc((void**)&sv->slot_levels, sizeof(int32_t*) * (size_t)S);
+    alloc((void**)&sv->slot_row, sizeof(int32_t) * (size_t)S);
+    alloc((void**)&sv->slot_n, sizeof(int64_t) * (size_t)S);
+    if (ok) {
+        ok = cudaMemset(sv->arena[0].row, 0, sizeof(int64_t)) == cudaSuccess &&
+             cudaMemset(sv->arena[1].row, 0, sizeof(int64_t)) == cudaSuccess &&
+             cudaMemset(sv->bitmap2, 0, sizeof(uint32_t) * (size_t)((N >> 5) + 1)) == cudaSuccess;
+    }
+    if (!ok) {
+        kb_server_destroy(sv);
+        return KB_ERR_OOM;
+    }
+    *out = sv;
+    return KB_OK;
+}
+
+kb_status kb_server_destroy(kb_server* sv) {
+    if (!sv) return KB_OK;
+    if (sv->ctx) {
+        cudaSetDevice(sv->ctx->device);
+        if (sv->ctx->stream) cudaStreamSynchronize(sv->ctx->stream); else cudaDeviceSynchronize();
+    }
+    for (auto& kv : sv->reqs)
+        if (kv.second.d_levels) cudaFree(kv.second.d_levels);
+    for (int a = 0; a < 2; ++a) {
+        Arena& A = sv->arena[a];
+        cudaFree(A.row);
+        cudaFree(A.col);
+        cudaFree(A.lab);
+        cudaFree(A.vlab);
+        cudaFree(A.B[0]);
+        cudaFree(A.B[1]);
+    }
+    cudaFree(sv->vgraph);
+    cudaFree(sv->voff);
+    cudaFree(sv->gactive);
+    cudaFree(sv->gmode);
+    cudaFree(sv->bases[0]);
+    cudaFree(sv->bases[1]);
+    cudaFree(sv->bitmap2);
+    cudaFree(sv->slot_levels);
+    cudaFree(sv->slot_row);
+    cudaFree(sv->slot_n);
+    cudaFree(sv->stage);
+    kb_destroy(sv->ctx);
+    delete sv;
+    return KB_OK;
+}
+
+const char* kb_server_last_error(const kb_server* sv) { return sv ? sv->last_error.c_str() : "no server"; }
+
+kb_status kb_server_submit(kb_server* sv, const kb_graph* g, const kb_options* opt, int k, int64_t* ticket) {
+    if (!sv || !ticket) return KB_ERR_INVALID_ARG;
+    if (!g || !opt) return sfail(sv, KB_ERR_INVALID_ARG, "graph and options must not be NULL");
+    if (g->n < 0 || g->m < 0 || k < 0 || opt->direction < 0 || opt->direction > 2)
+        return sfail(sv, KB_ERR_INVALID_ARG, "bad request");
+    if (g->n > 0 && !g->row_offsets) return sfail(sv, KB_ERR_INVALID_ARG, "row_offsets is NULL");
+    if (g->m > 0 && !g->col_indices) return sfail(sv, KB_ERR_INVALID_ARG, "col_indices is NULL");
+    const int64_t mp = opt->direction == KB_DIR_BOTH ? 2 * g->m : g->m;
+    if (g->n > sv->cfg.max_vertices || mp > sv->cfg.max_edges)
+        return sfail(sv, KB_ERR_INVALID_ARG, "request larger than the arena");
+    // host-side validation of the CSR (the arena is shared: a bad request must not reach it)
+    if (g->n > 0 && (g->row_offsets[0] != 0 || g->row_offsets[g->n] != g->m))
+        return sfail(sv, KB_ERR_INVALID_ARG, "row_offsets must run from 0 to m");
+    for (int64_t v = 0; v < g->n; ++v)
+        if (g->row_offsets[v + 1] < g->row_offsets[v]) return sfail(sv, KB_ERR_INVALID_ARG, "row_offsets not monotone");
+    for (int64_t e = 0; e < g->m; ++e)
+        if (g->col_indices[e] < 0 || g->col_indices[e] >= g->n)
+            return sfail(sv, KB_ERR_INVALID_ARG, "neighbour id out of range");
+    ServeRequest r;
+    r.n = g->n;
+    r.m = g->m;
+    r.m_proc = mp;
+    r.opt = *opt;
+    r.k = k;
+    if (g->n > 0) r.row.assign(g->row_offsets, g->row_offsets + g->n + 1);
+    else r.row.assign(1, 0);
+    if (g->m) r.col.assign(g->col_indices, g->col_indices + g->m);
+    if (g->m && g->edge_labels && opt->use_edge_labels) r.lab.assign(g->edge_labels, g->edge_labels + g->m);
+    if (g->n && g->vertex_labels && opt->use_vertex_labels) r.vlab.assign(g->vertex_labels, g->vertex_labels + g->n);
+    r.t_submit = now_s();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r.ticket = sv->next_ticket++;
+    *ticket = r.ticket;
+    if (sv->t_first < 0) sv->t_first = r.t_submit;
+    ++sv->submitted;
+    const int64_t t = r.ticket;
+    sv->reqs.emplace(t, std::move(r));
+    sv->waiting.push_back(t);
+    return KB_OK;
+}
+
+kb_status kb_server_step(kb_server* sv, int32_t* running, int32_t* waiting) {
+    if (!sv) return KB_ERR_INVALID_ARG;
+    sv->last_error.clear();
+    return server_step(sv, running, waiting);
+}
+
+kb_status kb_server_poll(kb_server* sv, int64_t ticket, int32_t* state) {
+    if (!sv || !state) return KB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return KB_ERR_NOT_FOUND;
+    *state = it->second.state;
+    return KB_OK;
+}
+
+kb_status kb_server_fetch(kb_server* sv, int64_t ticket, int32_t* levels, int64_t* counts, int32_t* levels_computed) {
+    if (!sv) return KB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(ticket);
+    if (it == sv->reqs.end()) return KB_ERR_NOT_FOUND;
+    ServeRequest& r = it->second;
+    if (r.state != 2) return sfail(sv, KB_ERR_INVALID_ARG, "request %lld has not finished", (long long)ticket);
+    if (levels && !r.levels.empty()) std::memcpy(levels, r.levels.data(), sizeof(int32_t) * r.levels.size());
+    if (counts) std::memcpy(counts, r.counts.data(), sizeof(int64_t) * r.counts.size());
+    if (levels_computed) *levels_computed = r.levels_computed;
+    sv->reqs.erase(it);
+    return KB_OK;
+}
+
+kb_status kb_server_get_stats(kb_server* sv, kb_server_stats* st) {
+    if (!sv || !st) return KB_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->submitted = sv->submitted;
+    st->completed = sv->completed;
+    int run = 0;
+    for (const Slot& sl : sv->slots) run += sl.ticket >= 0;
+    st->running = run;
+    st->waiting = (int64_t)sv->waiting.size();
+    st->steps = sv->steps;
+    st->compactions = sv->compactions;
+    if (!sv->latencies_ms.empty()) {
+        std::vector<double> l = sv->latencies_ms;
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double q) {
+            const size_t i = (size_t)std::min<double>((double)(l.size() - 1), std::ceil(q * (double)l.size()) - 1);
+            return l[i];
+        };
+        st->p50_ms = pct(0.50);
+        st->p99_ms = pct(0.99);
+        double sum = 0;
+        for (double x : l) sum += x;
+        st->mean_ms = sum / (double)l.size();
+    }
+    const double span = sv->t_first >= 0 ? now_s() - sv->t_first : 0;
+    if (span > 0) {
+        st->requests_per_s = (double)sv->completed / span;
+        st->edge_rounds_per_s = sv->edge_rounds / span;
+    }
     return KB_OK;
 }
 

@@ -39,6 +39,22 @@ __device__ __forceinline__ bool vertex_active(const RoundParams& p, int64_t v) {
     return !p.gactive || p.gactive[p.vgraph[v]];
 }
 
+// A graph in level-0 mode (serving: admitted this step) keys its vertices by
+// (graph, label) and ignores its edges.
+__device__ __forceinline__ bool vertex_level0(const RoundParams& p, int64_t v) {
+    return p.gmode && p.gmode[p.vgraph[v]] == 1;
+}
+
+// Active and refining by signature (not in level-0 mode).
+__device__ __forceinline__ bool vertex_refines(const RoundParams& p, int64_t v) {
+    return vertex_active(p, v) && !vertex_level0(p, v);
+}
+
+// In multi-graph runs a representative must belong to the same graph.
+__device__ __forceinline__ bool same_graph(const RoundParams& p, int64_t a, int64_t b) {
+    return !p.vgraph || p.vgraph[a] == p.vgraph[b];
+}
+
 // A vertex without edges in the processed direction has the key (own block,
 // empty set): it is grouped by its own block exactly, without hashing or a
 // signature compare.  emin[own] keeps the smallest such vertex of this round;

@@ -78,6 +78,8 @@ struct RoundParams {
     const uint8_t* gactive;    // [G] the graph refines this round (else it keeps its partition)
     const int64_t* voff;       // [G+1] first vertex of every graph
     int32_t n_graphs;
+    const uint8_t* gmode;      // [G] 1: the graph computes its level 0 this round (serving), or nullptr
+    const int32_t* vlab;       // [n] vertex labels read by graphs in level-0 mode, or nullptr (all 0)
     const uint32_t* bitmap_prev;  // block minima of the previous level (kept by inactive graphs)
     const uint32_t* gbase_prev;   // [G+1] rank of every graph's first vertex at the previous level
     uint32_t* gbase_cur;          // [G+1] the same at this level (written by the renumbering)
@@ -169,5 +171,32 @@ void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int3
                      cudaStream_t s);
 // Copy row src of the level store to the rows [first, last] of levels.
 void launch_copy_rows(int32_t* levels, int64_t n, int src, int first, int last, cudaStream_t s);
+
+// ---- serving arena (kb_serve.cu)
+// Copy vertices [src_vbase, src_vbase+n] and edges [src_ebase, src_ebase+m)
+// of a CSR into an arena at dst_vbase / dst_ebase, rebasing row offsets and
+// neighbour ids (the in-edge bit of a neighbour id is kept).  Labels may be
+// null (written as 0).  When sB and dB are given, block ids move too, as
+// sB - b_sub + b_add.
+struct PlaceArgs {
+    const int64_t* srow;
+    const int32_t* scol;
+    const int32_t* slab;
+    const int32_t* svlab;
+    const int32_t* sB;
+    int64_t* drow;
+    int32_t* dcol;
+    int32_t* dlab;
+    int32_t* dvlab;
+    int32_t* dB;
+    int64_t n, m;
+    int64_t src_vbase, dst_vbase, src_ebase, dst_ebase;
+    uint32_t b_sub, b_add;
+};
+void launch_place(const PlaceArgs& a, cudaStream_t s);
+// For every arena vertex whose graph g has slot_row[g] >= 0:
+// slot_levels[g][slot_row[g] * slot_n[g] + (v - voff[g])] = B[v] - gbase[g].
+void launch_emit(int64_t n, const int32_t* vgraph, const int32_t* B, const uint32_t* gbase, int32_t* const* slot_levels,
+                 const int32_t* slot_row, const int64_t* slot_n, const int64_t* voff, cudaStream_t s);
 
 }  // namespace kb

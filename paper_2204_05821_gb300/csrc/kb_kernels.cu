@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
         vid = p.med_v[base + tid];
         rs = p.row[vid];
         const int64_t d = p.row[(int64_t)vid + 1] - rs;
-        if (d > p.small_max && d <= p.hub_threshold && vertex_active(p, vid)) {
+        if (d > p.small_max && d <= p.hub_threshold && vertex_refines(p, vid)) {
             st = kPending;
             cdeg = (int)d;
         }
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
             for (int q = warp; q < qn; q += kTileThreads / 32) {
                 const int j = s_qj[q];
                 const uint32_t r = s_qr[q];
-                bool ok = (__ldg(p.prev + r) == s_own[j]);
+                bool ok = same_graph(p, r, s_vid[j]) && (__ldg(p.prev + r) == s_own[j]);
                 if (ok) {
                     const int64_t rb = p.row[r], re = p.row[r + 1];
                     int nf = 0;
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     const int h = s_h;
     const int E = (int)s_E;
     const int64_t e0 = s_e0;
-    if (!vertex_active(p, p.hub_v[h])) return;  // uniform over the CTA
+    if (!vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
 
     for (int base = 0; base < E; base += 4 * kTileThreads) {
         int32_t w[4], l[4], b[4];
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
     const int tid = threadIdx.x;
     const int h = blockIdx.x;
     const int32_t v = p.hub_v[h];
-    if (!vertex_active(p, v)) return;
+    if (!vertex_refines(p, v)) return;
     const int32_t own = p.prev[v];
     const uint32_t cnt = p.hub_cnt[h];
     const uint64_t hv = vertex_hash(own, cnt, p.hub_acc[h], p.hash_mode);
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
             return;
         }
         const uint32_t r = s_rep;
-        bool ok = (__ldg(p.prev + r) == own);
+        bool ok = same_graph(p, r, v) && (__ldg(p.prev + r) == own);
         const int64_t rb = p.row[r], re = p.row[r + 1];
         if (ok && re - rb > p.hub_threshold) {
             // representative is a hub: compare distinct counts, then look its

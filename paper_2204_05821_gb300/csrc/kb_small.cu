@@ -47,11 +47,17 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
         bool small = false;
         int64_t a = 0;
         int32_t own = 0;
+        bool l0 = kLevel0;
         if (lane < nvw && vertex_active(p, v)) {
-            own = p.prev ? p.prev[v] : 0;
-            if (kLevel0) {
+            if (!kLevel0 && vertex_level0(p, v)) {
+                l0 = true;
+                own = p.vlab ? p.vlab[v] : 0;
+                small = true;
+            } else if (kLevel0) {
+                own = p.prev ? p.prev[v] : 0;
                 small = true;
             } else {
+                own = p.prev ? p.prev[v] : 0;
                 a = p.row[v];
                 const int64_t d = p.row[v + 1] - a;
                 small = d <= p.small_max;
@@ -120,12 +126,12 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
         uint64_t pos = 0;
         uint32_t hi = 0, rep = 0;
         if (pending) {
-            if (!kLevel0 && cd == 0) {
+            if (!l0 && cd == 0) {
                 join_empty(p, own, (uint32_t)v);
                 pending = false;
             } else {
-                // at level 0 of a batched run the key is (graph, label)
-                const uint32_t c2 = (kLevel0 && batched(p)) ? (uint32_t)p.vgraph[v] : cnt;
+                // at level 0 of a multi-graph run the key is (graph, label)
+                const uint32_t c2 = (l0 && batched(p)) ? (uint32_t)p.vgraph[v] : cnt;
                 const uint64_t h = vertex_hash(own, c2, acc, p.hash_mode);
                 pos = h & p.mask;
                 hi = table_hi(h, p.epoch);
@@ -150,9 +156,12 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
                 continue;
             }
             // full signature compare with the representative, on this lane
-            bool eq = (p.prev ? __ldg(p.prev + rep) : 0) == own;
-            if (kLevel0 && batched(p)) eq = eq && p.vgraph[rep] == p.vgraph[v];
-            if (!kLevel0 && eq) {
+            bool eq = same_graph(p, rep, v);
+            if (eq) {
+                const int32_t* keys = (l0 && !kLevel0) ? p.vlab : p.prev;
+                eq = (keys ? __ldg(keys + rep) : 0) == own;
+            }
+            if (!l0 && eq) {
                 const int64_t rb = p.row[rep], re = p.row[(int64_t)rep + 1];
                 unsigned vfound = 0;
                 for (int64_t e0 = rb; e0 < re && eq; e0 += 4) {
