@@ -258,6 +258,8 @@ def run_ours(args, rank, world, local):
     else:
         total_edge_rounds = float(rounds) * m
     value = total_edge_rounds / elapsed
+    counts_last = [int(x) for x in r.counts]
+    del r
 
     # roofline of the dominant kernel family (algorithmic bytes per launch)
     hub_thr, small_max = 2048, 32
@@ -289,7 +291,10 @@ def run_ours(args, rank, world, local):
                 "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                 "kernel_share": {kname: fam_ms[kname] / sum(fam_ms.values()) for kname in fam_ms},
                 "per_launch_ms": {kname: fam_ms[kname] / max(1, fam_n[kname]) for kname in fam_ms}}
-    launches = int(sum(fam_n.values()))
+    # our kernels per family event: renumbering is 4 kernels; per call add the
+    # setup kernels (validation, classification, hub search) and level 0 (5)
+    per_event = {"small": 1, "medium": 1, "hub_chunk": 1, "hub_final": 1, "renumber": 4, "other": 0}
+    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 8 * args.steps
 
     # end to end through the host-buffer entry point, pinned host memory
     e2e = None
@@ -309,6 +314,7 @@ def run_ours(args, rank, world, local):
         for _ in range(e_steps):
             rr = ctx.refine_host(np_row, np_col, np_el, np_vl, k, opts, out=np_out)
             e_rounds += rr.levels_computed
+            del rr
         et = time.perf_counter() - t0
         if dist:
             t = torch.tensor([et], device=device)
@@ -318,6 +324,19 @@ def run_ours(args, rank, world, local):
         d2h = hout.numel() * 4
         e2e = {"value": e_rounds * m * world / et, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": e_steps}
+        del hrow, hcol, hel, hvl, hout, np_row, np_col, np_el, np_vl, np_out
+
+    batch_info = serve_info = None
+    if world == 1 and not args.no_batch:
+        del wl, dg, levels
+        ctx.close()
+        torch.cuda.empty_cache()
+        ctx = kb.Context(local)
+        batch_info = bench_batch(ctx, device)
+        torch.cuda.empty_cache()
+    if world == 1 and not args.no_serve:
+        serve_info = bench_serve(device)
+        torch.cuda.empty_cache()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -326,17 +345,146 @@ def run_ours(args, rank, world, local):
                 "config": dict(describe(args.workload, cfg, k, "out"),
                                vertex_classes={"small_le32": [n_small, small_edges], "medium": [n_med, med_edges],
                                                "hub_gt2048": [n_hubs, hub_edges]},
-                               counts_last_step=[int(x) for x in r.counts],
+                               counts_last_step=counts_last,
                                l2="inputs larger than L2 (CSR %.1f GB); no flush" % ((8 * (n + 1) + 8 * m) / 1e9),
                                parallelism="replicas" if world > 1 else "single GPU",
                                rounds_per_step=rounds / args.steps),
-                "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
+                "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+                "batch": batch_info, "serve": serve_info}
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(cfg)
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+
+# ----------------------------------------------------------------------------- batching and serving
+
+
+def bench_batch(ctx, device, steps=3):
+    """The batching workload (4,096 uneven graphs) through kb_refine_batch,
+    against one kb_refine launch per graph on the same GPU."""
+    import torch
+
+    import paper_2204_05821_gb300 as kb
+
+    union, voff, ks = graphgen.batch_union_torch(device=device)
+    dg = kb.DeviceGraph(union["row_offsets"], union["col"], union["elabel"], union["vlabel"])
+    opts = kb.Options()
+    G = len(ks)
+    ctx.refine_batch(dg, voff, ks, opts)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _, counts, lc = ctx.refine_batch(dg, voff, ks, opts)
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / steps
+    # plain path: one kb_refine per graph
+    row, col, el, vl = union["row_offsets"], union["col"], union["elabel"], union["vlabel"]
+    singles = []
+    for j in range(G):
+        a, b = int(voff[j]), int(voff[j + 1])
+        e0, e1 = int(row[a].item()), int(row[b].item())
+        singles.append(kb.DeviceGraph((row[a:b + 1] - e0).contiguous(), (col[e0:e1] - a).contiguous(),
+                                      el[e0:e1].contiguous(), vl[a:b].contiguous()))
+    for j in range(4):
+        ctx.refine(singles[j], int(ks[j]), opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(G):
+        ctx.refine(singles[j], int(ks[j]), opts)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    edge_rounds = float(np.sum(lc.astype(np.float64) * np.diff([int(row[int(x)].item()) for x in voff])))
+    del singles
+    return {"workload": "4096 ER graphs, edges lognormal(median 5e4, sigma 1.25) in [1e3, 2e6], n=m/5, "
+                        "16 vertex / 8 edge labels uniform, k uniform 1..10, seed 3",
+            "graphs": G, "edges": int(union["m"]), "vertices": int(union["n"]),
+            "graphs_per_s": G / tb, "ms_per_batch": 1000 * tb, "edge_rounds_per_s": edge_rounds / tb,
+            "plain_graphs_per_s": G / tp, "plain_ms": 1000 * tp, "speedup_vs_plain": tp / tb}
+
+
+def bench_serve(device, duration_s=8.0, rate=200.0, seed=4, plain_requests=120):
+    """A Poisson stream of summarisation requests through kb_server_*.
+    Graphs come from a pre-drawn pool spanning the size distribution (each
+    request takes the pool graph closest to its drawn size), since drawing
+    hundreds of million-edge graphs per second on the host is not possible."""
+    import torch
+
+    import paper_2204_05821_gb300 as kb
+
+    stream = graphgen.serve_workload(duration_s=duration_s, rate=rate, seed=seed)
+    sizes = np.array([r[1] for r in stream])
+    qs = np.unique(np.quantile(sizes, np.linspace(0, 1, 24)).astype(np.int64))
+    pool = []
+    for i, mm in enumerate(qs):
+        n = max(1, int(mm) // 5)
+        c = dict(n=n, m=int(mm), gamma_out=2.1, gamma_in=2.1, max_out_deg=max(1.0, mm / 10),
+                 max_in_deg=max(1.0, mm / 10), n_vlabels=64, zipf_v=1.5, n_elabels=32, zipf_e=1.2, seed=1000 + i)
+        d = graphgen.chung_lu_torch(device=device, **c)
+        pool.append(tuple(d[kx].cpu().numpy() for kx in ("row_offsets", "col", "elabel", "vlabel")))
+        del d
+    torch.cuda.synchronize()
+    pick = [int(np.argmin(np.abs(qs - mm))) for mm in sizes]
+    opts = kb.Options()
+    import threading as th
+
+    done = {}
+    with kb.Server(int(str(device).split(":")[-1]) if ":" in str(device) else 0, max_vertices=1 << 26,
+                   max_edges=1 << 28, max_requests=256) as sv:
+        lock = th.Lock()
+        tickets = []
+        t_start = time.perf_counter()
+
+        def producer():
+            for (ta, mm, k, _), pi in zip(stream, pick):
+                dt = t_start + ta - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                r, c, e, v = pool[pi]
+                t = sv.submit(r, c, e, v, k, opts)
+                with lock:
+                    tickets.append(t)
+
+        prod = th.Thread(target=producer)
+        prod.start()
+        while True:
+            running, waiting = sv.step()
+            with lock:
+                pending = list(tickets)
+            for t in pending:
+                if sv.poll(t) == kb.Server.DONE:
+                    sv.fetch(t)
+                    with lock:
+                        tickets.remove(t)
+                    done[t] = 1
+            if not prod.is_alive() and running == 0 and waiting == 0:
+                with lock:
+                    if not tickets:
+                        break
+            if running == 0 and waiting == 0:
+                time.sleep(0.0005)
+        prod.join()
+        st = sv.stats()
+    # plain path: the same requests one after another through kb_refine_host
+    ctx = kb.Context(int(str(device).split(":")[-1]) if ":" in str(device) else 0)
+    t0 = time.perf_counter()
+    for (ta, mm, k, _), pi in list(zip(stream, pick))[:plain_requests]:
+        r, c, e, v = pool[pi]
+        ctx.refine_host(r, c, e, v, k, opts)
+    tp = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": "Poisson arrivals %.0f/s for %.0f s; edges lognormal(median 7e5, sigma 1.4) in [1e4, 5e7], "
+                        "Chung-Lu exponent 2.1, 64 vertex / 32 edge labels Zipf, k uniform 1..10, seed %d; graphs "
+                        "from a pool of %d pre-drawn graphs at the size quantiles" % (rate, duration_s, seed, len(qs)),
+            "requests": len(stream), "completed": int(st["completed"]), "p50_ms": st["p50_ms"],
+            "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "requests_per_s": st["requests_per_s"],
+            "edge_rounds_per_s": st["edge_rounds_per_s"], "steps": int(st["steps"]),
+            "compactions": int(st["compactions"]), "plain_requests_per_s": min(plain_requests, len(stream)) / tp,
+            "plain_sample": "first %d requests, one kb_refine_host each, back to back" % min(plain_requests,
+                                                                                         len(stream))}
 
 
 def main():
@@ -349,6 +497,8 @@ def main():
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
