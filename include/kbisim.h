@@ -88,7 +88,7 @@ typedef struct {
  *                      signature compare); results are identical in both modes
  *   validate           1: check offsets and ids on the device before refining
  *   small_task_vertices vertices each warp of the small-vertex kernel takes per task
- *                      (tile size); 0 -> default 256, else 32..65536 */
+ *                      (tile size); 0 -> default 128, else 32..65536 */
 typedef struct {
     int32_t direction;
     int32_t use_vertex_labels;

@@ -480,6 +480,9 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
 // Advance the table epoch (entries of other epochs read as empty); the table
 // is cleared once every 255 rounds.
 kb_status next_epoch(kb_context* ctx, Prepared& R, cudaStream_t s) {
+#ifdef KB_DIRECT_CAS
+    if (R.epoch > 0) KB_CUDA(ctx, cudaMemsetAsync(R.p.table, 0, sizeof(uint64_t) * (size_t)R.P.cap, s));
+#endif
     if (R.epoch == 255) {
         KB_CUDA(ctx, cudaMemsetAsync(R.p.table, 0, sizeof(uint64_t) * (size_t)R.P.cap, s));
         R.epoch = 0;
@@ -1393,7 +1396,7 @@ kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     std::vector<int64_t> counts((size_t)rounds + 1);
     const float lfs[] = {0.35f, 0.5f, 0.7f};
     const int32_t thrs[] = {512, 1024, 2048};
-    const int32_t wvs[] = {64, 256, 1024};
+    const int32_t wvs[] = {64, 128, 256};
     float best = 1e30f;
     kb_options o = *opt;
     o.early_stop = 0;

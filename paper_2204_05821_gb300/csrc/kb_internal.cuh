@@ -26,7 +26,7 @@ constexpr int kHubChunk = 4096;  // edges per hub-chunk CTA (== kStage)
 constexpr int kHubFinalThreads = 256;
 constexpr int kProbeLimit = 1 << 22;  // bound on block-table probes per vertex
 constexpr int kSmallDegree = 32;      // vertices with at most this many edges take the warp kernel
-constexpr int kDefaultWarpVerts = 256;
+constexpr int kDefaultWarpVerts = 128;
 
 constexpr uint64_t kEmptyPair = ~0ull;  // block field 0x7fffffff never occurs (n <= 2^31-2)
 

@@ -14,8 +14,16 @@
 //     pairs and looks each up among its own vertex's pairs, which the warp
 //     parks in a 256-byte shared buffer; equality needs every pair of each
 //     side found on the other.
-// No block-level barriers: occupancy hides the latency of the gather, the
-// table probes and the compares.
+//
+// Hot keys.  In power-law graphs millions of vertices share a key (all
+// edgeless vertices with the same label, all vertices with one edge to the
+// same hub block), and a global atomic per vertex on the same word serialises.
+// So joins are aggregated per CTA: a shared map keyed by the table slot (or by
+// the own block of an empty signature) keeps the smallest joining vertex, and
+// the CTA applies one global atomicMin per key when it finishes.  New-block
+// owners toggle their minimum bits once per window (one atomicXor per bitmap
+// word).  The XOR toggling of block minima is order independent, so the
+// aggregation leaves the result unchanged.
 #include <cuda_runtime.h>
 
 #include "kb_device.cuh"
@@ -25,19 +33,80 @@ namespace kb {
 namespace {
 
 constexpr int kSmallThreads = 256;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr int kMapCap = 2048;  // joins a CTA can aggregate (>= 2 x its vertices at the default task size)
+constexpr uint64_t kMapEmpty = ~0ull;
+constexpr uint64_t kEmptyKeyBit = 1ull << 63;  // map key of an empty-signature join: bit 63 | own
 
 __device__ __forceinline__ uint64_t shfl64(uint64_t x, int src) {
     return __shfl_sync(kFull, (unsigned long long)x, src);
 }
 
+struct JoinMap {
+    uint64_t key[kMapCap];
+    uint32_t hi[kMapCap];
+    uint32_t vmin[kMapCap];
+};
+
+// Record that v joins `key`; false when the map has no room (the caller then
+// joins globally right away).
+__device__ __forceinline__ bool map_join(JoinMap& M, uint64_t key, uint32_t hi, uint32_t v) {
+    uint32_t slot = (uint32_t)(mix64(key) >> 32) & (kMapCap - 1);
+    for (int t = 0; t < 32; ++t) {
+        uint64_t cur = M.key[slot];
+        if (cur == kMapEmpty) {
+            cur = atomicCAS(reinterpret_cast<unsigned long long*>(&M.key[slot]), (unsigned long long)kMapEmpty,
+                            (unsigned long long)key);
+            if (cur == kMapEmpty) {
+                M.hi[slot] = hi;
+                cur = key;
+            }
+        }
+        if (cur == key) {
+            atomicMin(&M.vmin[slot], v);
+            return true;
+        }
+        slot = (slot + 1) & (kMapCap - 1);
+    }
+    return false;
+}
+
+// Global atomicMin of a CTA's smallest joining vertex, with minimum toggles.
+__device__ __forceinline__ void flush_join(const RoundParams& p, uint64_t key, uint32_t hi, uint32_t v) {
+    if (key & kEmptyKeyBit) {
+        const int32_t own = (int32_t)(uint32_t)key;
+        const uint64_t want = ((uint64_t)p.ehigh << 32) | v;
+        const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(&p.emin[own]), (unsigned long long)want);
+        if ((uint32_t)(old >> 32) != p.ehigh) {
+            toggle_min(p.bitmap, v);
+        } else if (v < (uint32_t)old) {
+            toggle_min(p.bitmap, v);
+            toggle_min(p.bitmap, (uint32_t)old);
+        }
+    } else {
+        const uint64_t want = ((uint64_t)hi << 32) | v;
+        const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(&p.table[key]), (unsigned long long)want);
+        if (v < (uint32_t)old) {
+            toggle_min(p.bitmap, v);
+            toggle_min(p.bitmap, (uint32_t)old);
+        }
+    }
+}
+
 template <bool kLevel0>
 __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundParams p) {
     __shared__ uint64_t s_pairs[kSmallThreads];
+    __shared__ JoinMap M;
     const int lane = threadIdx.x & 31;
     uint64_t* wpairs = s_pairs + (threadIdx.x & ~31);
-    const int64_t warp = ((int64_t)blockIdx.x * kSmallThreads + threadIdx.x) >> 5;
-    const int64_t vb = warp * p.warp_verts;
-    if (vb >= p.n) return;
+    for (int i = threadIdx.x; i < kMapCap; i += kSmallThreads) {
+        M.key[i] = kMapEmpty;
+        M.vmin[i] = 0xffffffffu;
+    }
+    __syncthreads();
+
+    const int64_t cta_base = (int64_t)blockIdx.x * kSmallWarps * p.warp_verts;
+    const int64_t vb = cta_base + (int64_t)(threadIdx.x >> 5) * p.warp_verts;
     const int64_t ve = min(p.n, vb + p.warp_verts);
 
     for (int64_t v0 = vb; v0 < ve;) {
@@ -123,11 +192,15 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
         }
 
         bool pending = lane < nfit && small;
+        bool inserted = false;
         uint64_t pos = 0;
         uint32_t hi = 0, rep = 0;
         if (pending) {
             if (!l0 && cd == 0) {
-                join_empty(p, own, (uint32_t)v);
+                // (own block, empty set): grouped by the own block exactly
+                const uint64_t key = kEmptyKeyBit | (uint32_t)own;
+                if (!map_join(M, key, 0u, (uint32_t)v)) flush_join(p, key, 0u, (uint32_t)v);
+                p.slot_of[v] = (int32_t)(0x80000000u | (uint32_t)own);
                 pending = false;
             } else {
                 // at level 0 of a multi-graph run the key is (graph, label)
@@ -145,8 +218,9 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
         const unsigned vmask = cd >= 32 ? kFull : ((1u << cd) - 1u);
         while (__any_sync(kFull, pending)) {
             if (!pending) continue;
-            const int r = probe_table(p, &pos, hi, (uint32_t)v, &rep);
+            const int r = probe_table(p, &pos, hi, (uint32_t)v, &rep, false);
             if (r == 0) {
+                inserted = true;
                 pending = false;
                 continue;
             }
@@ -191,13 +265,31 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
                 if (vfound != vmask) eq = false;
             }
             if (eq) {
-                join_slot(p, pos, hi, (uint32_t)v);
+                if (!map_join(M, pos, hi, (uint32_t)v)) flush_join(p, pos, hi, (uint32_t)v);
+                p.slot_of[v] = (int32_t)pos;
                 pending = false;
             } else {
                 pos = (pos + 1) & p.mask;
             }
         }
+        // new-block owners of this window: one atomicXor per bitmap word
+        {
+            const uint32_t sh = (uint32_t)(v0 & 31);
+            const int64_t w0 = v0 >> 5;
+            const bool in0 = ((v0 + lane) >> 5) == w0;
+            const unsigned m0 = __ballot_sync(kFull, inserted && in0);
+            const unsigned m1 = __ballot_sync(kFull, inserted && !in0);
+            if (lane == 0) {
+                if (m0) atomicXor(&p.bitmap[w0], m0 << sh);
+                if (m1) atomicXor(&p.bitmap[w0 + 1], m1 >> (32 - sh));
+            }
+        }
         v0 += nfit;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kMapCap; i += kSmallThreads) {
+        const uint64_t key = M.key[i];
+        if (key != kMapEmpty) flush_join(p, key, M.hi[i], M.vmin[i]);
     }
 }
 
@@ -206,8 +298,8 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
 void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s) {
     if (p.n <= 0) return;
     const int64_t wv = p.warp_verts > 0 ? p.warp_verts : kDefaultWarpVerts;
-    const int64_t warps = (p.n + wv - 1) / wv;
-    const int64_t blocks = (warps * 32 + kSmallThreads - 1) / kSmallThreads;
+    const int64_t per_cta = wv * kSmallWarps;
+    const int64_t blocks = (p.n + per_cta - 1) / per_cta;
     RoundParams q = p;
     q.warp_verts = (int32_t)wv;
     if (level0)
