@@ -210,7 +210,7 @@ def run_ours(args, rank, world, local):
     dg = kb.DeviceGraph(wl["row_offsets"], wl["col"], wl["elabel"], wl["vlabel"])
     n, m = dg.n, dg.m
     k = args.k
-    opts = kb.Options(direction=kb.DIR_OUT)
+    opts = kb.Options(direction=kb.DIR_OUT, hub_threshold=args.hub_threshold)
     ctx = kb.Context(local)
     levels = torch.empty((k + 1, n), dtype=torch.int32, device=device)
     stream = ctx.stream
@@ -262,7 +262,7 @@ def run_ours(args, rank, world, local):
     del r
 
     # roofline of the dominant kernel family (algorithmic bytes per launch)
-    hub_thr, small_max = 2048, 32
+    hub_thr, small_max = (args.hub_threshold or 2048), 32
     deg = (wl["row_offsets"][1:] - wl["row_offsets"][:-1])
     small = deg <= small_max
     hub = deg > hub_thr
@@ -498,6 +498,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--hub-threshold", type=int, default=0)
     ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     rank, world, local = dist_env()

@@ -22,7 +22,15 @@ constexpr int kStage = 4096;
 constexpr int kSetCap = 8192;  // shared dedup set slots (>= 2 * kStage)
 constexpr int kMaxHubThreshold = kStage - kSplit;
 constexpr int kDefaultHubThreshold = 2048;
-constexpr int kHubChunk = 4096;  // edges per hub-chunk CTA (== kStage)
+#ifndef KB_HUB_CHUNK
+#define KB_HUB_CHUNK 512
+#endif
+#ifndef KB_HUB_THREADS
+#define KB_HUB_THREADS 128
+#endif
+constexpr int kHubChunk = KB_HUB_CHUNK;      // edges per hub-chunk CTA
+constexpr int kHubThreads = KB_HUB_THREADS;  // threads of a hub-chunk CTA
+constexpr int kHubSetCap = 2 * kHubChunk;    // its shared dedup set
 constexpr int kHubFinalThreads = 256;
 constexpr int kProbeLimit = 1 << 22;  // bound on block-table probes per vertex
 constexpr int kSmallDegree = 32;      // vertices with at most this many edges take the warp kernel

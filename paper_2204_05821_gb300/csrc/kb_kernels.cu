@@ -326,10 +326,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
 // memory, then the chunk's distinct pairs go into the hub's global set; pairs
 // new to the hub are appended to its list and summed into its hash.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundParams p) {
+__global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParams p) {
     __shared__ uint64_t s_pair[kHubChunk];
     __shared__ uint64_t s_new[kHubChunk];
-    __shared__ uint32_t s_set[kSetCap];
+    __shared__ uint32_t s_set[kHubSetCap];
     __shared__ uint8_t s_isnew[kHubChunk];
     __shared__ int s_h, s_nuniq, s_nnew;
     __shared__ int64_t s_e0, s_E, s_base;
@@ -349,18 +349,18 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
         s_nnew = 0;
         s_accsum = 0ull;
     }
-    for (int i = tid; i < kSetCap; i += kTileThreads) s_set[i] = 0u;
+    for (int i = tid; i < kHubSetCap; i += kHubThreads) s_set[i] = 0u;
     __syncthreads();
     const int h = s_h;
     const int E = (int)s_E;
     const int64_t e0 = s_e0;
     if (!vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
 
-    for (int base = 0; base < E; base += 4 * kTileThreads) {
+    for (int base = 0; base < E; base += 4 * kHubThreads) {
         int32_t w[4], l[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int le = base + u * kTileThreads + tid;
+            const int le = base + u * kHubThreads + tid;
             if (le < E) {
                 w[u] = __ldcs(p.col + e0 + le);
                 l[u] = p.lab ? __ldcs(p.lab + e0 + le) : 0;
@@ -368,25 +368,25 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int le = base + u * kTileThreads + tid;
+            const int le = base + u * kHubThreads + tid;
             if (le < E) b[u] = __ldg(p.prev + (w[u] & 0x7fffffff));
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int le = base + u * kTileThreads + tid;
+            const int le = base + u * kHubThreads + tid;
             if (le < E) s_pair[le] = pack_pair(l[u], (uint32_t)w[u], b[u]);
         }
     }
     __syncthreads();
 
     // chunk-local distinct pairs, compacted into s_new with one shared atomic per warp
-    for (int base = 0; base < E; base += kTileThreads) {
+    for (int base = 0; base < E; base += kHubThreads) {
         const int le = base + tid;
         bool isu = false;
         uint64_t pr = 0;
         if (le < E) {
             pr = s_pair[le];
-            uint32_t slot = set_slot(pr, 0u) & (kSetCap - 1);
+            uint32_t slot = set_slot(pr, 0u) & (kHubSetCap - 1);
             while (true) {
                 uint32_t cur = s_set[slot];
                 if (cur == 0u) {
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
                     cur = old;
                 }
                 if (s_pair[(int)cur - 1] == pr) break;
-                slot = (slot + 1) & (kSetCap - 1);
+                slot = (slot + 1) & (kHubSetCap - 1);
             }
         }
         const unsigned b = __ballot_sync(kFull, isu);
@@ -414,13 +414,14 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     uint64_t* gset = p.hub_sets + p.hub_set_off[h];
     const uint64_t gmask = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]) - 1;
     uint64_t lacc = 0;
-    // Up to kHubChunk / kTileThreads pairs per thread: issue the first probe of
-    // every pair before waiting on any, then finish the rare collisions.
-    constexpr int kPer = kHubChunk / kTileThreads;
+    // Up to kHubChunk / kHubThreads pairs per thread: the first probe of every
+    // pair is a CAS issued before waiting on any, then the rare collisions are
+    // finished one by one.
+    constexpr int kPer = kHubChunk / kHubThreads;
     uint64_t prs[kPer], slots[kPer], olds[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-        const int i = tid + u * kTileThreads;
+        const int i = tid + u * kHubThreads;
         if (i < nu) {
             prs[u] = s_new[i];
             slots[u] = (pair_mix(prs[u]) >> 17) & gmask;
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     }
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-        const int i = tid + u * kTileThreads;
+        const int i = tid + u * kHubThreads;
         if (i >= nu) continue;
         const uint64_t pr = prs[u];
         uint64_t slot = slots[u], old = olds[u];
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     if ((tid & 31) == 0 && lacc) atomicAdd(reinterpret_cast<unsigned long long*>(&s_accsum), (unsigned long long)lacc);
     __syncthreads();
     // compact the new pairs (one shared atomic per warp)
-    for (int base = 0; base < nu; base += kTileThreads) {
+    for (int base = 0; base < nu; base += kHubThreads) {
         const int i = base + tid;
         const bool keep = i < nu && s_isnew[i];
         const unsigned b = __ballot_sync(kFull, keep);
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(kTileThreads) hub_chunk_kernel(const RoundPara
     }
     __syncthreads();
     uint64_t* list = p.hub_lists + p.hub_list_off[h];
-    for (int i = tid; i < nnew; i += kTileThreads) list[s_base + i] = s_pair[i];
+    for (int i = tid; i < nnew; i += kHubThreads) list[s_base + i] = s_pair[i];
 }
 
 __device__ __forceinline__ bool hub_set_contains(const uint64_t* gset, uint64_t gmask, uint64_t pr) {
@@ -799,7 +800,7 @@ void launch_tile_round(const RoundParams& p, cudaStream_t s) {
 
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s) {
     if (p.n_hubs <= 0 || total_chunks <= 0) return;
-    hub_chunk_kernel<<<(unsigned)total_chunks, kTileThreads, 0, s>>>(p);
+    hub_chunk_kernel<<<(unsigned)total_chunks, kHubThreads, 0, s>>>(p);
 }
 
 void launch_hub_final(const RoundParams& p, cudaStream_t s) {
