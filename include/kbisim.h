@@ -82,7 +82,7 @@ typedef struct {
  *                      count test); later levels are then copies
  *   load_factor        block-table load factor in (0, 0.9]; 0 -> 0.5
  *   hub_threshold      vertices with more edges than this (in the chosen direction)
- *                      take the multi-CTA hub path; 0 -> default; at most 2048
+ *                      take the multi-CTA hub path; 0 -> default 1024; at most 1024
  *   hash_mode          0: full 64-bit signature hash.  1: weak hash of the previous
  *                      block only, which forces collisions (tests the full
  *                      signature compare); results are identical in both modes
@@ -267,7 +267,7 @@ kb_status kb_server_get_stats(kb_server* server, kb_server_stats* stats);
  *   stream   cudaStream_t to run on (NULL = legacy default stream); the call
  *            synchronises it before returning
  *   g        DEVICE CSR as for kb_refine, with n <= KB_NOALLOC_MAX_VERTICES and
- *            no vertex with more than hub_threshold (default 2048) edges
+ *            no vertex with more than hub_threshold (default 1024) edges
  *   opt      direction must be KB_DIR_OUT; use_edge_labels, hash_mode,
  *            hub_threshold and validate are honoured
  *   prev     DEVICE int32[n], canonical ids of level i-1, each in [0, n)

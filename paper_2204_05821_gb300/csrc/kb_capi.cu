@@ -1395,7 +1395,7 @@ kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     int32_t* lev = reinterpret_cast<int32_t*>(ctx->tune_buf);
     std::vector<int64_t> counts((size_t)rounds + 1);
     const float lfs[] = {0.35f, 0.5f, 0.7f};
-    const int32_t thrs[] = {512, 1024, 2048};
+    const int32_t thrs[] = {256, 512, 1024};
     const int32_t wvs[] = {64, 128, 256};
     float best = 1e30f;
     kb_options o = *opt;

@@ -15,13 +15,16 @@ namespace kb {
 // excluded) are staged in shared memory in sub-tiles that hold at most
 // kStage pairs: vertices are grouped by floor(edge prefix / kSplit), so a
 // sub-tile holds < kSplit + hub_threshold <= kStage edges.
-constexpr int kTileVerts = 512;
-constexpr int kTileThreads = 512;
-constexpr int kSplit = 2048;
-constexpr int kStage = 4096;
-constexpr int kSetCap = 8192;  // shared dedup set slots (>= 2 * kStage)
+#ifndef KB_TILE_VERTS
+#define KB_TILE_VERTS 256
+#endif
+constexpr int kTileVerts = KB_TILE_VERTS;
+constexpr int kTileThreads = KB_TILE_VERTS;
+constexpr int kSplit = 4 * KB_TILE_VERTS;
+constexpr int kStage = 8 * KB_TILE_VERTS;
+constexpr int kSetCap = 2 * kStage;  // shared dedup set slots
 constexpr int kMaxHubThreshold = kStage - kSplit;
-constexpr int kDefaultHubThreshold = 2048;
+constexpr int kDefaultHubThreshold = kMaxHubThreshold;
 #ifndef KB_HUB_CHUNK
 #define KB_HUB_CHUNK 512
 #endif

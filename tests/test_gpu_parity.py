@@ -160,14 +160,15 @@ def test_hot_slot_and_hubs(ctx):
 
 
 def test_subtile_boundaries(ctx):
-    # degrees around the sub-tile split and the hub threshold: 2047, 2048
-    # (largest non-hub), 2049 (hub), mixed with zero-degree runs, over several
-    # 512-vertex tiles with a ragged last tile
+    # degrees around the sub-tile split and the default hub threshold (1024):
+    # 1023, 1024 (largest non-hub), 1025 (hub), 32/33 (small/medium edge),
+    # larger hubs, mixed with zero-degree runs, over several tiles with a
+    # ragged last tile
     degs = []
     rng = np.random.Generator(np.random.PCG64(12))
-    for t in range(7):
-        degs += [2047, 0, 0, 2048, 1, 2049, 0] + list(rng.integers(0, 9, size=505))
-    degs = np.array(degs[: 7 * 512 - 137])
+    for t in range(9):
+        degs += [1023, 0, 0, 1024, 1, 1025, 0, 32, 33, 2049, 0] + list(rng.integers(0, 9, size=245))
+    degs = np.array(degs[: 9 * 256 - 77])
     n = degs.shape[0]
     src = np.repeat(np.arange(n), degs)
     dst = rng.integers(0, n, size=src.shape[0])

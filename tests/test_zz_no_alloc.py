@@ -39,7 +39,7 @@ def test_noalloc_round_with_medium_vertices_and_weak_hash():
     rng = np.random.Generator(np.random.PCG64(4))
     n = 20_000
     deg = rng.integers(0, 40, size=n)
-    deg[::97] = rng.integers(33, 2000, size=deg[::97].shape[0])
+    deg[::97] = rng.integers(33, 1000, size=deg[::97].shape[0])
     src = np.repeat(np.arange(n), deg)
     dst = rng.integers(0, 300, size=src.shape[0])
     g = graphgen.from_edges(n, src, dst, rng.integers(0, 3, size=src.shape[0]), rng.integers(0, 4, size=n))
