@@ -109,6 +109,21 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
     const int64_t vb = cta_base + (int64_t)(threadIdx.x >> 5) * p.warp_verts;
     const int64_t ve = min(p.n, vb + p.warp_verts);
 
+    // The next window's row offsets and own blocks are loaded while the
+    // current window works (its start is known once the current one is packed).
+    int64_t pf_a = 0, pf_b = 0;
+    int32_t pf_own = 0;
+    auto prefetch = [&](int64_t w0) {
+        const int64_t vv = w0 + lane;
+        if (vv < ve) {
+            pf_own = p.prev ? p.prev[vv] : 0;
+            if (!kLevel0) {
+                pf_a = p.row[vv];
+                pf_b = p.row[vv + 1];
+            }
+        }
+    };
+    prefetch(vb);
     for (int64_t v0 = vb; v0 < ve;) {
         const int nvw = (int)min((int64_t)32, ve - v0);
         const int64_t v = v0 + lane;
@@ -117,18 +132,20 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
         int64_t a = 0;
         int32_t own = 0;
         bool l0 = kLevel0;
+        const int64_t cur_a = pf_a, cur_b = pf_b;
+        const int32_t cur_own = pf_own;
         if (lane < nvw && vertex_active(p, v)) {
             if (!kLevel0 && vertex_level0(p, v)) {
                 l0 = true;
                 own = p.vlab ? p.vlab[v] : 0;
                 small = true;
             } else if (kLevel0) {
-                own = p.prev ? p.prev[v] : 0;
+                own = cur_own;
                 small = true;
             } else {
-                own = p.prev ? p.prev[v] : 0;
-                a = p.row[v];
-                const int64_t d = p.row[v + 1] - a;
+                own = cur_own;
+                a = cur_a;
+                const int64_t d = cur_b - a;
                 small = d <= p.small_max;
                 cd = small ? (int)d : 0;
             }
@@ -144,6 +161,7 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
         const int nfit = __popc(fit);  // incl is non-decreasing, so the fitting lanes are 0..nfit-1
         const int E = __shfl_sync(kFull, incl, nfit - 1);
         const int start = incl - cd;
+        if (v0 + nfit < ve) prefetch(v0 + nfit);
 
         uint64_t pr = 0;
         int j = 0;
@@ -229,14 +247,17 @@ __global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundP
                 pending = false;
                 continue;
             }
-            // full signature compare with the representative, on this lane
-            bool eq = same_graph(p, rep, v);
-            if (eq) {
-                const int32_t* keys = (l0 && !kLevel0) ? p.vlab : p.prev;
-                eq = (keys ? __ldg(keys + rep) : 0) == own;
+            // full signature compare with the representative, on this lane;
+            // its key and its row offsets are loaded together
+            const int32_t* keys = (l0 && !kLevel0) ? p.vlab : p.prev;
+            const int32_t rkey = keys ? __ldg(keys + rep) : 0;
+            int64_t rb = 0, re = 0;
+            if (!l0) {
+                rb = p.row[rep];
+                re = p.row[(int64_t)rep + 1];
             }
+            bool eq = same_graph(p, rep, v) && rkey == own;
             if (!l0 && eq) {
-                const int64_t rb = p.row[rep], re = p.row[(int64_t)rep + 1];
                 unsigned vfound = 0;
                 for (int64_t e0 = rb; e0 < re && eq; e0 += 4) {
                     uint64_t x[4];
