@@ -39,6 +39,32 @@ WORKLOADS = {
     "tiny": graphgen.CONFIG_TINY,
 }
 METRIC = "k-bisim edges/s per round"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
+# byte of a kernel, from one ncu capture of it on the large recipe at a tenth
+# of the size (profiles/*_large_tenth.md), where its traffic grows in
+# proportion to its units.  Valid only for the kernel source it was measured
+# on: the file's SHA-1 must match.
+TRAFFIC_PER_ALGO_BYTE = {
+    "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "6c52ca547bf641105ae9c03ff7ca462654e7bc17", 5.62),
+    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "753e7fe8cb8c191304179bb3754fa15cf9924a63", 4.353),
+}
+
+
+def traffic_for(kernel, algo_bytes):
+    entry = TRAFFIC_PER_ALGO_BYTE.get(kernel)
+    if not entry:
+        return None
+    import hashlib
+
+    path, sha, ratio = entry
+    try:
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return ratio * algo_bytes
 UNIT = "edges/s"
 
 
@@ -262,7 +288,7 @@ def run_ours(args, rank, world, local):
     del r
 
     # roofline of the dominant kernel family (algorithmic bytes per launch)
-    hub_thr, small_max = (args.hub_threshold or 2048), 32
+    hub_thr, small_max = (args.hub_threshold or 1024), 32
     deg = (wl["row_offsets"][1:] - wl["row_offsets"][:-1])
     small = deg <= small_max
     hub = deg > hub_thr
@@ -288,7 +314,8 @@ def run_ours(args, rank, world, local):
     per_launch_ms = fam_ms[dom] / max(1, fam_n[dom])
     achieved = algo_bytes.get(dom, 0) / (per_launch_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "frac": achieved / peak, "traffic": traffic_for(dom, algo_bytes.get(dom, 0)), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": algo_bytes.get(dom, 0),
                 "kernel_share": {kname: fam_ms[kname] / sum(fam_ms.values()) for kname in fam_ms},
                 "per_launch_ms": {kname: fam_ms[kname] / max(1, fam_n[kname]) for kname in fam_ms}}
     # our kernels per family event: renumbering is 4 kernels; per call add the
@@ -344,7 +371,7 @@ def run_ours(args, rank, world, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": dict(describe(args.workload, cfg, k, "out"),
                                vertex_classes={"small_le32": [n_small, small_edges], "medium": [n_med, med_edges],
-                                               "hub_gt2048": [n_hubs, hub_edges]},
+                                               "hub_gt%d" % hub_thr: [n_hubs, hub_edges]},
                                counts_last_step=counts_last,
                                l2="inputs larger than L2 (CSR %.1f GB); no flush" % ((8 * (n + 1) + 8 * m) / 1e9),
                                parallelism="replicas" if world > 1 else "single GPU",
