@@ -33,6 +33,9 @@ namespace kb {
 namespace {
 
 constexpr int kSmallThreads = 256;
+#ifndef KB_SMALL_MIN_BLOCKS
+#define KB_SMALL_MIN_BLOCKS 5  // caps registers at 48: 40 warps per SM
+#endif
 constexpr int kSmallWarps = kSmallThreads / 32;
 constexpr int kMapCap = 2048;  // joins a CTA can aggregate (>= 2 x its vertices at the default task size)
 constexpr uint64_t kMapEmpty = ~0ull;
@@ -94,7 +97,7 @@ __device__ __forceinline__ void flush_join(const RoundParams& p, uint64_t key, u
 }
 
 template <bool kLevel0>
-__global__ void __launch_bounds__(kSmallThreads) small_round_kernel(const RoundParams p) {
+__global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_round_kernel(const RoundParams p) {
     __shared__ uint64_t s_pairs[kSmallThreads];
     __shared__ JoinMap M;
     const int lane = threadIdx.x & 31;
