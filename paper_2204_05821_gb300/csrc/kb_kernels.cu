@@ -794,6 +794,10 @@ void launch_clear_round(const RoundParams& p, cudaStream_t s) {
 
 void launch_tile_round(const RoundParams& p, cudaStream_t s) {
     if (p.n_med <= 0) return;
+#ifndef KB_MEDIUM_TILE
+    launch_medium_round(p, s);
+    return;
+#endif
     const int64_t blocks = (p.n_med + kTileVerts - 1) / kTileVerts;
     tile_round_kernel<<<(unsigned)blocks, kTileThreads, 0, s>>>(p);
 }
