@@ -219,8 +219,13 @@ def chung_lu_torch(
     g.manual_seed(seed)
     chunk = 1 << 27
 
-    def capped(gamma, cap):
-        return torch.from_numpy(_capped_powerlaw_degrees(n, m, gamma, cap)).to(device)
+    # Cumulative distributions are summed on the host: a floating-point scan on
+    # the device may combine partial sums in a different order from run to run,
+    # which would move a few draws across bin boundaries.
+    def capped_cdf(gamma, cap):
+        c = np.cumsum(_capped_powerlaw_degrees(n, m, gamma, cap))
+        c /= c[-1]
+        return torch.from_numpy(c).to(device)
 
     def draw(cdf, count, out, transform):
         for a in range(0, count, chunk):
@@ -229,9 +234,7 @@ def chung_lu_torch(
             idx = torch.searchsorted(cdf, u, right=True).clamp_(max=cdf.shape[0] - 1)
             transform(a, b, idx)
 
-    d_out = capped(gamma_out, max_out_deg)
-    cdf_out = torch.cumsum(d_out, 0)
-    cdf_out /= cdf_out[-1].clone()
+    cdf_out = capped_cdf(gamma_out, max_out_deg)
     deg_rank = torch.zeros(n, dtype=torch.int64, device=device)
 
     def acc_deg(a, b, idx):
@@ -246,9 +249,7 @@ def chung_lu_torch(
     torch.cumsum(deg, 0, out=row[1:])
     del deg
 
-    d_in = capped(gamma_in, max_in_deg)
-    cdf_in = torch.cumsum(d_in, 0)
-    cdf_in /= cdf_in[-1].clone()
+    cdf_in = capped_cdf(gamma_in, max_in_deg)
     perm_in = torch.randperm(n, generator=g, device=device).to(torch.int32)
     col = torch.empty(m, dtype=torch.int32, device=device)
 
@@ -259,9 +260,8 @@ def chung_lu_torch(
     del perm_in
 
     def zipf_cdf(L, s):
-        p = torch.arange(1, L + 1, dtype=torch.float64, device=device) ** (-s)
-        c = torch.cumsum(p, 0)
-        return c / c[-1]
+        c = np.cumsum(np.arange(1, L + 1, dtype=np.float64) ** (-s))
+        return torch.from_numpy(c / c[-1]).to(device)
 
     el = torch.empty(m, dtype=torch.int32, device=device)
 

@@ -45,6 +45,7 @@ class Options:
     hash_mode: int = 0
     validate: bool = True
     small_task_vertices: int = 0
+    reorder: int = 0  # 0 automatic, 1 off, 2 on
 
     @classmethod
     def schaetzle(cls, **kw) -> "Options":
@@ -67,6 +68,7 @@ class Options:
         o.hash_mode = int(self.hash_mode)
         o.validate = int(bool(self.validate))
         o.small_task_vertices = int(self.small_task_vertices)
+        o.reorder = int(self.reorder)
         return o
 
 

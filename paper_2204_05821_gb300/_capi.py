@@ -47,7 +47,8 @@ class KbOptions(ctypes.Structure):
         ("hash_mode", ctypes.c_int32),
         ("validate", ctypes.c_int32),
         ("small_task_vertices", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("reorder", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 

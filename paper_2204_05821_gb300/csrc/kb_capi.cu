@@ -102,15 +102,16 @@ struct Plan {
     bool labels = false;
     int thr = kb::kDefaultHubThreshold;
     uint64_t cap = 0;
+    bool reorder = false;  // locality order of the gather (RoundParams::perm)
     // hubs (host copies, ascending vertex id)
     std::vector<int32_t> hub_v;
-    std::vector<int64_t> chunk_off, set_off, list_off;
+    std::vector<int64_t> chunk_off, set_off;
     std::vector<int32_t> chunk_hub;
     // layout
     size_t o_rowp = 0, o_colp = 0, o_labp = 0, o_cursor = 0, o_inpref = 0, o_i64tmp = 0;
     size_t csr_bytes = 0;
     size_t o_emin = 0, o_med = 0, o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
-           o_listoff = 0, o_chunkhub = 0, o_acc = 0, o_cnt = 0, o_sets = 0, o_lists = 0;
+           o_chunkhub = 0, o_chunkext = 0, o_perm = 0, o_gat = 0, o_colr = 0, o_hist = 0, o_acc = 0, o_cnt = 0, o_sets = 0;
     size_t total = 0;
 };
 
@@ -145,12 +146,17 @@ void layout_round(Plan& P) {
     P.o_hubv = take(sizeof(int32_t) * H);
     P.o_chunk = take(sizeof(int64_t) * (H + 1));
     P.o_setoff = take(sizeof(int64_t) * (H + 1));
-    P.o_listoff = take(sizeof(int64_t) * (H + 1));
     P.o_chunkhub = take(sizeof(int32_t) * P.chunk_hub.size());
+    P.o_chunkext = take(sizeof(uint64_t) * P.chunk_hub.size());
     P.o_acc = take(sizeof(uint64_t) * H);
     P.o_cnt = take(sizeof(uint32_t) * H);
     P.o_sets = take(sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0));
-    P.o_lists = take(sizeof(uint64_t) * (size_t)(H ? P.list_off[H] : 0));
+    P.o_perm = take(P.reorder ? sizeof(int32_t) * (size_t)P.n : 0);
+    P.o_gat = take(P.reorder ? sizeof(int32_t) * (size_t)P.n : 0);
+    // a reordered copy of the caller's neighbour ids; the library's own in-edge
+    // CSR is reordered in place
+    P.o_colr = take(P.reorder && !needs_in_csr(P.dir) ? sizeof(int32_t) * (size_t)P.m_proc : 0);
+    P.o_hist = take(P.reorder ? sizeof(unsigned long long) * 512 : 0);
     P.total = off;
 }
 
@@ -158,6 +164,7 @@ kb_status check_graph(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     if (!g || !opt) return fail(ctx, KB_ERR_INVALID_ARG, "graph and options must not be NULL");
     if (g->n < 0 || g->m < 0) return fail(ctx, KB_ERR_INVALID_ARG, "negative n or m");
     if (g->n > 2147483646LL) return fail(ctx, KB_ERR_INVALID_ARG, "n exceeds 2^31-2");
+    if (g->m > (1LL << 45)) return fail(ctx, KB_ERR_INVALID_ARG, "m exceeds 2^45");
     if (k < 0) return fail(ctx, KB_ERR_INVALID_ARG, "k must be >= 0");
     if (opt->direction < 0 || opt->direction > 2) return fail(ctx, KB_ERR_INVALID_ARG, "bad direction");
     if (g->n > 0 && !g->row_offsets) return fail(ctx, KB_ERR_INVALID_ARG, "row_offsets is NULL");
@@ -168,6 +175,7 @@ kb_status check_graph(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     if (opt->hub_threshold < 0 || opt->hub_threshold > kb::kMaxHubThreshold)
         return fail(ctx, KB_ERR_INVALID_ARG, "hub_threshold must be in [0, %d]", kb::kMaxHubThreshold);
     if (opt->hash_mode < 0 || opt->hash_mode > 1) return fail(ctx, KB_ERR_INVALID_ARG, "bad hash_mode");
+    if (opt->reorder < 0 || opt->reorder > 2) return fail(ctx, KB_ERR_INVALID_ARG, "reorder must be 0, 1 or 2");
     if (opt->small_task_vertices != 0 && (opt->small_task_vertices < 32 || opt->small_task_vertices > 65536))
         return fail(ctx, KB_ERR_INVALID_ARG, "small_task_vertices must be 0 or in [32, 65536]");
     if (opt->direction == KB_DIR_BOTH && g->m > (int64_t)1 << 62)
@@ -225,7 +233,6 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
     P.hub_v.clear();
     P.chunk_off.assign(1, 0);
     P.set_off.assign(1, 0);
-    P.list_off.assign(1, 0);
     if (P.n == 0 || P.m_proc == 0) return KB_OK;
     const int64_t hmax = std::min<int64_t>(P.n, P.m_proc / (P.thr + 1) + 1);
     const size_t deg_off = align_up(sizeof(int32_t) * (size_t)hmax);
@@ -255,12 +262,10 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
     }
     P.chunk_off.resize((size_t)H + 1);
     P.set_off.resize((size_t)H + 1);
-    P.list_off.resize((size_t)H + 1);
     for (int32_t i = 0; i < H; ++i) {
         const int64_t d = deg[(size_t)i];
         P.chunk_off[(size_t)i + 1] = P.chunk_off[(size_t)i] + (d + kb::kHubChunk - 1) / kb::kHubChunk;
-        P.set_off[(size_t)i + 1] = P.set_off[(size_t)i] + (int64_t)next_pow2((uint64_t)(2 * d));
-        P.list_off[(size_t)i + 1] = P.list_off[(size_t)i] + d;
+        P.set_off[(size_t)i + 1] = P.set_off[(size_t)i] + kb::hub_set_capacity(d);
     }
     P.chunk_hub.resize((size_t)P.chunk_off[(size_t)H]);
     for (int32_t i = 0; i < H; ++i)
@@ -268,12 +273,16 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
     return KB_OK;
 }
 
+// `rounds`: refinement rounds the call runs (decides the automatic locality
+// order); negative for batched and served refinement, which never reorder.
 kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, Plan& P, char** csr_base_out,
-                    bool for_query) {
+                    bool for_query, int rounds) {
     P.n = g->n;
     P.m = g->m;
     P.dir = opt->direction;
     P.m_proc = P.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
+    P.reorder = rounds >= 0 && P.n > 0 && P.m_proc > 0 &&
+                (opt->reorder == 2 || (opt->reorder == 0 && rounds >= 24 && P.m_proc >= ((int64_t)1 << 22)));
     P.labels = opt->use_edge_labels && g->edge_labels != nullptr;
     int thr = opt->hub_threshold ? opt->hub_threshold : ctx->tuned_hub_threshold;
     P.thr = thr > 0 ? thr : kb::kDefaultHubThreshold;
@@ -366,7 +375,7 @@ struct Prepared {
 // Validate, plan, acquire the workspace, bind the round parameters, list the
 // medium vertices and reset the per-call state (block table, empty-signature
 // minima).  Synchronises.
-kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Prepared& R) {
+kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Prepared& R, int rounds) {
     cudaStream_t s = ctx->stream;
     const int64_t n = g->n;
     KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
@@ -397,7 +406,7 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
             base = reinterpret_cast<char*>(ctx->plan_tmp);
         }
     }
-    KB_TRY(make_plan(ctx, g, opt, P, &base, false));
+    KB_TRY(make_plan(ctx, g, opt, P, &base, false, rounds));
     char* ws = nullptr;
     if (ctx->user_ws) {
         KB_TRY(acquire_workspace(ctx, P.total, &ws));
@@ -439,10 +448,9 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
     p.hub_v = reinterpret_cast<const int32_t*>(ws + P.o_hubv);
     p.hub_chunk_off = reinterpret_cast<const int64_t*>(ws + P.o_chunk);
     p.hub_set_off = reinterpret_cast<const int64_t*>(ws + P.o_setoff);
-    p.hub_list_off = reinterpret_cast<const int64_t*>(ws + P.o_listoff);
     p.chunk_hub = reinterpret_cast<const int32_t*>(ws + P.o_chunkhub);
+    p.chunk_ext = reinterpret_cast<const uint64_t*>(ws + P.o_chunkext);
     p.hub_sets = reinterpret_cast<uint64_t*>(ws + P.o_sets);
-    p.hub_lists = reinterpret_cast<uint64_t*>(ws + P.o_lists);
     p.hub_acc = reinterpret_cast<uint64_t*>(ws + P.o_acc);
     p.hub_cnt = reinterpret_cast<uint32_t*>(ws + P.o_cnt);
     R.prefix = reinterpret_cast<uint32_t*>(ws + P.o_prefix);
@@ -453,10 +461,25 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
                                      cudaMemcpyHostToDevice, s));
         KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_setoff, P.set_off.data(), sizeof(int64_t) * (H + 1),
                                      cudaMemcpyHostToDevice, s));
-        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_listoff, P.list_off.data(), sizeof(int64_t) * (H + 1),
-                                     cudaMemcpyHostToDevice, s));
         KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunkhub, P.chunk_hub.data(), sizeof(int32_t) * P.chunk_hub.size(),
                                      cudaMemcpyHostToDevice, s));
+        kb::launch_chunk_ext((int64_t)P.chunk_hub.size(), p.chunk_hub, p.hub_v, p.hub_chunk_off, p.row,
+                             reinterpret_cast<uint64_t*>(ws + P.o_chunkext), s);
+        KB_CUDA(ctx, cudaGetLastError());
+    }
+    if (P.reorder) {
+        // rank vertices by how often they are gathered (the slot array serves as
+        // the count buffer: every round rewrites it) and move the neighbour ids
+        // to those ranks
+        int32_t* perm = reinterpret_cast<int32_t*>(ws + P.o_perm);
+        kb::launch_locality_order(n, P.m_proc, p.col, reinterpret_cast<uint32_t*>(p.slot_of),
+                                  reinterpret_cast<unsigned long long*>(ws + P.o_hist), perm, s);
+        int32_t* colr = needs_in_csr(P.dir) ? const_cast<int32_t*>(p.col) : reinterpret_cast<int32_t*>(ws + P.o_colr);
+        kb::launch_remap_cols(P.m_proc, p.col, perm, colr, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        p.col = colr;
+        p.perm = perm;
+        p.gat = reinterpret_cast<int32_t*>(ws + P.o_gat);
     }
     // medium vertices, once per call
     int32_t* med = reinterpret_cast<int32_t*>(ws + P.o_med);
@@ -557,7 +580,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     }
     cudaStream_t s = ctx->stream;
     Prepared R;
-    KB_TRY(prepare(ctx, g, opt, R));
+    KB_TRY(prepare(ctx, g, opt, R, k - i_start));
     kb::RoundParams& p = R.p;
 
     // ---- the starting level
@@ -570,6 +593,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         counts[i_start] = ctx->h_ctr->count;
     } else {
         kb::launch_fill_i32(row0, n, 0, s);
+        if (p.perm) kb::launch_fill_i32(p.gat, n, 0, s);
         counts[i_start] = 1;
     }
 
@@ -632,7 +656,7 @@ kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, 
     reset_timing(ctx);
     cudaStream_t s = ctx->stream;
     Prepared R;
-    KB_TRY(prepare(ctx, g, opt, R));
+    KB_TRY(prepare(ctx, g, opt, R, -1));
     kb::RoundParams& p = R.p;
 
     // batch scratch
@@ -1106,7 +1130,7 @@ kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
             o.load_factor = sv->cfg.load_factor;
             o.hub_threshold = sv->cfg.hub_threshold;
             o.hash_mode = sv->cfg.hash_mode;
-            SV_TRY(sv, prepare(ctx, &view, &o, sv->R));
+            SV_TRY(sv, prepare(ctx, &view, &o, sv->R, -1));
             sv->bm_ws = sv->R.p.bitmap;
             std::vector<int64_t> voff((size_t)G + 1);
             for (int j = 0; j < G; ++j) voff[(size_t)j] = sv->slots[(size_t)j].vbase;
@@ -1291,7 +1315,7 @@ kb_status kb_workspace_size(kb_context* ctx, const kb_graph* g, const kb_options
     }
     Plan P;
     char* unused = nullptr;
-    KB_TRY(make_plan(ctx, g, opt, P, &unused, true));
+    KB_TRY(make_plan(ctx, g, opt, P, &unused, true, k));
     *bytes = P.total;
     return KB_OK;
 }

@@ -34,6 +34,7 @@ constexpr int kDefaultHubThreshold = kMaxHubThreshold;
 constexpr int kHubChunk = KB_HUB_CHUNK;      // edges per hub-chunk CTA
 constexpr int kHubThreads = KB_HUB_THREADS;  // threads of a hub-chunk CTA
 constexpr int kHubSetCap = 2 * kHubChunk;    // its shared dedup set
+static_assert(kHubChunk < 65536, "a chunk's edge count is packed in 16 bits");
 constexpr int kHubFinalThreads = 256;
 constexpr int kProbeLimit = 1 << 22;  // bound on block-table probes per vertex
 constexpr int kSmallDegree = 32;      // vertices with at most this many edges take the warp kernel
@@ -57,6 +58,13 @@ struct RoundParams {
     const int32_t* col;   // [m_proc] neighbour; bit 31 set for in-edges
     const int32_t* lab;   // [m_proc] edge label or nullptr (all labels 0)
     const int32_t* prev;  // [n] previous level (vertex labels at level 0)
+    // Locality order (optional).  perm[v] is v's position in an order that puts
+    // often-gathered vertices first; col then holds positions instead of ids and
+    // gat holds the previous level in that order (gat[perm[v]] = prev[v]), so
+    // the per-edge gather of neighbour blocks hits a compact, cache-resident
+    // head.  perm == nullptr: col holds ids and the gather reads prev.
+    const int32_t* perm;
+    int32_t* gat;
     int32_t hub_threshold;
     int32_t small_max;    // min(kSmallDegree, hub_threshold)
     int32_t warp_verts;   // vertices per warp task of the small-vertex kernel
@@ -78,10 +86,9 @@ struct RoundParams {
     const int32_t* hub_v;          // [n_hubs] ascending
     const int64_t* hub_chunk_off;  // [n_hubs+1]
     const int32_t* chunk_hub;      // [total chunks] hub index of every chunk
-    const int64_t* hub_set_off;    // [n_hubs+1] power-of-two set per hub
-    const int64_t* hub_list_off;   // [n_hubs+1] unique-pair list per hub
+    const uint64_t* chunk_ext;     // [total chunks] (first edge << 16) | edges of every chunk
+    const int64_t* hub_set_off;    // [n_hubs+1] open-addressing set per hub (hub_set_capacity slots)
     uint64_t* hub_sets;
-    uint64_t* hub_lists;
     uint64_t* hub_acc;  // [n_hubs] sum of pair mixes over unique pairs
     uint32_t* hub_cnt;  // [n_hubs] unique pairs
     // several graphs at once (batched refinement, serving); all null for one graph
@@ -97,6 +104,11 @@ struct RoundParams {
 };
 
 __host__ __device__ __forceinline__ bool batched(const RoundParams& p) { return p.vgraph != nullptr; }
+
+// The array the per-edge gather reads through col (see RoundParams::perm).
+__host__ __device__ __forceinline__ const int32_t* gather_base(const RoundParams& p) {
+    return p.perm ? p.gat : p.prev;
+}
 
 // ---------------------------------------------------------------- hashing
 // SplitMix64 output function (Steele, Lea & Flood, "Fast splittable
@@ -117,6 +129,17 @@ __device__ __forceinline__ uint64_t pack_pair(int32_t label, uint32_t col_word, 
 }
 
 __device__ __forceinline__ uint64_t pair_mix(uint64_t p) { return mix64(p ^ 0x9e3779b97f4a7c15ULL); }
+
+// A hub's global dedup set: 1.5 x its degree (at most two thirds full), any
+// size, home slot by multiply-shift range reduction of the pair mix.
+__host__ __device__ __forceinline__ int64_t hub_set_capacity(int64_t degree) {
+    const int64_t c = degree + degree / 2 + 4;
+    return c < 64 ? 64 : (c & ~(int64_t)3);
+}
+
+__device__ __forceinline__ uint64_t hub_set_home(uint64_t pr, uint64_t cap) {
+    return __umul64hi(pair_mix(pr), cap);
+}
 
 // Slot of (local vertex j, pair p) in a shared dedup set.
 __device__ __forceinline__ uint32_t set_slot(uint64_t p, uint32_t j) {
@@ -179,6 +202,11 @@ void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v
                       int32_t* n_out, cudaStream_t s);
 // Append the vertices with lo < degree <= hi to out (order within a warp
 // preserved); count in *n_out.
+void launch_chunk_ext(int64_t chunks, const int32_t* chunk_hub, const int32_t* hub_v, const int64_t* chunk_off,
+                      const int64_t* row, uint64_t* out, cudaStream_t s);
+void launch_locality_order(int64_t n, int64_t m, const int32_t* col, uint32_t* cnt, unsigned long long* hist,
+                           int32_t* perm, cudaStream_t s);
+void launch_remap_cols(int64_t m, const int32_t* col, const int32_t* perm, int32_t* out, cudaStream_t s);
 void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,
                      cudaStream_t s);
 // Copy row src of the level store to the rows [first, last] of levels.

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (le[u] < E) b[u] = __ldg(p.prev + (w[u] & 0x7fffffff));
+                    if (le[u] < E) b[u] = __ldg(gather_base(p) + (w[u] & 0x7fffffff));
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (le[u] < E) {
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const Round
                         if (e < re) {
                             const int32_t w = __ldg(p.col + e);
                             const int32_t l = p.lab ? __ldg(p.lab + e) : 0;
-                            const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(p.prev + (w & 0x7fffffff)));
+                            const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
                             uint32_t slot = set_slot(pr, (uint32_t)j) & (kSetCap - 1);
                             found = false;
                             while (true) {
@@ -330,31 +330,23 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
     __shared__ uint64_t s_pair[kHubChunk];
     __shared__ uint64_t s_new[kHubChunk];
     __shared__ uint32_t s_set[kHubSetCap];
-    __shared__ uint8_t s_isnew[kHubChunk];
-    __shared__ int s_h, s_nuniq, s_nnew;
-    __shared__ int64_t s_e0, s_E, s_base;
+    __shared__ int s_nuniq, s_nnew;
     __shared__ uint64_t s_accsum;
 
     const int tid = threadIdx.x;
     const int64_t c = blockIdx.x;
+    // every thread reads the chunk's hub and packed extent (one broadcast word each)
+    const int h = p.chunk_hub[c];
+    const uint64_t ext = p.chunk_ext[c];
+    const int64_t e0 = (int64_t)(ext >> 16);
+    const int E = (int)(ext & 0xffffu);
+    if (batched(p) && !vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
     if (tid == 0) {
-        const int lo = p.chunk_hub[c];
-        s_h = lo;
-        const int32_t v = p.hub_v[lo];
-        const int64_t rb = p.row[v], re = p.row[v + 1];
-        const int64_t e0 = rb + (c - p.hub_chunk_off[lo]) * (int64_t)kHubChunk;
-        s_e0 = e0;
-        s_E = min((int64_t)kHubChunk, re - e0);
         s_nuniq = 0;
         s_nnew = 0;
         s_accsum = 0ull;
     }
     for (int i = tid; i < kHubSetCap; i += kHubThreads) s_set[i] = 0u;
-    __syncthreads();
-    const int h = s_h;
-    const int E = (int)s_E;
-    const int64_t e0 = s_e0;
-    if (!vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
 
     for (int base = 0; base < E; base += 4 * kHubThreads) {
         int32_t w[4], l[4], b[4];
@@ -369,7 +361,7 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int le = base + u * kHubThreads + tid;
-            if (le < E) b[u] = __ldg(p.prev + (w[u] & 0x7fffffff));
+            if (le < E) b[u] = __ldg(gather_base(p) + (w[u] & 0x7fffffff));
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -412,8 +404,9 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
     // insert into the hub's global set
     const int nu = s_nuniq;
     uint64_t* gset = p.hub_sets + p.hub_set_off[h];
-    const uint64_t gmask = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]) - 1;
+    const uint64_t gcap = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]);
     uint64_t lacc = 0;
+    uint32_t lnew = 0;
     // Up to kHubChunk / kHubThreads pairs per thread: the first probe of every
     // pair is a CAS issued before waiting on any, then the rare collisions are
     // finished one by one.
@@ -424,7 +417,7 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
         const int i = tid + u * kHubThreads;
         if (i < nu) {
             prs[u] = s_new[i];
-            slots[u] = (pair_mix(prs[u]) >> 17) & gmask;
+            slots[u] = hub_set_home(prs[u], gcap);
             olds[u] = atomicCAS(reinterpret_cast<unsigned long long*>(&gset[slots[u]]),
                                 (unsigned long long)kEmptyPair, (unsigned long long)prs[u]);
         }
@@ -435,50 +428,42 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
         if (i >= nu) continue;
         const uint64_t pr = prs[u];
         uint64_t slot = slots[u], old = olds[u];
-        uint8_t isnew = 0;
-        for (uint64_t t = 0; t <= gmask; ++t) {
-            if (old == kEmptyPair) { isnew = 1; break; }
+        for (uint64_t t = 0; t < gcap; ++t) {
+            if (old == kEmptyPair) {
+                lacc += pair_mix(pr);
+                ++lnew;
+                break;
+            }
             if (old == pr) break;
-            slot = (slot + 1) & gmask;
+            slot = slot + 1 == gcap ? 0 : slot + 1;
             old = atomicCAS(reinterpret_cast<unsigned long long*>(&gset[slot]), (unsigned long long)kEmptyPair,
                             (unsigned long long)pr);
         }
-        s_isnew[i] = isnew;
-        if (isnew) lacc += pair_mix(pr);
     }
-    // CTA hash sum of the pairs new to the hub
+    // CTA sums of the pairs new to the hub: hash and count
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(kFull, lacc, o);
-    if ((tid & 31) == 0 && lacc) atomicAdd(reinterpret_cast<unsigned long long*>(&s_accsum), (unsigned long long)lacc);
-    __syncthreads();
-    // compact the new pairs (one shared atomic per warp)
-    for (int base = 0; base < nu; base += kHubThreads) {
-        const int i = base + tid;
-        const bool keep = i < nu && s_isnew[i];
-        const unsigned b = __ballot_sync(kFull, keep);
-        int wbase = 0;
-        if ((tid & 31) == 0 && b) wbase = atomicAdd(&s_nnew, __popc(b));
-        wbase = __shfl_sync(kFull, wbase, 0);
-        if (keep) s_pair[wbase + __popc(b & ((1u << (tid & 31)) - 1u))] = s_new[i];
+    for (int o = 16; o > 0; o >>= 1) {
+        lacc += __shfl_xor_sync(kFull, lacc, o);
+        lnew += __shfl_xor_sync(kFull, lnew, o);
+    }
+    if ((tid & 31) == 0 && lnew) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&s_accsum), (unsigned long long)lacc);
+        atomicAdd(&s_nnew, (int)lnew);
     }
     __syncthreads();
-    const int nnew = s_nnew;
-    if (tid == 0) {
-        if (nnew) s_base = atomicAdd(&p.hub_cnt[h], (uint32_t)nnew);
-        if (s_accsum) atomicAdd(reinterpret_cast<unsigned long long*>(&p.hub_acc[h]), (unsigned long long)s_accsum);
+    if (tid == 0 && s_nnew) {
+        atomicAdd(&p.hub_cnt[h], (uint32_t)s_nnew);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.hub_acc[h]), (unsigned long long)s_accsum);
     }
-    __syncthreads();
-    uint64_t* list = p.hub_lists + p.hub_list_off[h];
-    for (int i = tid; i < nnew; i += kHubThreads) list[s_base + i] = s_pair[i];
 }
 
-__device__ __forceinline__ bool hub_set_contains(const uint64_t* gset, uint64_t gmask, uint64_t pr) {
-    uint64_t slot = (pair_mix(pr) >> 17) & gmask;
-    for (uint64_t t = 0; t <= gmask; ++t) {
+__device__ __forceinline__ bool hub_set_contains(const uint64_t* gset, uint64_t gcap, uint64_t pr) {
+    uint64_t slot = hub_set_home(pr, gcap);
+    for (uint64_t t = 0; t < gcap; ++t) {
         const uint64_t cur = gset[slot];
         if (cur == pr) return true;
         if (cur == kEmptyPair) return false;
-        slot = (slot + 1) & gmask;
+        slot = slot + 1 == gcap ? 0 : slot + 1;
     }
     return false;
 }
@@ -504,7 +489,7 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
     const uint64_t hv = vertex_hash(own, cnt, p.hub_acc[h], p.hash_mode);
     const uint32_t hi = table_hi(hv, p.epoch);
     const uint64_t* gset = p.hub_sets + p.hub_set_off[h];
-    const uint64_t gmask = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]) - 1;
+    const uint64_t gcap = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]);
     if (tid == 0) s_pos = hv & p.mask;
 
     for (int iter = 0; iter < kProbeLimit; ++iter) {
@@ -530,16 +515,20 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
         const int64_t rb = p.row[r], re = p.row[r + 1];
         if (ok && re - rb > p.hub_threshold) {
             // representative is a hub: compare distinct counts, then look its
-            // distinct pairs up in our set
+            // distinct pairs (the filled slots of its set) up in our set
             int lo = 0, hi2 = p.n_hubs;
             while (hi2 - lo > 1) { int mid = (lo + hi2) >> 1; if (p.hub_v[mid] <= (int32_t)r) lo = mid; else hi2 = mid; }
             const uint32_t cnt_r = p.hub_cnt[lo];
             ok = (cnt_r == cnt);
             if (ok) {
-                const uint64_t* list = p.hub_lists + p.hub_list_off[lo];
+                // its set holds exactly its distinct pairs (and empty slots)
+                const uint64_t* rset = p.hub_sets + p.hub_set_off[lo];
+                const int64_t rcap = p.hub_set_off[lo + 1] - p.hub_set_off[lo];
                 bool all = true;
-                for (uint32_t i = tid; i < cnt_r; i += kHubFinalThreads)
-                    if (!hub_set_contains(gset, gmask, list[i])) all = false;
+                for (int64_t i = tid; i < rcap && all; i += kHubFinalThreads) {
+                    const uint64_t pr = rset[i];
+                    if (pr != kEmptyPair && !hub_set_contains(gset, gcap, pr)) all = false;
+                }
                 if (!all) s_ok = 0;
             } else if (tid == 0) {
                 s_ok = 0;
@@ -554,9 +543,9 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
             for (int i = tid; i < d; i += kHubFinalThreads) {
                 const int32_t w = __ldg(p.col + rb + i);
                 const int32_t l = p.lab ? __ldg(p.lab + rb + i) : 0;
-                const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(p.prev + (w & 0x7fffffff)));
+                const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
                 s_pair[i] = pr;
-                if (!hub_set_contains(gset, gmask, pr)) all = false;
+                if (!hub_set_contains(gset, gcap, pr)) all = false;
             }
             __syncthreads();
             for (int i = tid; i < d; i += kHubFinalThreads) {
@@ -700,7 +689,9 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
         if (!vertex_active(p, v)) {
             const int32_t g = p.vgraph[v];
-            out[v] = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
+            const int32_t b = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
+            out[v] = b;
+            if (p.perm) p.gat[p.perm[v]] = b;
             continue;
         }
         const uint32_t bw = p.bitmap[v >> 5];
@@ -714,7 +705,9 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
             if ((int64_t)mn >= p.n) mn = (uint32_t)v;  // only after a reported device error
         }
         const uint32_t mw = p.bitmap[mn >> 5];
-        out[v] = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
+        const int32_t b = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
+        out[v] = b;
+        if (p.perm) p.gat[p.perm[v]] = b;
     }
 }
 

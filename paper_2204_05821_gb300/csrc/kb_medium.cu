@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kWarps * 32) medium_round_kernel(const RoundPa
             int32_t b[U];
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (e0 + u * 32 + lane < re) b[u] = __ldg(p.prev + (w[u] & 0x7fffffff));
+                if (e0 + u * 32 + lane < re) b[u] = __ldg(gather_base(p) + (w[u] & 0x7fffffff));
             // the next batch's neighbours and labels, issued before the gather is consumed
             int32_t w2[U], l2[U];
             const int64_t e1 = e0 + 32 * U;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kWarps * 32) medium_round_kernel(const RoundPa
                     if (e < rend) {
                         const int32_t ww = __ldg(p.col + e);
                         const int32_t ll = p.lab ? __ldg(p.lab + e) : 0;
-                        const uint64_t pr = pack_pair(ll, (uint32_t)ww, __ldg(p.prev + (ww & 0x7fffffff)));
+                        const uint64_t pr = pack_pair(ll, (uint32_t)ww, __ldg(gather_base(p) + (ww & 0x7fffffff)));
                         uint32_t slot = set_slot(pr, 0u) & cmask;
                         found = false;
                         while (true) {

@@ -90,6 +90,99 @@ __global__ void find_hubs_kernel(int64_t n, const int64_t* row, int32_t thr, int
     }
 }
 
+// Extent of every hub chunk, packed as (first edge << 16) | edge count, so a
+// chunk CTA reads one word instead of a chain of four dependent loads.
+__global__ void chunk_ext_kernel(int64_t chunks, const int32_t* chunk_hub, const int32_t* hub_v,
+                                 const int64_t* chunk_off, const int64_t* row, uint64_t* out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += stride) {
+        const int32_t h = chunk_hub[c];
+        const int32_t v = hub_v[h];
+        const int64_t e0 = row[v] + (c - chunk_off[h]) * (int64_t)kHubChunk;
+        const int64_t len = min((int64_t)kHubChunk, row[(int64_t)v + 1] - e0);
+        out[c] = ((uint64_t)e0 << 16) | (uint64_t)len;
+    }
+}
+
+// ---- locality order (see RoundParams::perm)
+// How often each vertex is gathered: its occurrences in the processed col,
+// counted over runs of 32 edges taken every `stride` edges (all edges when
+// stride == 32).
+__global__ void count_targets_kernel(int64_t m, const int32_t* col, int64_t stride, uint32_t* cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t runs = (m + stride - 1) / stride;
+    for (int64_t r = warp; r < runs; r += nwarps) {
+        const int64_t e = r * stride + lane;
+        if (e < m) atomicAdd(&cnt[col[e] & 0x7fffffff], 1u);
+    }
+}
+
+// 256 classes, about 8 per octave of the count; class 0 = never gathered.
+__device__ __forceinline__ int hot_class(uint32_t c) {
+    if (c == 0) return 0;
+    const int e = 31 - __clz(c);
+    const int frac = e >= 3 ? (int)((c >> (e - 3)) & 7u) : (int)((c << (3 - e)) & 7u);
+    return min(255, 1 + e * 8 + frac);
+}
+
+__global__ void class_hist_kernel(int64_t n, const uint32_t* cnt, unsigned long long* hist) {
+    __shared__ uint32_t h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        atomicAdd(&h[hot_class(cnt[v])], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+
+// cursor[k] = vertices in classes above k (hotter classes come first).
+__global__ void class_base_kernel(const unsigned long long* hist, unsigned long long* cursor) {
+    __shared__ unsigned long long s[256];
+    const int k = threadIdx.x;
+    s[k] = hist[k];
+    __syncthreads();
+    if (k == 0) {
+        unsigned long long run = 0;
+        for (int j = 255; j >= 0; --j) {
+            const unsigned long long c = s[j];
+            s[j] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    cursor[k] = s[k];
+}
+
+// perm[v] = position of v in the class order; one atomic per class and warp.
+__global__ void class_scatter_kernel(int64_t n, const uint32_t* cnt, unsigned long long* cursor, int32_t* perm) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += stride) {
+        const int64_t v = b + threadIdx.x;
+        const bool ok = v < n;
+        const int k = ok ? hot_class(cnt[v]) : 256 + lane;  // lanes past the end match nobody
+        const unsigned grp = __match_any_sync(kFull, k);
+        const int leader = __ffs(grp) - 1;
+        unsigned long long base = 0;
+        if (ok && lane == leader) base = atomicAdd(&cursor[k], (unsigned long long)__popc(grp));
+        base = __shfl_sync(kFull, base, leader);
+        if (ok) perm[v] = (int32_t)(base + __popc(grp & ((1u << lane) - 1u)));
+    }
+}
+
+// Neighbour ids -> positions in the order, keeping the direction bit.
+__global__ void remap_cols_kernel(int64_t m, const int32_t* col, const int32_t* perm, int32_t* out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const int32_t w = col[e];
+        out[e] = (int32_t)((uint32_t)perm[w & 0x7fffffff] | ((uint32_t)w & 0x80000000u));
+    }
+}
+
 __global__ void classify_kernel(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out,
                                 unsigned long long* n_out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -224,6 +317,33 @@ void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v
                       cudaStream_t s) {
     if (n <= 0) return;
     find_hubs_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, row, thr, out_v, out_deg, n_out);
+}
+
+void launch_chunk_ext(int64_t chunks, const int32_t* chunk_hub, const int32_t* hub_v, const int64_t* chunk_off,
+                      const int64_t* row, uint64_t* out, cudaStream_t s) {
+    if (chunks <= 0) return;
+    chunk_ext_kernel<<<grid_for(chunks, 256), 256, 0, s>>>(chunks, chunk_hub, hub_v, chunk_off, row, out);
+}
+
+void launch_locality_order(int64_t n, int64_t m, const int32_t* col, uint32_t* cnt, unsigned long long* hist,
+                           int32_t* perm, cudaStream_t s) {
+    if (n <= 0) return;
+    cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)n, s);
+    cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 512, s);
+    if (m > 0) {
+        // every edge up to 2^26 edges, then one run of 32 in every 256
+        const int64_t stride = m <= ((int64_t)1 << 26) ? 32 : 256;
+        const int64_t runs = (m + stride - 1) / stride;
+        count_targets_kernel<<<grid_for(runs * 32, 256), 256, 0, s>>>(m, col, stride, cnt);
+    }
+    class_hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, hist);
+    class_base_kernel<<<1, 256, 0, s>>>(hist, hist + 256);
+    class_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, cnt, hist + 256, perm);
+}
+
+void launch_remap_cols(int64_t m, const int32_t* col, const int32_t* perm, int32_t* out, cudaStream_t s) {
+    if (m <= 0) return;
+    remap_cols_kernel<<<grid_for(m, 256), 256, 0, s>>>(m, col, perm, out);
 }
 
 void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
                 const int64_t e = aj + (lane - sj);
                 const int32_t w = __ldcs(p.col + e);
                 const int32_t l = p.lab ? __ldcs(p.lab + e) : 0;
-                pr = pack_pair(l, (uint32_t)w, __ldg(p.prev + (w & 0x7fffffff)));
+                pr = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
                 const unsigned act = E == 32 ? kFull : ((1u << E) - 1u);
                 const unsigned m = __match_any_sync(act, (unsigned long long)pr) & __match_any_sync(act, (unsigned)j);
                 if (__ffs(m) - 1 == lane) {
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
                         if (e0 + u < re) {
                             const int32_t w = __ldg(p.col + e0 + u);
                             const int32_t l = p.lab ? __ldg(p.lab + e0 + u) : 0;
-                            x[u] = pack_pair(l, (uint32_t)w, __ldg(p.prev + (w & 0x7fffffff)));
+                            x[u] = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
                         }
                     }
 #pragma unroll

@@ -107,6 +107,42 @@ def test_load_factor_invariance(ctx, er_tiny, lf):
     assert_same(ctx, er_tiny, 0, True, True, 8, load_factor=lf)
 
 
+# ---------------------------------------------------------------- locality order of the gather
+
+
+@pytest.mark.parametrize("reorder", [1, 2])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_locality_order(ctx, er_tiny, d, reorder):
+    # neighbour ids moved to hotness ranks must not change a single level
+    assert_same(ctx, er_tiny, d, True, True, 8, reorder=reorder)
+    assert_same(ctx, er_tiny, d, False, True, 6, reorder=reorder, hash_mode=1)
+    assert_same(ctx, er_tiny, d, True, False, 6, reorder=reorder, hub_threshold=17)
+    assert_same(ctx, er_tiny, d, False, False, 5, early_stop=False, reorder=reorder)
+
+
+@pytest.fixture(scope="module")
+def power_law():
+    # a small Chung-Lu graph: skewed in-degrees (a real hot head) and hubs
+    return graphgen.make(graphgen.scaled(graphgen.CONFIG_RDF, 0.002, seed=21))
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_locality_order_power_law(ctx, power_law, d):
+    for reorder in (1, 2):
+        assert_same(ctx, power_law, d, True, True, 6, reorder=reorder)
+        assert_same(ctx, power_law, d, True, True, 4, reorder=reorder, hub_threshold=40, hash_mode=1)
+
+
+def test_locality_order_resume(ctx, power_law):
+    L, C, _ = oracle.refine_graph(power_law, 0, True, True, k=6, early_stop=False)
+    dg = kb.DeviceGraph.from_numpy(power_law, "cuda:0")
+    for j in (0, 3):
+        start = torch.from_numpy(L[j]).to("cuda:0")
+        res = ctx.refine_from(dg, start, j, 6, kb.Options(early_stop=False, reorder=2))
+        assert np.array_equal(res.levels.cpu().numpy()[j:], L[j:])
+        assert np.array_equal(res.counts[j:], C[j:])
+
+
 # ---------------------------------------------------------------- random small graphs and edge cases
 
 
@@ -116,7 +152,8 @@ def test_random_tiny_graphs(ctx):
         g = graphgen.tiny_random(rng, n_max=40, m_max=120, n_labels=int(rng.integers(1, 4)))
         d = int(rng.integers(0, 3))
         assert_same(ctx, g, d, bool(rng.integers(0, 2)), bool(rng.integers(0, 2)), int(rng.integers(0, 7)),
-                    hash_mode=int(rng.integers(0, 2)), hub_threshold=int(rng.choice([0, 1, 2, 5])))
+                    hash_mode=int(rng.integers(0, 2)), hub_threshold=int(rng.choice([0, 1, 2, 5])),
+                    reorder=int(rng.choice([1, 2])))
 
 
 def test_edge_cases(ctx):
@@ -133,6 +170,7 @@ def test_edge_cases(ctx):
             for k in (0, 1, 5):
                 assert_same(ctx, g, d, True, True, k)
                 assert_same(ctx, g, d, False, False, k, early_stop=False)
+                assert_same(ctx, g, d, True, True, k, reorder=2)
 
 
 def test_extreme_labels(ctx):
@@ -234,5 +272,7 @@ def test_invalid_inputs_rejected(ctx):
         gpu_levels(ctx, bad2, 0, True, True, 3)
     with pytest.raises(kb.KbError):
         gpu_levels(ctx, g, 0, True, True, 3, hub_threshold=5000)
+    with pytest.raises(kb.KbError):
+        gpu_levels(ctx, g, 0, True, True, 3, reorder=3)
     # the context stays usable after errors
     assert_same(ctx, g, 0, True, True, 3)
