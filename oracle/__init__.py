@@ -52,6 +52,8 @@ def _load():
                 ctypes.c_int64, ctypes.c_int64, P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                 ctypes.c_int, ctypes.c_int, P, P, P, P,
             ]
+            lib.oracle_summary.restype = ctypes.c_int64
+            lib.oracle_summary.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
             lib.oracle_count_distinct.restype = ctypes.c_int64
             lib.oracle_count_distinct.argtypes = [ctypes.c_int64, P]
             _lib = lib
@@ -90,6 +92,24 @@ def refine_graph(g, direction=DIR_OUT, use_vertex_labels=True, use_edge_labels=T
     """:func:`refine` on a :class:`graphgen.Graph`."""
     return refine(g.n, g.row_offsets, g.col, g.elabel, g.vlabel, direction, use_vertex_labels,
                   use_edge_labels, k, early_stop, initial)
+
+
+def summary(g, direction, use_edge_labels, src_level, dst_level):
+    """Summary-graph triples of a graph under (src_level, dst_level), as three
+    int32 arrays in order of first occurrence (see oracle_summary)."""
+    lib = _load()
+    row = np.ascontiguousarray(g.row_offsets, dtype=np.int64)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    el = None if g.elabel is None else np.ascontiguousarray(g.elabel, dtype=np.int32)
+    a = np.ascontiguousarray(src_level, dtype=np.int32)
+    b = np.ascontiguousarray(dst_level, dtype=np.int32)
+    m = int(col.shape[0])
+    out = [np.zeros(max(m, 1), dtype=np.int32) for _ in range(3)]
+    cnt = lib.oracle_summary(int(g.n), _ptr(row), _ptr(col), _ptr(el), int(direction), int(bool(use_edge_labels)),
+                             _ptr(a), _ptr(b), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+    if cnt < 0:
+        raise ValueError("oracle_summary takes direction out (0) or in (1)")
+    return tuple(o[:cnt].copy() for o in out)
 
 
 def count_distinct(a) -> int:

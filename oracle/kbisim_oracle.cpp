@@ -24,6 +24,8 @@
 //   * Early stop (Alg. 1, the block-count test and its footnote: blocks only
 //     split): when count_i == count_{i-1} the partition is stable; levels
 //     i+1..k are copies of level i.
+//   * Summary graph (Sec. "Graph Summaries for Bisimulation"): the distinct
+//     (block, label, block) triples over the edges, see oracle_summary.
 //
 // Readings where the paper is silent or ambiguous (each is also listed in the
 // design notes): the key includes the vertex's own previous block (needed once
@@ -35,6 +37,7 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <set>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -153,6 +156,41 @@ int oracle_refine(int64_t n, int64_t m, const int64_t* row, const int32_t* col,
     return oracle_refine_init(n, m, row, col, elabel, vlabel, dir, use_vertex_labels,
                               use_edge_labels, k, early_stop, nullptr, levels, counts,
                               levels_computed);
+}
+
+// Summary graph of a partition (Sec. "Graph Summaries for Bisimulation": one
+// summary vertex per block, a labelled summary edge from block b to block c
+// when the vertices of b have an edge with that label into c).  Every graph
+// edge v -> w with label l yields the triple (src_level[x], l or 0, dst_level[y])
+// where x -> y is the edge in the processed direction (out: x = v, y = w; in:
+// x = w, y = v); the output lists each distinct triple once, in the order of
+// its first occurrence in the edge list (sources ascending, then CSR order).
+// With src_level = P_i and dst_level = P_{i-1} of a stratified refinement this
+// is the paper's layer of summary edges between the two levels; with both the
+// same partition it is the quotient graph.  Returns the number of triples, or
+// -1 for a direction other than out (0) or in (1).
+int64_t oracle_summary(int64_t n, const int64_t* row, const int32_t* col, const int32_t* elabel, int dir,
+                       int use_edge_labels, const int32_t* src_level, const int32_t* dst_level,
+                       int32_t* out_src, int32_t* out_label, int32_t* out_dst) {
+    if (dir != 0 && dir != 1) return -1;
+    std::set<std::tuple<int32_t, int32_t, int32_t>> seen;
+    int64_t count = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t e = row[v]; e < row[v + 1]; ++e) {
+            const int64_t w = col[e];
+            const int64_t x = dir == 0 ? v : w;
+            const int64_t y = dir == 0 ? w : v;
+            const int32_t l = (use_edge_labels && elabel) ? elabel[e] : 0;
+            const std::tuple<int32_t, int32_t, int32_t> t(src_level[x], l, dst_level[y]);
+            if (seen.insert(t).second) {
+                out_src[count] = std::get<0>(t);
+                out_label[count] = std::get<1>(t);
+                out_dst[count] = std::get<2>(t);
+                ++count;
+            }
+        }
+    }
+    return count;
 }
 
 // Number of distinct values of an int32 array (used to count the blocks of a

@@ -1,4 +1,5 @@
-"""Parser for tests/golden/paper_example.txt (the paper's worked example)."""
+"""Parsers for tests/golden/paper_example.txt (the paper's worked example) and
+tests/golden/paper_summary.txt (its summary graphs)."""
 import os
 
 import numpy as np
@@ -46,3 +47,34 @@ def partition(ids):
     for v, b in enumerate(ids):
         blocks.setdefault(int(b), set()).add(v)
     return frozenset(frozenset(s) for s in blocks.values())
+
+
+SUMMARY_GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_summary.txt")
+
+
+def canonical_ids(blocks, n):
+    """Block ids of a partition (a set of frozensets) numbered by smallest member."""
+    ids = np.zeros(n, dtype=np.int32)
+    for rank, b in enumerate(sorted(blocks, key=min)):
+        for v in b:
+            ids[v] = rank
+    return ids
+
+
+def load_summary():
+    """The hand-derived summary graphs: a list of (table, source level, target
+    level, [(source block, label id, target block), ...]).  Label names map to
+    the ids load() gives them; "0" stands for an unlabelled edge."""
+    edges = [line.split() for line in open(GOLDEN) if line.startswith("edge ")]
+    enames = sorted(set(e[3] for e in edges))
+    cases = []
+    for line in open(SUMMARY_GOLDEN):
+        tok = line.split()
+        if not tok or tok[0].startswith("#"):
+            continue
+        if tok[0] == "case":
+            cases.append((tok[1], int(tok[2]), int(tok[3]), []))
+        elif tok[0] == "summary":
+            lab = 0 if tok[2] == "0" else enames.index(tok[2])
+            cases[-1][3].append((int(tok[1]), lab, int(tok[3])))
+    return cases

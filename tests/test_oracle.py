@@ -17,7 +17,7 @@ import pytest
 import graphgen
 import oracle
 from oracle import bruteforce
-from paper_fixture import load, partition
+from paper_fixture import canonical_ids, load, load_summary, partition
 
 
 # ---------------------------------------------------------------- paper tables
@@ -97,6 +97,48 @@ def test_oracle_matches_bruteforce_many():
         src, dst, lab = g.edges()
         ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k)
         assert [r.tolist() for r in L] == ids
+
+
+def _stable(g, d, el, ids):
+    # Paige-Tarjan stability (Def. "relational coarsest partition problem"):
+    # no block holds both a vertex with an edge of some label into some block S
+    # and a vertex without one (per processed direction).
+    src, dst, lab = g.edges()
+    lab = lab if el else np.zeros_like(lab)
+    members = {}
+    for v, b in enumerate(ids):
+        members.setdefault(b, []).append(v)
+    for direction in {0: [0], 1: [1], 2: [0, 1]}[d]:
+        a, b = (src, dst) if direction == 0 else (dst, src)
+        has = set((int(a[i]), int(lab[i]), ids[int(b[i])]) for i in range(len(a)))
+        for (v, l, s) in has:
+            if any((u, l, s) not in has for u in members[ids[v]]):
+                return False
+    return True
+
+
+def test_fixpoint_is_coarsest_stable_refinement():
+    # full bisimulation (Sec. "Bisimulation Variants": iterate until no change):
+    # the oracle's stable level equals the brute-force relation iterated to
+    # its fixpoint, and it is stable in the Paige-Tarjan sense
+    for g, d, vl, el, _ in _random_cases(150, 14):
+        L, C, lc = oracle.refine_graph(g, d, vl, el, k=g.n + 1, early_stop=True)
+        src, dst, lab = g.edges()
+        ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, g.n + 1)
+        assert ids[-1] == ids[-2]  # the relation reached its fixpoint
+        assert L[lc].tolist() == ids[-1]
+        assert lc <= g.n
+        assert _stable(g, d, el, ids[-1])
+        if lc >= 2:
+            # the level two before the stop was still split by the next round
+            assert not _stable(g, d, el, L[lc - 2].tolist())
+
+
+def test_stability_check_catches_unstable_partition():
+    # the path 0 -> 1 -> 2: {0, 1, 2} is unstable (2 has no out-edge)
+    g = graphgen.path_graph(3)
+    assert not _stable(g, 0, False, [0, 0, 0])
+    assert _stable(g, 0, False, [0, 1, 2])
 
 
 def test_bruteforce_relation_is_equivalence():
@@ -296,3 +338,85 @@ def test_unmutated_copy_agrees():
         ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k)
         got = _mutant_refine(g, d, vl, el, k, None)
         assert [list(x) for x in got] == ids
+
+
+# ---------------------------------------------------------------- summary graph
+
+
+def test_summary_paper_example():
+    # hand-derived summary graphs of the running example (Section 3.4)
+    g, tables = load()
+    for table, i_src, i_dst, expected in load_summary():
+        t = tables[table]
+        a = canonical_ids(t["levels"][i_src], g.n)
+        b = canonical_ids(t["levels"][i_dst], g.n)
+        s, lab, d = oracle.summary(g, t["direction"], t["use_edge_labels"], a, b)
+        assert list(zip(s.tolist(), lab.tolist(), d.tolist())) == expected, table
+
+
+def _first_occurrence(triples):
+    # numpy: distinct rows, ordered by the index of their first occurrence
+    if len(triples) == 0:
+        return np.zeros((0, 3), dtype=np.int64)
+    u, first = np.unique(triples, axis=0, return_index=True)
+    return u[np.argsort(first, kind="stable")]
+
+
+def test_summary_identity_and_trivial_partitions():
+    for g, d, _, el, _ in itertools.islice(_random_cases(200, 15), 200):
+        if d == 2:
+            continue
+        src, dst, lab = g.edges()
+        lab = lab if el else np.zeros_like(lab)
+        ident = np.arange(g.n, dtype=np.int32)
+        x, y = (src, dst) if d == 0 else (dst, src)
+        expect = _first_occurrence(np.stack([x, lab, y], axis=1))
+        s, l, t = oracle.summary(g, d, el, ident, ident)
+        assert np.array_equal(np.stack([s, l, t], axis=1), expect)
+        zero = np.zeros(g.n, dtype=np.int32)
+        s, l, t = oracle.summary(g, d, el, zero, zero)
+        labs = _first_occurrence(lab.reshape(-1, 1)).reshape(-1)
+        assert s.tolist() == [0] * len(labs) and t.tolist() == [0] * len(labs) and l.tolist() == labs.tolist()
+
+
+def test_summary_edges_hold_for_every_represented_vertex():
+    # the paper's description: a summary edge (b, l, c) means every vertex of b
+    # has an l-edge into c.  For the layering P_i -> P_{i-1} of a bisimulation
+    # refinement that holds, because the vertices of a block of P_i share
+    # their signature over P_{i-1}.
+    for g, d, vl, el, k in itertools.islice(_random_cases(300, 16), 300):
+        if d == 2 or k == 0:
+            continue
+        L, _, _ = oracle.refine_graph(g, d, vl, el, k=k, early_stop=False)
+        src, dst, lab = g.edges()
+        lab = lab if el else np.zeros_like(lab)
+        x, y = (src, dst) if d == 0 else (dst, src)
+        for i in range(1, k + 1):
+            s, l, t = oracle.summary(g, d, el, L[i], L[i - 1])
+            have = set(zip(x.tolist(), lab.tolist(), L[i - 1][y].tolist()))
+            for b, ll, c in zip(s.tolist(), l.tolist(), t.tolist()):
+                for v in np.nonzero(L[i] == b)[0].tolist():
+                    assert (v, ll, c) in have
+            assert len(s) <= g.m
+
+
+def test_summary_in_direction_reverses_out():
+    for g, _, vl, el, k in itertools.islice(_random_cases(100, 17), 100):
+        L, _, _ = oracle.refine_graph(g, 0, vl, el, k=k, early_stop=False)
+        P = L[k]
+        so, lo, do = oracle.summary(g, 0, el, P, P)
+        si, li, di = oracle.summary(g, 1, el, P, P)
+        assert set(zip(di.tolist(), li.tolist(), si.tolist())) == set(zip(so.tolist(), lo.tolist(), do.tolist()))
+
+
+def test_summary_follows_block_renaming():
+    rng = np.random.Generator(np.random.PCG64(18))
+    for g, d, vl, el, k in itertools.islice(_random_cases(60, 19), 60):
+        if d == 2:
+            continue
+        L, _, _ = oracle.refine_graph(g, d, vl, el, k=k, early_stop=False)
+        P = L[k]
+        perm = rng.permutation(g.n).astype(np.int32) - 5  # any int32 ids, negatives included
+        s, l, t = oracle.summary(g, d, el, P, P)
+        s2, l2, t2 = oracle.summary(g, d, el, perm[P], perm[P])
+        assert np.array_equal(s2, perm[s]) and np.array_equal(l2, l) and np.array_equal(t2, perm[t])
