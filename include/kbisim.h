@@ -163,6 +163,54 @@ kb_status kb_refine_from(kb_context* ctx, const kb_graph* g, const kb_options* o
                          const int32_t* start, int i_start, int k, int32_t* levels,
                          int64_t* counts, int* levels_computed);
 
+/* Full (unstratified) bisimulation: refine until a round leaves the partition
+ * unchanged, as Schaetzle et al. do (Sec. "Bisimulation Variants": they iterate
+ * until no further change instead of stopping after k rounds), keeping only
+ * the last two levels instead of k+1 rows.  With an initial partition this is
+ * the coarsest stable refinement of P_0 (Def. "relational coarsest partition
+ * problem", Sec. "Native Kaushik et al. Algorithm"), here for the direction and
+ * labels of `opt`.
+ *   initial      DEVICE int32[n] or NULL; starting partition (equal values = same
+ *                block).  NULL: vertex labels (opt->use_vertex_labels) or {V}.
+ *   max_rounds   upper bound on rounds (>= 0); stops earlier when stable
+ *   final_level  DEVICE int32[n], caller-owned; the last partition, canonical ids
+ *   count        HOST; blocks of final_level
+ *   rounds       HOST; rounds run (a stable run's last round reproduced its input)
+ *   stable       HOST, may be NULL; 1 when a round found the partition stable
+ *                (always when n == 0), 0 when max_rounds ran out first
+ * opt->early_stop is ignored (the run always stops at stability).  Uses 8 B x n
+ * of library scratch besides the refinement workspace.  Synchronises. */
+kb_status kb_refine_fixpoint(kb_context* ctx, const kb_graph* g, const kb_options* opt,
+                             const int32_t* initial, int max_rounds, int32_t* final_level,
+                             int64_t* count, int* rounds, int* stable);
+
+/* Summary graph of a partition pair (Sec. "Graph Summaries for Bisimulation":
+ * one summary vertex per block, a labelled edge from block b to block c when
+ * the vertices of b have an edge with that label into c).  Every graph edge
+ * v -> w with label l gives the triple (src_level[x], l, dst_level[y]), x -> y
+ * being the edge in `direction` (out: x = v, y = w; in: x = w, y = v); the
+ * output lists each distinct triple once, in order of its first occurrence in
+ * the edge list (sources ascending, then CSR order).
+ * With src_level = P_i and dst_level = P_{i-1} of one refinement this is the
+ * paper's layer of summary edges between the two levels, and then every vertex
+ * of b has the edge (its signature over P_{i-1} is its block's); with both the
+ * same partition it is the quotient graph (an edge when some vertex has one).
+ *   g                  DEVICE CSR as for kb_refine, m < 2^32; ids are validated
+ *   direction          KB_DIR_OUT or KB_DIR_IN (call twice for both)
+ *   use_edge_labels    0: every label reads 0 (g->edge_labels may be NULL)
+ *   src_level, dst_level DEVICE int32[n]: block of every vertex; any int32 values
+ *   out_src, out_label, out_dst DEVICE int32[capacity] each, caller-owned
+ *   capacity           entries the outputs hold; m always suffices; 0 with NULL
+ *                      outputs counts only
+ *   count              HOST; the number of summary edges, set also when the
+ *                      outputs are too small (then KB_ERR_INVALID_ARG, outputs
+ *                      untouched)
+ * Scratch: about 24 B x next_pow2(1.25 m) + m/4 B from the stream-ordered
+ * allocator, released before return.  Synchronises. */
+kb_status kb_summary(kb_context* ctx, const kb_graph* g, int direction, int use_edge_labels,
+                     const int32_t* src_level, const int32_t* dst_level, int32_t* out_src,
+                     int32_t* out_label, int32_t* out_dst, int64_t capacity, int64_t* count);
+
 /* kb_refine with HOST buffers: g's arrays and `levels` (int32[(k+1)*n]) are host
  * memory (pinned memory copies fastest).  The library copies the graph to the
  * device, refines, and copies every level back.  Synchronises. */

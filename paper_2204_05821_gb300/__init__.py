@@ -185,7 +185,7 @@ class Context:
         import torch
 
         key = (graph.row_offsets.data_ptr(), graph.n, graph.m, options.direction, options.hub_threshold,
-               options.load_factor, options.use_edge_labels)
+               options.load_factor, options.use_edge_labels, options.reorder, k)
         if self._ws is not None and self._ws_key == key:
             return
         need = self.workspace_size(graph, k, options)
@@ -225,6 +225,56 @@ class Context:
                                              ctypes.c_void_p(start.data_ptr()), int(i_start), int(k),
                                              ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts), ctypes.byref(lc)))
         return Result(levels, counts, int(lc.value))
+
+    def refine_fixpoint(self, graph: DeviceGraph, max_rounds: int, options: Options = None, initial=None, out=None):
+        """kb_refine_fixpoint: refine until stable (full bisimulation, or the
+        coarsest stable refinement of ``initial``).  Returns
+        ``(final_level, count, rounds, stable)``."""
+        import torch
+
+        options = options or Options()
+        self._prepare_workspace(graph, max_rounds, options)
+        final = out if out is not None else torch.empty(graph.n, dtype=torch.int32, device=graph.device)
+        cnt, rounds, stable = ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_int(0)
+        g, o = graph.to_c(), options.to_c()
+        init = ctypes.c_void_p(initial.data_ptr()) if initial is not None else None
+        self._check(self._lib.kb_refine_fixpoint(self._h, ctypes.byref(g), ctypes.byref(o), init, int(max_rounds),
+                                                 ctypes.c_void_p(final.data_ptr()), ctypes.byref(cnt),
+                                                 ctypes.byref(rounds), ctypes.byref(stable)))
+        return final, int(cnt.value), int(rounds.value), bool(stable.value)
+
+    def summary(self, graph: DeviceGraph, src_level, dst_level=None, direction: int = DIR_OUT,
+                use_edge_labels: bool = True, capacity: int = None):
+        """kb_summary: the summary graph of (src_level, dst_level) as three
+        int32 device tensors (source block, label, target block) in order of
+        first occurrence.  dst_level defaults to src_level (quotient graph)."""
+        import torch
+
+        if dst_level is None:
+            dst_level = src_level
+        cap = graph.m if capacity is None else int(capacity)
+        outs = [torch.empty(max(cap, 1), dtype=torch.int32, device=graph.device) for _ in range(3)]
+        cnt = ctypes.c_int64(0)
+        g = graph.to_c()
+        self._check(self._lib.kb_summary(self._h, ctypes.byref(g), int(direction), int(bool(use_edge_labels)),
+                                         ctypes.c_void_p(src_level.data_ptr()), ctypes.c_void_p(dst_level.data_ptr()),
+                                         *[ctypes.c_void_p(o.data_ptr()) for o in outs], cap, ctypes.byref(cnt)))
+        c = int(cnt.value)
+        return tuple(o[:c] for o in outs)
+
+    def summary_count(self, graph: DeviceGraph, src_level, dst_level=None, direction: int = DIR_OUT,
+                      use_edge_labels: bool = True) -> int:
+        """Number of summary edges only (kb_summary with capacity 0)."""
+        if dst_level is None:
+            dst_level = src_level
+        cnt = ctypes.c_int64(0)
+        g = graph.to_c()
+        st = self._lib.kb_summary(self._h, ctypes.byref(g), int(direction), int(bool(use_edge_labels)),
+                                  ctypes.c_void_p(src_level.data_ptr()), ctypes.c_void_p(dst_level.data_ptr()),
+                                  None, None, None, 0, ctypes.byref(cnt))
+        if st != 0 and not (st == 1 and cnt.value > 0):
+            self._check(st)
+        return int(cnt.value)
 
     def refine_host(self, row_offsets, col, elabel, vlabel, k: int, options: Options = None, out=None) -> Result:
         """kb_refine_host: numpy (ideally pinned) host arrays in and out."""

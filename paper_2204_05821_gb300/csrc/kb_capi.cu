@@ -49,6 +49,9 @@ struct kb_context {
     size_t batch_ws_bytes = 0;
     void* tune_buf = nullptr;
     size_t tune_buf_bytes = 0;
+    // fixpoint refinement: the last two levels
+    void* fix_buf = nullptr;
+    size_t fix_buf_bytes = 0;
     cudaStream_t cap_stream = nullptr;  // non-default stream used only to capture CUDA graphs
     // timing
     bool timing = false;
@@ -563,19 +566,30 @@ void reset_timing(kb_context* ctx) {
     }
 }
 
-// The refinement driver shared by kb_refine and kb_refine_from.
-kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
-                      int k, int32_t* levels, int64_t* counts, int* levels_computed) {
-    KB_TRY(check_graph(ctx, g, opt, k));
-    if (i_start < 0 || i_start > k) return fail(ctx, KB_ERR_INVALID_ARG, "i_start must be in [0, k]");
-    if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
-    if (g->n > 0 && !levels) return fail(ctx, KB_ERR_INVALID_ARG, "levels is NULL");
-    KB_CUDA(ctx, cudaSetDevice(ctx->device));
-    reset_timing(ctx);
+// Where the levels go: the caller's (k+1) x n array, or (fixpoint mode, levels
+// == nullptr) two library buffers used in turn.
+struct LevelRows {
+    int32_t* levels = nullptr;
+    int32_t* ping[2] = {nullptr, nullptr};
+    int64_t n = 0;
+    int32_t* row(int i) const { return levels ? levels + (size_t)i * (size_t)n : ping[i & 1]; }
+};
+
+// The refinement driver shared by kb_refine, kb_refine_from and
+// kb_refine_fixpoint.  counts (k+1 entries) may be NULL in fixpoint mode;
+// *last_count receives the block count of the last level computed and
+// *stopped_stable whether a round reproduced its input partition.
+kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
+                      int k, const LevelRows& rows, int64_t* counts, int* levels_computed, int64_t* last_count,
+                      bool* stopped_stable = nullptr) {
     const int64_t n = g->n;
+    const bool fixpoint = rows.levels == nullptr;
     if (levels_computed) *levels_computed = i_start;
+    if (stopped_stable) *stopped_stable = false;
     if (n == 0) {
-        for (int i = i_start; i <= k; ++i) counts[i] = 0;
+        if (counts)
+            for (int i = i_start; i <= k; ++i) counts[i] = 0;
+        if (last_count) *last_count = 0;
         return KB_OK;
     }
     cudaStream_t s = ctx->stream;
@@ -584,26 +598,28 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     kb::RoundParams& p = R.p;
 
     // ---- the starting level
-    int32_t* row0 = levels + (size_t)i_start * (size_t)n;
+    int32_t* row0 = rows.row(i_start);
     const int32_t* init_key = start ? start : (opt->use_vertex_labels ? g->vertex_labels : nullptr);
+    int64_t prev_count = 1;
     if (init_key) {
         KB_TRY(launch_level0(ctx, R, init_key, row0, s));
         KB_TRY(read_counters(ctx));
         KB_TRY(device_error(ctx));
-        counts[i_start] = ctx->h_ctr->count;
+        prev_count = ctx->h_ctr->count;
     } else {
         kb::launch_fill_i32(row0, n, 0, s);
         if (p.perm) kb::launch_fill_i32(p.gat, n, 0, s);
-        counts[i_start] = 1;
     }
+    if (counts) counts[i_start] = prev_count;
+    if (last_count) *last_count = prev_count;
 
     // ---- refinement rounds
     for (int i = i_start + 1; i <= k; ++i) {
         Timer T(ctx);
         KB_TRY(next_epoch(ctx, R, s));
         p.ehigh = 0xffffffffu - (uint32_t)(i - i_start);
-        p.prev = levels + (size_t)(i - 1) * (size_t)n;
-        int32_t* out = levels + (size_t)i * (size_t)n;
+        p.prev = rows.row(i - 1);
+        int32_t* out = rows.row(i);
         KB_TRY(launch_round_body(ctx, R, s, &T));
         T.begin(KB_KERNEL_RENUMBER);
         kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
@@ -612,16 +628,153 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         KB_TRY(read_counters(ctx));
         ctx->round_ms.push_back(T.collect());
         KB_TRY(device_error(ctx));
-        counts[i] = ctx->h_ctr->count;
+        const int64_t c = ctx->h_ctr->count;
+        if (counts) counts[i] = c;
+        if (last_count) *last_count = c;
         if (levels_computed) *levels_computed = i;
-        if (opt->early_stop && counts[i] == counts[i - 1]) {
-            if (i < k) kb::launch_copy_rows(levels, n, i, i + 1, k, s);
-            for (int j = i + 1; j <= k; ++j) counts[j] = counts[i];
+        if ((opt->early_stop || fixpoint) && c == prev_count) {
+            // blocks only split, so an unchanged count means an unchanged partition
+            if (stopped_stable) *stopped_stable = true;
+            if (!fixpoint && i < k) kb::launch_copy_rows(rows.levels, n, i, i + 1, k, s);
+            if (counts)
+                for (int j = i + 1; j <= k; ++j) counts[j] = c;
             KB_CUDA(ctx, cudaGetLastError());
             break;
         }
+        prev_count = c;
     }
     KB_CUDA(ctx, cudaStreamSynchronize(s));
+    return KB_OK;
+}
+
+kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
+                      int k, int32_t* levels, int64_t* counts, int* levels_computed) {
+    KB_TRY(check_graph(ctx, g, opt, k));
+    if (i_start < 0 || i_start > k) return fail(ctx, KB_ERR_INVALID_ARG, "i_start must be in [0, k]");
+    if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
+    if (g->n > 0 && !levels) return fail(ctx, KB_ERR_INVALID_ARG, "levels is NULL");
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    reset_timing(ctx);
+    LevelRows rows;
+    rows.levels = levels;
+    rows.n = g->n;
+    return refine_core(ctx, g, opt, start, i_start, k, rows, counts, levels_computed, nullptr);
+}
+
+// Summary graph of (src_level, dst_level): distinct triples in order of first
+// occurrence (see kb_summary in kbisim.h).  Scratch comes from the
+// stream-ordered allocator and is released before returning.
+kb_status summary_impl(kb_context* ctx, const kb_graph* g, int direction, int use_edge_labels,
+                       const int32_t* src_level, const int32_t* dst_level, int32_t* out_src, int32_t* out_label,
+                       int32_t* out_dst, int64_t capacity, int64_t* count) {
+    if (!g || !count) return fail(ctx, KB_ERR_INVALID_ARG, "graph and count must not be NULL");
+    if (g->n < 0 || g->m < 0 || g->n > 2147483646LL) return fail(ctx, KB_ERR_INVALID_ARG, "bad n or m");
+    if (g->m >= ((int64_t)1 << 32)) return fail(ctx, KB_ERR_INVALID_ARG, "the summary graph takes m < 2^32");
+    if (direction != KB_DIR_OUT && direction != KB_DIR_IN)
+        return fail(ctx, KB_ERR_INVALID_ARG, "direction must be out or in (call once per direction)");
+    if (capacity < 0) return fail(ctx, KB_ERR_INVALID_ARG, "negative capacity");
+    if (g->n > 0 && (!g->row_offsets || !src_level || !dst_level))
+        return fail(ctx, KB_ERR_INVALID_ARG, "row_offsets and levels must not be NULL");
+    if (g->m > 0 && !g->col_indices) return fail(ctx, KB_ERR_INVALID_ARG, "col_indices is NULL");
+    if (capacity > 0 && (!out_src || !out_label || !out_dst))
+        return fail(ctx, KB_ERR_INVALID_ARG, "output arrays must not be NULL when capacity > 0");
+    *count = 0;
+    if (g->m == 0) return KB_OK;
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const int64_t m = g->m;
+    const uint64_t cap = std::max<uint64_t>(1024, next_pow2((uint64_t)(m + m / 4 + 64)));
+    const int64_t nw = (m >> 5) + 1;
+    const size_t sz_table = 16 * (size_t)cap, sz_first = 8 * (size_t)cap, sz_bitmap = 4 * (size_t)nw,
+                 sz_prefix = 4 * (size_t)(nw + 1), sz_scan = 4 * kb::scan_tmp_words(nw);
+    const size_t total = align_up(sz_table) + align_up(sz_first) + align_up(sz_bitmap) + align_up(sz_prefix) +
+                         align_up(sz_scan);
+    char* base = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&base), total, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KB_ERR_OOM, "cannot allocate %zu bytes for the summary graph", total);
+    }
+    kb::SummaryParams q{};
+    q.n = g->n;
+    q.m = m;
+    q.row = g->row_offsets;
+    q.col = g->col_indices;
+    q.lab = use_edge_labels ? g->edge_labels : nullptr;
+    q.dir = direction;
+    q.lsrc = src_level;
+    q.ldst = dst_level;
+    size_t off = 0;
+    q.table = reinterpret_cast<unsigned long long*>(base + off);
+    off += align_up(sz_table);
+    q.first = reinterpret_cast<unsigned long long*>(base + off);
+    off += align_up(sz_first);
+    q.bitmap = reinterpret_cast<uint32_t*>(base + off);
+    off += align_up(sz_bitmap);
+    uint32_t* prefix = reinterpret_cast<uint32_t*>(base + off);
+    off += align_up(sz_prefix);
+    uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(base + off);
+    q.mask = cap - 1;
+    q.ctr = ctx->d_ctr;
+    kb_status st = KB_OK;
+    auto run = [&]() -> kb_status {
+        KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+        KB_CUDA(ctx, cudaMemsetAsync(q.table, 0, sz_table, s));
+        KB_CUDA(ctx, cudaMemsetAsync(q.first, 0xff, sz_first, s));
+        KB_CUDA(ctx, cudaMemsetAsync(q.bitmap, 0, sz_bitmap, s));
+        kb::launch_validate(g->n, m, g->row_offsets, g->col_indices, ctx->d_ctr, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_TRY(read_counters(ctx));
+        KB_TRY(device_error(ctx));
+        kb::launch_summary_insert(q, s);
+        kb::launch_summary_mark(q, s);
+        kb::launch_bitmap_rank(q.bitmap, nw, scan_tmp, prefix, ctx->d_ctr, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_TRY(read_counters(ctx));
+        if (ctx->h_ctr->err & kb::kErrTableFull) return fail(ctx, KB_ERR_TABLE_FULL, "summary table probe limit reached");
+        KB_TRY(device_error(ctx));
+        *count = ctx->h_ctr->count;
+        if (*count > capacity)
+            return fail(ctx, KB_ERR_INVALID_ARG, "capacity %lld is below the %lld summary edges", (long long)capacity,
+                        (long long)*count);
+        kb::launch_summary_emit(q, prefix, out_src, out_label, out_dst, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        return KB_OK;
+    };
+    st = run();
+    cudaFreeAsync(base, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == KB_OK) st = fail(ctx, KB_ERR_CUDA, "summary graph failed");
+    return st;
+}
+
+// Rounds until the partition is stable (or max_rounds), keeping only the
+// last two levels.
+kb_status fixpoint_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* initial,
+                        int max_rounds, int32_t* final_level, int64_t* count, int* rounds, int* stable) {
+    KB_TRY(check_graph(ctx, g, opt, max_rounds));
+    if (!count || !rounds) return fail(ctx, KB_ERR_INVALID_ARG, "count and rounds must not be NULL");
+    if (g->n > 0 && !final_level) return fail(ctx, KB_ERR_INVALID_ARG, "final_level is NULL");
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    reset_timing(ctx);
+    const int64_t n = g->n;
+    LevelRows rows;
+    rows.n = n;
+    if (n > 0) {
+        const size_t half = (sizeof(int32_t) * (size_t)n + 255) & ~(size_t)255;
+        KB_TRY(ensure_buffer(ctx, &ctx->fix_buf, &ctx->fix_buf_bytes, 2 * half));
+        rows.ping[0] = reinterpret_cast<int32_t*>(ctx->fix_buf);
+        rows.ping[1] = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(ctx->fix_buf) + half);
+    }
+    int last = 0;
+    int64_t c = 0;
+    bool st = false;
+    KB_TRY(refine_core(ctx, g, opt, initial, 0, max_rounds, rows, nullptr, &last, &c, &st));
+    *rounds = last;
+    *count = c;
+    if (stable) *stable = (st || n == 0) ? 1 : 0;
+    if (n == 0) return KB_OK;
+    KB_CUDA(ctx, cudaMemcpyAsync(final_level, rows.row(last), sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+    KB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return KB_OK;
 }
 
@@ -1296,6 +1449,7 @@ kb_status kb_destroy(kb_context* ctx) {
     cudaFree(ctx->stage);
     cudaFree(ctx->batch_ws);
     cudaFree(ctx->tune_buf);
+    cudaFree(ctx->fix_buf);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -1338,6 +1492,20 @@ kb_status kb_refine_from(kb_context* ctx, const kb_graph* g, const kb_options* o
     if (!ctx) return KB_ERR_INVALID_ARG;
     if (!start && g && g->n > 0) return fail(ctx, KB_ERR_INVALID_ARG, "start is NULL");
     return refine_impl(ctx, g, opt, start, i_start, k, levels, counts, levels_computed);
+}
+
+kb_status kb_summary(kb_context* ctx, const kb_graph* g, int direction, int use_edge_labels,
+                     const int32_t* src_level, const int32_t* dst_level, int32_t* out_src, int32_t* out_label,
+                     int32_t* out_dst, int64_t capacity, int64_t* count) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    return summary_impl(ctx, g, direction, use_edge_labels, src_level, dst_level, out_src, out_label, out_dst,
+                        capacity, count);
+}
+
+kb_status kb_refine_fixpoint(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* initial,
+                             int max_rounds, int32_t* final_level, int64_t* count, int* rounds, int* stable) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    return fixpoint_impl(ctx, g, opt, initial, max_rounds, final_level, count, rounds, stable);
 }
 
 kb_status kb_refine_host(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k, int32_t* levels,

@@ -207,6 +207,29 @@ void launch_chunk_ext(int64_t chunks, const int32_t* chunk_hub, const int32_t* h
 void launch_locality_order(int64_t n, int64_t m, const int32_t* col, uint32_t* cnt, unsigned long long* hist,
                            int32_t* perm, cudaStream_t s);
 void launch_remap_cols(int64_t m, const int32_t* col, const int32_t* perm, int32_t* out, cudaStream_t s);
+// Rank of every set bit of a bitmap: prefix[w] = set bits before word w, the
+// total in ctr->count (kb_kernels.cu).
+void launch_bitmap_rank(const uint32_t* bitmap, int64_t nw, uint32_t* scan_tmp, uint32_t* prefix, Counters* ctr,
+                        cudaStream_t s);
+// Summary graph (kb_summary.cu)
+struct SummaryParams {
+    int64_t n, m;
+    const int64_t* row;         // [n+1] the caller's out-edge CSR
+    const int32_t* col;         // [m]
+    const int32_t* lab;         // [m] or nullptr (every label reads 0)
+    int32_t dir;                // 0: x = source, y = target; 1: reversed
+    const int32_t* lsrc;        // [n] block of x
+    const int32_t* ldst;        // [n] block of y
+    unsigned long long* table;  // [2 * cap] 16-byte slots; both words zero = empty
+    unsigned long long* first;  // [cap] smallest edge index of the slot's triple
+    uint64_t mask;              // cap - 1
+    uint32_t* bitmap;           // [m/32+1] edges that are first occurrences
+    Counters* ctr;
+};
+void launch_summary_insert(const SummaryParams& q, cudaStream_t s);
+void launch_summary_mark(const SummaryParams& q, cudaStream_t s);
+void launch_summary_emit(const SummaryParams& q, const uint32_t* prefix, int32_t* out_src, int32_t* out_label,
+                         int32_t* out_dst, cudaStream_t s);
 void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,
                      cudaStream_t s);
 // Copy row src of the level store to the rows [first, last] of levels.

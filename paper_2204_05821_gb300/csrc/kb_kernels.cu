@@ -807,12 +807,17 @@ void launch_hub_final(const RoundParams& p, cudaStream_t s) {
 
 size_t scan_tmp_words(int64_t n_items) { return (size_t)((n_items + kScanTile - 1) / kScanTile) + 1; }
 
+void launch_bitmap_rank(const uint32_t* bitmap, int64_t nw, uint32_t* scan_tmp, uint32_t* prefix, Counters* ctr,
+                        cudaStream_t s) {
+    const int64_t nb = (nw + kScanTile - 1) / kScanTile;
+    popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(bitmap, nw, scan_tmp);
+    scan_block_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, nb, ctr);
+    popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(bitmap, nw, scan_tmp, prefix);
+}
+
 void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
     const int64_t nw = (p.n >> 5) + 1;
-    const int64_t nb = (nw + kScanTile - 1) / kScanTile;
-    popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp);
-    scan_block_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, nb, p.ctr);
-    popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp, prefix);
+    launch_bitmap_rank(p.bitmap, nw, scan_tmp, prefix, p.ctr, s);
     if (batched(p)) {
         // prefix[nw] (one past the last word) is not written by the scan: the
         // total sits in the counters; graph_base_kernel reads prefix only for

@@ -143,6 +143,42 @@ def test_locality_order_resume(ctx, power_law):
         assert np.array_equal(res.counts[j:], C[j:])
 
 
+# ---------------------------------------------------------------- full bisimulation (fixpoint)
+
+
+def assert_fixpoint(ctx, g, d, vl, el, max_rounds=None, initial=None, **kw):
+    mr = g.n + 1 if max_rounds is None else max_rounds
+    L, C, lc = oracle.refine_graph(g, d, vl, el, k=mr, early_stop=True, initial=initial)
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    init = torch.from_numpy(initial).to("cuda:0") if initial is not None else None
+    final, cnt, rounds, stable = ctx.refine_fixpoint(
+        dg, mr, kb.Options(direction=d, use_vertex_labels=vl, use_edge_labels=el, **kw), initial=init)
+    assert np.array_equal(final.cpu().numpy(), L[lc])
+    assert cnt == C[lc] and rounds == lc
+    assert stable == (lc < mr or (lc >= 1 and C[lc] == C[lc - 1]))
+    return lc
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_fixpoint_matches_oracle(ctx, er_tiny, power_law, d):
+    assert_fixpoint(ctx, er_tiny, d, True, True)
+    assert_fixpoint(ctx, er_tiny, d, False, False)
+    assert_fixpoint(ctx, power_law, d, True, True, reorder=2)
+    assert_fixpoint(ctx, power_law, d, False, True, hash_mode=1)
+
+
+def test_fixpoint_cutoff_and_closed_forms(ctx, er_tiny):
+    # a path of n vertices needs n-1 rounds to separate them; a cutoff stops early
+    path = graphgen.path_graph(300)
+    assert assert_fixpoint(ctx, path, 0, False, False) == 300
+    assert assert_fixpoint(ctx, path, 0, False, False, max_rounds=7) == 7
+    assert assert_fixpoint(ctx, graphgen.cycle_graph(500), 0, False, False) == 1
+    # the coarsest stable refinement of a given partition
+    init = (er_tiny.vlabel.astype(np.int64) * 7919 % 5).astype(np.int32)
+    assert_fixpoint(ctx, er_tiny, 1, False, False, initial=init)
+    assert_fixpoint(ctx, er_tiny, 0, True, True, max_rounds=0)
+
+
 # ---------------------------------------------------------------- random small graphs and edge cases
 
 
