@@ -52,6 +52,11 @@ def _load():
                 ctypes.c_int64, ctypes.c_int64, P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                 ctypes.c_int, ctypes.c_int, P, P, P, P,
             ]
+            lib.oracle_refine_cse.restype = ctypes.c_int
+            lib.oracle_refine_cse.argtypes = [
+                ctypes.c_int64, ctypes.c_int64, P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P,
+            ]
             lib.oracle_summary.restype = ctypes.c_int64
             lib.oracle_summary.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
             lib.oracle_count_distinct.restype = ctypes.c_int64
@@ -65,8 +70,9 @@ def _ptr(a):
 
 
 def refine(n, row_offsets, col, elabel=None, vlabel=None, direction=DIR_OUT, use_vertex_labels=True,
-           use_edge_labels=True, k=10, early_stop=True, initial=None):
-    """Run the oracle.  Returns (levels int32[k+1, n], counts int64[k+1], levels_computed)."""
+           use_edge_labels=True, k=10, early_stop=True, initial=None, subject=0):
+    """Run the oracle.  Returns (levels int32[k+1, n], counts int64[k+1], levels_computed).
+    ``subject`` selects the subject part of the key (see oracle_refine_cse)."""
     lib = _load()
     row = np.ascontiguousarray(row_offsets, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
@@ -77,10 +83,10 @@ def refine(n, row_offsets, col, elabel=None, vlabel=None, direction=DIR_OUT, use
     levels = np.zeros((k + 1, max(n, 0)), dtype=np.int32)
     counts = np.zeros(k + 1, dtype=np.int64)
     lc = ctypes.c_int(0)
-    rc = lib.oracle_refine_init(
+    rc = lib.oracle_refine_cse(
         int(n), m, _ptr(row), _ptr(col), _ptr(el), _ptr(vl), int(direction), int(bool(use_vertex_labels)),
-        int(bool(use_edge_labels)), int(k), int(bool(early_stop)), _ptr(ini), _ptr(levels), _ptr(counts),
-        ctypes.byref(lc),
+        int(bool(use_edge_labels)), int(subject), int(k), int(bool(early_stop)), _ptr(ini), _ptr(levels),
+        _ptr(counts), ctypes.byref(lc),
     )
     if rc != 0:
         raise ValueError("oracle_refine rejected its arguments")
@@ -88,10 +94,10 @@ def refine(n, row_offsets, col, elabel=None, vlabel=None, direction=DIR_OUT, use
 
 
 def refine_graph(g, direction=DIR_OUT, use_vertex_labels=True, use_edge_labels=True, k=10, early_stop=True,
-                 initial=None):
+                 initial=None, subject=0):
     """:func:`refine` on a :class:`graphgen.Graph`."""
     return refine(g.n, g.row_offsets, g.col, g.elabel, g.vlabel, direction, use_vertex_labels,
-                  use_edge_labels, k, early_stop, initial)
+                  use_edge_labels, k, early_stop, initial, subject)
 
 
 def summary(g, direction, use_edge_labels, src_level, dst_level):

@@ -14,6 +14,9 @@ recursive step of the paper's definitions literally:
 * BOTH: the forward and the backward conditions must hold together.
 * R_0: everything related, or equal vertex label (Def. "vertex-labeled-bw-
   bisimulation", first bullet).
+* Generic CSE rounds (Def. "cse", Def. "chaining-parameterization"): the
+  first condition u ~s v replaces "u R_i v" -- T, equal labels or id -- and
+  the nested CSE^{i-1} is R_i.
 
 Only for tiny graphs: cost is O(k n^2 deg^2).
 """
@@ -46,8 +49,11 @@ def _matches(adj, R, u, v, use_labels):
 
 
 def relations(n: int, src: Sequence[int], dst: Sequence[int], elabel: Sequence[int], vlabel: Sequence[int],
-              direction: int, use_vertex_labels: bool, use_edge_labels: bool, k: int) -> List[List[List[bool]]]:
-    """R_0..R_k as n x n boolean matrices."""
+              direction: int, use_vertex_labels: bool, use_edge_labels: bool, k: int,
+              subject: int = 0) -> List[List[List[bool]]]:
+    """R_0..R_k as n x n boolean matrices.  ``subject`` is the first condition
+    of Def. "cse" (v ~s v'): 0 keeps R_i itself (stratified bisimulation),
+    1 is T, 2 equal vertex labels, 3 id."""
     src = [int(x) for x in src]
     dst = [int(x) for x in dst]
     lab = [int(x) for x in elabel] if elabel is not None else [0] * len(src)
@@ -62,7 +68,11 @@ def relations(n: int, src: Sequence[int], dst: Sequence[int], elabel: Sequence[i
         nR = [[False] * n for _ in range(n)]
         for u in range(n):
             for v in range(n):
-                if not R[u][v]:
+                if subject == 0 and not R[u][v]:
+                    continue
+                if subject == 2 and int(vlabel[u]) != int(vlabel[v]):
+                    continue
+                if subject == 3 and u != v:
                     continue
                 ok = True
                 if direction in (0, 2):
@@ -105,6 +115,7 @@ def is_equivalence(R: List[List[bool]]) -> bool:
     return True
 
 
-def levels(n, src, dst, elabel, vlabel, direction, use_vertex_labels, use_edge_labels, k) -> Tuple[List[List[int]], List[List[List[bool]]]]:
-    Rs = relations(n, src, dst, elabel, vlabel, direction, use_vertex_labels, use_edge_labels, k)
+def levels(n, src, dst, elabel, vlabel, direction, use_vertex_labels, use_edge_labels, k,
+           subject=0) -> Tuple[List[List[int]], List[List[List[bool]]]]:
+    Rs = relations(n, src, dst, elabel, vlabel, direction, use_vertex_labels, use_edge_labels, k, subject)
     return [canonical_ids(R) for R in Rs], Rs

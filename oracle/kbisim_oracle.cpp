@@ -85,12 +85,22 @@ extern "C" {
 //                              label partition -- refinement of an arbitrary starting
 //                              partition (the relational coarsest partition setting,
 //                              Def. "rel-coar-par-prob", stratified to k rounds).
-int oracle_refine_init(int64_t n, int64_t m, const int64_t* row, const int32_t* col,
-                       const int32_t* elabel, const int32_t* vlabel, int dir,
-                       int use_vertex_labels, int use_edge_labels, int k, int early_stop,
-                       const int32_t* initial,
-                       int32_t* levels, int64_t* counts, int* levels_computed) {
-    if (n < 0 || m < 0 || k < 0 || dir < 0 || dir > 2) return -1;
+//   subject                  : the subject part of the key (Def. "cse": v ~s v').
+//                              0: the vertex's own block at the previous level
+//                              (stratified k-bisimulation, Section 3); 1: T (no
+//                              condition); 2: equal vertex labels (the paper's OC
+//                              type cluster); 3: id (the vertex itself).  With
+//                              1..3 the levels are the chained CSE^i = (~s, ~p,
+//                              CSE^{i-1}) of Def. "chaining-parameterization",
+//                              CSE^0 = P_0, ~p = id with edge labels, T without.
+//                              Those levels need not refine each other, so early
+//                              stop compares whole levels instead of counts.
+int oracle_refine_cse(int64_t n, int64_t m, const int64_t* row, const int32_t* col,
+                      const int32_t* elabel, const int32_t* vlabel, int dir,
+                      int use_vertex_labels, int use_edge_labels, int subject, int k, int early_stop,
+                      const int32_t* initial,
+                      int32_t* levels, int64_t* counts, int* levels_computed) {
+    if (n < 0 || m < 0 || k < 0 || dir < 0 || dir > 2 || subject < 0 || subject > 3) return -1;
     if (n > 0 && (!row || !levels || !counts)) return -1;
     if (m > 0 && !col) return -1;
     if (n > 0 && (row[0] != 0 || row[n] != m)) return -1;
@@ -131,14 +141,20 @@ int oracle_refine_init(int64_t n, int64_t m, const int64_t* row, const int32_t* 
                     sig.push_back(Pair(1, inL.adj[(size_t)v][t].second, prev[inL.adj[(size_t)v][t].first]));
             std::sort(sig.begin(), sig.end());
             sig.erase(std::unique(sig.begin(), sig.end()), sig.end());
-            Key key(prev[v], sig);
+            int32_t s = prev[v];
+            if (subject == 1) s = 0;
+            if (subject == 2) s = vlabel ? vlabel[v] : 0;
+            if (subject == 3) s = (int32_t)v;
+            Key key(s, sig);
             std::map<Key, int32_t>::iterator it = ids.find(key);
             if (it == ids.end()) it = ids.insert(std::make_pair(key, (int32_t)ids.size())).first;
             cur[v] = it->second;
         }
         counts[i] = (int64_t)ids.size();
         if (levels_computed) *levels_computed = i;
-        if (early_stop && counts[i] == counts[i - 1]) {
+        const bool same = subject == 0 ? counts[i] == counts[i - 1]
+                                       : std::memcmp(cur, prev, sizeof(int32_t) * (size_t)n) == 0;
+        if (early_stop && same) {
             for (int j = i + 1; j <= k; ++j) {
                 std::memcpy(levels + (size_t)j * (size_t)n, cur, sizeof(int32_t) * (size_t)n);
                 counts[j] = counts[i];
@@ -147,6 +163,15 @@ int oracle_refine_init(int64_t n, int64_t m, const int64_t* row, const int32_t* 
         }
     }
     return 0;
+}
+
+int oracle_refine_init(int64_t n, int64_t m, const int64_t* row, const int32_t* col,
+                       const int32_t* elabel, const int32_t* vlabel, int dir,
+                       int use_vertex_labels, int use_edge_labels, int k, int early_stop,
+                       const int32_t* initial,
+                       int32_t* levels, int64_t* counts, int* levels_computed) {
+    return oracle_refine_cse(n, m, row, col, elabel, vlabel, dir, use_vertex_labels, use_edge_labels, 0, k,
+                             early_stop, initial, levels, counts, levels_computed);
 }
 
 int oracle_refine(int64_t n, int64_t m, const int64_t* row, const int32_t* col,

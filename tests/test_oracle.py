@@ -420,3 +420,46 @@ def test_summary_follows_block_renaming():
         s, l, t = oracle.summary(g, d, el, P, P)
         s2, l2, t2 = oracle.summary(g, d, el, perm[P], perm[P])
         assert np.array_equal(s2, perm[s]) and np.array_equal(l2, l) and np.array_equal(t2, perm[t])
+
+
+# ---------------------------------------------------------------- generic CSE rounds
+
+
+def test_cse_matches_bruteforce():
+    # Def. "cse": v ~s v', and the (label ~p, object CSE^{i-1}) sets match both ways
+    for g, d, vl, el, k in itertools.islice(_random_cases(300, 20), 300):
+        src, dst, lab = g.edges()
+        for subject in (1, 2, 3):
+            L, C, _ = oracle.refine_graph(g, d, vl, el, k=k, early_stop=False, subject=subject)
+            ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, vl, el, k, subject)
+            assert [r.tolist() for r in L] == ids, (subject, d, vl, el)
+            assert C.tolist() == [max(r) + 1 for r in ids]
+
+
+def test_cse_presets_are_the_paper_models():
+    # Eq. (gsm:schaetzle): (T, id, T)^k forward; Eq. (gsm:kaushik): ((OC, T, OC)^-1)^k
+    g, tables = load()
+    L, _, _ = oracle.refine_graph(g, 0, False, True, k=2, early_stop=False, subject=1)
+    for i, expected in tables["sch"]["levels"].items():
+        assert partition(L[i]) == expected
+    L, _, _ = oracle.refine_graph(g, 1, True, False, k=2, early_stop=False, subject=2)
+    for i, expected in tables["kau"]["levels"].items():
+        assert partition(L[i]) == expected
+
+
+def test_cse_levels_need_not_refine():
+    # (T, id, OC): subjects are not compared, objects by label at depth 1.  Two
+    # differently labelled vertices with an edge to the same vertex share a
+    # level-1 block, so level 1 has fewer blocks than level 0.
+    g = graphgen.from_edges(3, [0, 1], [2, 2], [0, 0], [7, 8, 9])
+    L, C, _ = oracle.refine_graph(g, 0, True, True, k=2, early_stop=False, subject=1)
+    assert C.tolist() == [3, 2, 2]
+    assert L[1].tolist() == [0, 0, 1]
+
+
+def test_cse_early_stop_equals_full_run():
+    for g, d, vl, el, k in itertools.islice(_random_cases(200, 21), 200):
+        for subject in (1, 2, 3):
+            A, CA, lc = oracle.refine_graph(g, d, vl, el, k=k, early_stop=True, subject=subject)
+            B, CB, _ = oracle.refine_graph(g, d, vl, el, k=k, early_stop=False, subject=subject)
+            assert np.array_equal(A, B) and np.array_equal(CA, CB)
