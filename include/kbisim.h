@@ -99,7 +99,24 @@ typedef struct {
  *                      processed edges and 24 rounds: on a 2e9-edge power-law graph
  *                      it saves ~7% per round and costs about 1.2 rounds once),
  *                      1 -> off, 2 -> on (single-graph calls; batched and served
- *                      refinement never reorder) */
+ *                      refinement never reorder)
+ *   subject            the subject part of every key, v ~s v' of Def. "cse" (complex
+ *                      schema element, Sec. "Graph Summaries for Bisimulation"):
+ *                      KB_SUBJECT_PREVIOUS (0): the own block at the previous level,
+ *                      i.e. stratified k-bisimulation (Defs. of Sec. 3);
+ *                      KB_SUBJECT_ALL (1): T, no condition; KB_SUBJECT_LABEL (2):
+ *                      equal vertex labels (the OC type cluster; all equal when
+ *                      vertex_labels is NULL); KB_SUBJECT_ID (3): id, the vertex itself.
+ *                      With 1..3 level i is the chained CSE^i = (~s, ~p, CSE^{i-1})
+ *                      (Def. "chaining-parameterization") with CSE^0 = level 0 (labels
+ *                      or {V} per use_vertex_labels, or kb_refine_from's start) and ~p
+ *                      = id with edge labels, T without; e.g. Eq. (gsm:schaetzle) is
+ *                      (T, id, T)^k: KB_SUBJECT_ALL, edge labels, no vertex labels, out;
+ *                      Eq. (gsm:kaushik) is ((OC, T, OC)^-1)^k: KB_SUBJECT_LABEL, vertex
+ *                      labels, no edge labels, in.  Such levels need not refine one
+ *                      another: early stop then compares whole levels (one extra pass).
+ *                      Single-graph calls only (KB_ERR_INVALID_ARG in batched, served
+ *                      and allocation-free refinement). */
 typedef struct {
     int32_t direction;
     int32_t use_vertex_labels;
@@ -111,8 +128,11 @@ typedef struct {
     int32_t validate;
     int32_t small_task_vertices;
     int32_t reorder;
-    int32_t reserved[6];
+    int32_t subject;
+    int32_t reserved[5];
 } kb_options;
+
+enum { KB_SUBJECT_PREVIOUS = 0, KB_SUBJECT_ALL = 1, KB_SUBJECT_LABEL = 2, KB_SUBJECT_ID = 3 };
 
 typedef struct kb_context kb_context;
 

@@ -20,10 +20,14 @@ from . import _capi
 from ._capi import KB_DIR_BOTH as DIR_BOTH
 from ._capi import KB_DIR_IN as DIR_IN
 from ._capi import KB_DIR_OUT as DIR_OUT
+from ._capi import KB_SUBJECT_ALL as SUBJECT_ALL
+from ._capi import KB_SUBJECT_ID as SUBJECT_ID
+from ._capi import KB_SUBJECT_LABEL as SUBJECT_LABEL
+from ._capi import KB_SUBJECT_PREVIOUS as SUBJECT_PREVIOUS
 from ._capi import KbError
 
 __all__ = [
-    "DIR_OUT", "DIR_IN", "DIR_BOTH", "Options", "DeviceGraph", "Context", "Result", "KbError", "refine",
+    "DIR_OUT", "DIR_IN", "DIR_BOTH", "SUBJECT_PREVIOUS", "SUBJECT_ALL", "SUBJECT_LABEL", "SUBJECT_ID", "Options", "DeviceGraph", "Context", "Result", "KbError", "refine",
     "refine_round_noalloc", "library_path", "Server",
 ]
 
@@ -46,6 +50,7 @@ class Options:
     validate: bool = True
     small_task_vertices: int = 0
     reorder: int = 0  # 0 automatic, 1 off, 2 on
+    subject: int = 0  # SUBJECT_PREVIOUS, SUBJECT_ALL, SUBJECT_LABEL or SUBJECT_ID (generic CSE rounds)
 
     @classmethod
     def schaetzle(cls, **kw) -> "Options":
@@ -69,6 +74,7 @@ class Options:
         o.validate = int(bool(self.validate))
         o.small_task_vertices = int(self.small_task_vertices)
         o.reorder = int(self.reorder)
+        o.subject = int(self.subject)
         return o
 
 

@@ -21,6 +21,7 @@ KB_ERR_DEVICE_CHECK = 6
 KB_ERR_NOT_FOUND = 7
 
 KB_DIR_OUT, KB_DIR_IN, KB_DIR_BOTH = 0, 1, 2
+KB_SUBJECT_PREVIOUS, KB_SUBJECT_ALL, KB_SUBJECT_LABEL, KB_SUBJECT_ID = 0, 1, 2, 3
 KB_KERNEL_COUNT = 6
 KERNEL_NAMES = ("small", "medium", "hub_chunk", "hub_final", "renumber", "other")
 
@@ -48,7 +49,8 @@ class KbOptions(ctypes.Structure):
         ("validate", ctypes.c_int32),
         ("small_task_vertices", ctypes.c_int32),
         ("reorder", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("subject", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 

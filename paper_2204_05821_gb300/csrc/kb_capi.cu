@@ -106,6 +106,7 @@ struct Plan {
     int thr = kb::kDefaultHubThreshold;
     uint64_t cap = 0;
     bool reorder = false;  // locality order of the gather (RoundParams::perm)
+    int subject = 0;       // kb_options::subject (generic CSE rounds when > 0)
     // hubs (host copies, ascending vertex id)
     std::vector<int32_t> hub_v;
     std::vector<int64_t> chunk_off, set_off;
@@ -114,7 +115,7 @@ struct Plan {
     size_t o_rowp = 0, o_colp = 0, o_labp = 0, o_cursor = 0, o_inpref = 0, o_i64tmp = 0;
     size_t csr_bytes = 0;
     size_t o_emin = 0, o_med = 0, o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
-           o_chunkhub = 0, o_chunkext = 0, o_perm = 0, o_gat = 0, o_colr = 0, o_hist = 0, o_acc = 0, o_cnt = 0, o_sets = 0;
+           o_chunkhub = 0, o_chunkext = 0, o_perm = 0, o_gat = 0, o_colr = 0, o_hist = 0, o_ownkey = 0, o_acc = 0, o_cnt = 0, o_sets = 0;
     size_t total = 0;
 };
 
@@ -160,6 +161,7 @@ void layout_round(Plan& P) {
     // CSR is reordered in place
     P.o_colr = take(P.reorder && !needs_in_csr(P.dir) ? sizeof(int32_t) * (size_t)P.m_proc : 0);
     P.o_hist = take(P.reorder ? sizeof(unsigned long long) * 512 : 0);
+    P.o_ownkey = take(P.subject ? sizeof(int32_t) * (size_t)P.n : 0);
     P.total = off;
 }
 
@@ -179,6 +181,7 @@ kb_status check_graph(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         return fail(ctx, KB_ERR_INVALID_ARG, "hub_threshold must be in [0, %d]", kb::kMaxHubThreshold);
     if (opt->hash_mode < 0 || opt->hash_mode > 1) return fail(ctx, KB_ERR_INVALID_ARG, "bad hash_mode");
     if (opt->reorder < 0 || opt->reorder > 2) return fail(ctx, KB_ERR_INVALID_ARG, "reorder must be 0, 1 or 2");
+    if (opt->subject < 0 || opt->subject > 3) return fail(ctx, KB_ERR_INVALID_ARG, "subject must be 0..3");
     if (opt->small_task_vertices != 0 && (opt->small_task_vertices < 32 || opt->small_task_vertices > 65536))
         return fail(ctx, KB_ERR_INVALID_ARG, "small_task_vertices must be 0 or in [32, 65536]");
     if (opt->direction == KB_DIR_BOTH && g->m > (int64_t)1 << 62)
@@ -284,6 +287,7 @@ kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, P
     P.m = g->m;
     P.dir = opt->direction;
     P.m_proc = P.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
+    P.subject = opt->subject;
     P.reorder = rounds >= 0 && P.n > 0 && P.m_proc > 0 &&
                 (opt->reorder == 2 || (opt->reorder == 0 && rounds >= 24 && P.m_proc >= ((int64_t)1 << 22)));
     P.labels = opt->use_edge_labels && g->edge_labels != nullptr;
@@ -367,6 +371,7 @@ struct Timer {
 // parameters and the table epoch.
 struct Prepared {
     Plan P;
+    char* ws = nullptr;  // workspace base (round buffers)
     kb::RoundParams p{};
     uint32_t* prefix = nullptr;
     uint32_t* scan_tmp = nullptr;
@@ -423,6 +428,7 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
         ws = reinterpret_cast<char*>(ctx->own_ws);
     }
     char* csr = base;
+    R.ws = ws;
     kb::RoundParams& p = R.p;
     p = kb::RoundParams{};
     p.n = n;
@@ -543,7 +549,7 @@ kb_status launch_round_body(kb_context* ctx, Prepared& R, cudaStream_t s, Timer*
     if (T) T->end();
     if (p.n_med) {
         if (T) T->begin(KB_KERNEL_MEDIUM);
-        kb::launch_tile_round(p, s);
+        kb::launch_medium_round(p, s);
         if (T) T->end();
     }
     if (p.n_hubs) {
@@ -597,6 +603,22 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     KB_TRY(prepare(ctx, g, opt, R, k - i_start));
     kb::RoundParams& p = R.p;
 
+    // ---- the subject part of every key (generic CSE rounds)
+    if (R.P.subject) {
+        int32_t* own = reinterpret_cast<int32_t*>(R.ws + R.P.o_ownkey);
+        if (R.P.subject == KB_SUBJECT_ALL || (R.P.subject == KB_SUBJECT_LABEL && !g->vertex_labels)) {
+            kb::launch_fill_i32(own, n, 0, s);
+        } else if (R.P.subject == KB_SUBJECT_ID) {
+            kb::launch_iota_i32(own, n, s);
+        } else {
+            // label classes with canonical ids < n (the level-0 pass on the labels)
+            KB_TRY(launch_level0(ctx, R, g->vertex_labels, own, s));
+            KB_TRY(read_counters(ctx));
+            KB_TRY(device_error(ctx));
+        }
+        KB_CUDA(ctx, cudaGetLastError());
+    }
+
     // ---- the starting level
     int32_t* row0 = rows.row(i_start);
     const int32_t* init_key = start ? start : (opt->use_vertex_labels ? g->vertex_labels : nullptr);
@@ -619,11 +641,14 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         KB_TRY(next_epoch(ctx, R, s));
         p.ehigh = 0xffffffffu - (uint32_t)(i - i_start);
         p.prev = rows.row(i - 1);
+        p.own_key = R.P.subject ? reinterpret_cast<const int32_t*>(R.ws + R.P.o_ownkey) : nullptr;
         int32_t* out = rows.row(i);
         KB_TRY(launch_round_body(ctx, R, s, &T));
         T.begin(KB_KERNEL_RENUMBER);
         kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
         T.end();
+        // CSE levels need not refine each other: compare whole levels
+        if (R.P.subject) kb::launch_levels_differ(out, p.prev, n, ctx->d_ctr, s);
         KB_CUDA(ctx, cudaGetLastError());
         KB_TRY(read_counters(ctx));
         ctx->round_ms.push_back(T.collect());
@@ -632,8 +657,10 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         if (counts) counts[i] = c;
         if (last_count) *last_count = c;
         if (levels_computed) *levels_computed = i;
-        if ((opt->early_stop || fixpoint) && c == prev_count) {
-            // blocks only split, so an unchanged count means an unchanged partition
+        const bool unchanged = R.P.subject ? ctx->h_ctr->diff == 0 : c == prev_count;
+        if ((opt->early_stop || fixpoint) && unchanged) {
+            // stratified levels only split blocks, so an unchanged count means an
+            // unchanged partition; generic CSE levels were compared entry by entry
             if (stopped_stable) *stopped_stable = true;
             if (!fixpoint && i < k) kb::launch_copy_rows(rows.levels, n, i, i + 1, k, s);
             if (counts)
@@ -798,6 +825,8 @@ kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, 
     if (G > 0 && (voff_h[0] != 0 || voff_h[G] != g->n))
         return fail(ctx, KB_ERR_INVALID_ARG, "graph_vertex_offsets must run from 0 to n");
     KB_TRY(check_graph(ctx, g, opt, kmax));
+    if (opt->subject != KB_SUBJECT_PREVIOUS)
+        return fail(ctx, KB_ERR_INVALID_ARG, "batched refinement takes subject = KB_SUBJECT_PREVIOUS only");
     const int64_t n = g->n;
     if (G == 0) return KB_OK;
     for (int64_t j = 0; j < G * (kmax + 1); ++j) counts[j] = 0;
@@ -1735,6 +1764,8 @@ const char* kb_server_last_error(const kb_server* sv) { return sv ? sv->last_err
 kb_status kb_server_submit(kb_server* sv, const kb_graph* g, const kb_options* opt, int k, int64_t* ticket) {
     if (!sv || !ticket) return KB_ERR_INVALID_ARG;
     if (!g || !opt) return sfail(sv, KB_ERR_INVALID_ARG, "graph and options must not be NULL");
+    if (opt->subject != KB_SUBJECT_PREVIOUS)
+        return sfail(sv, KB_ERR_INVALID_ARG, "served refinement takes subject = KB_SUBJECT_PREVIOUS only");
     if (g->n < 0 || g->m < 0 || k < 0 || opt->direction < 0 || opt->direction > 2)
         return sfail(sv, KB_ERR_INVALID_ARG, "bad request");
     if (g->n > 0 && !g->row_offsets) return sfail(sv, KB_ERR_INVALID_ARG, "row_offsets is NULL");

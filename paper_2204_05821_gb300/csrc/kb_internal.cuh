@@ -11,19 +11,10 @@
 namespace kb {
 
 // ---------------------------------------------------------------- geometry
-// A signature CTA owns kTileVerts consecutive vertices.  Their edges (hubs
-// excluded) are staged in shared memory in sub-tiles that hold at most
-// kStage pairs: vertices are grouped by floor(edge prefix / kSplit), so a
-// sub-tile holds < kSplit + hub_threshold <= kStage edges.
-#ifndef KB_TILE_VERTS
-#define KB_TILE_VERTS 256
-#endif
-constexpr int kTileVerts = KB_TILE_VERTS;
-constexpr int kTileThreads = KB_TILE_VERTS;
-constexpr int kSplit = 4 * KB_TILE_VERTS;
-constexpr int kStage = 8 * KB_TILE_VERTS;
-constexpr int kSetCap = 2 * kStage;  // shared dedup set slots
-constexpr int kMaxHubThreshold = kStage - kSplit;
+// Vertices with more than hub_threshold edges (at most kMaxHubThreshold) are
+// hubs, split into chunks of kHubChunk edges; medium vertices keep their pairs
+// in one shared-memory set of 2 x kMaxHubThreshold entries.
+constexpr int kMaxHubThreshold = 1024;
 constexpr int kDefaultHubThreshold = kMaxHubThreshold;
 #ifndef KB_HUB_CHUNK
 #define KB_HUB_CHUNK 512
@@ -47,7 +38,7 @@ enum : int32_t { kErrTableFull = 1, kErrInvalid = 2, kErrStage = 4, kErrHubSet =
 
 struct Counters {
     int32_t err;
-    int32_t pad;
+    int32_t diff;   // set when two compared levels differ (launch_levels_differ)
     int64_t count;  // blocks at the level just assigned
 };
 
@@ -65,6 +56,10 @@ struct RoundParams {
     // head.  perm == nullptr: col holds ids and the gather reads prev.
     const int32_t* perm;
     int32_t* gat;
+    // Generic CSE rounds (Def. "cse"): the subject part of every key, one class
+    // id (< n) per vertex; nullptr keys by the own previous block (stratified
+    // bisimulation).
+    const int32_t* own_key;
     int32_t hub_threshold;
     int32_t small_max;    // min(kSmallDegree, hub_threshold)
     int32_t warp_verts;   // vertices per warp task of the small-vertex kernel
@@ -104,6 +99,11 @@ struct RoundParams {
 };
 
 __host__ __device__ __forceinline__ bool batched(const RoundParams& p) { return p.vgraph != nullptr; }
+
+// The subject part of vertex v's key in a signature round.
+__host__ __device__ __forceinline__ int32_t own_of(const RoundParams& p, int64_t v) {
+    return p.own_key ? p.own_key[v] : p.prev[v];
+}
 
 // The array the per-edge gather reads through col (see RoundParams::perm).
 __host__ __device__ __forceinline__ const int32_t* gather_base(const RoundParams& p) {
@@ -163,7 +163,6 @@ __device__ __forceinline__ uint32_t table_hi(uint64_t h, uint32_t epoch) {
 // Signature rounds (kb_kernels.cu)
 void launch_clear_round(const RoundParams& p, cudaStream_t s);
 void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s);
-void launch_tile_round(const RoundParams& p, cudaStream_t s);
 void launch_medium_round(const RoundParams& p, cudaStream_t s);  // kb_medium.cu
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s);
 void launch_hub_final(const RoundParams& p, cudaStream_t s);
@@ -230,6 +229,10 @@ void launch_summary_insert(const SummaryParams& q, cudaStream_t s);
 void launch_summary_mark(const SummaryParams& q, cudaStream_t s);
 void launch_summary_emit(const SummaryParams& q, const uint32_t* prefix, int32_t* out_src, int32_t* out_label,
                          int32_t* out_dst, cudaStream_t s);
+// fill out[i] = i (kb_kernels.cu)
+void launch_iota_i32(int32_t* out, int64_t n, cudaStream_t s);
+// ctr->diff |= (a != b) over n entries (kb_kernels.cu)
+void launch_levels_differ(const int32_t* a, const int32_t* b, int64_t n, Counters* ctr, cudaStream_t s);
 void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,
                      cudaStream_t s);
 // Copy row src of the level store to the rows [first, last] of levels.

@@ -1,8 +1,8 @@
 // Refinement-round kernels of the GB300 k-bisimulation library.
 //
 // One round (paper Alg. 1, one pass of the loop; Def. "signature"):
-//   1. tile_round_kernel: every non-hub vertex gathers its (direction, edge
-//      label, previous block of neighbour) pairs, drops duplicates, hashes
+//   1. kb_small.cu / kb_medium.cu: every non-hub vertex gathers its (direction,
+//      edge label, previous block of neighbour) pairs, drops duplicates, hashes
 //      (own previous block, pair set) and finds or inserts its key in the
 //      block table.  A hash match is accepted only after the full signature
 //      compare (the paper's implementations trust the hash; Section 4.3 notes
@@ -19,307 +19,6 @@
 
 namespace kb {
 namespace {
-
-enum : uint8_t { kPending = 0, kDone = 1, kSkip = 2 };
-
-// Exclusive scan of one int per thread over a CTA of NT threads.
-template <int NT>
-__device__ __forceinline__ int block_exclusive_scan(int x, int* warp_tmp, int* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tmp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < NT / 32 ? warp_tmp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < NT / 32) warp_tmp[lane] = w;
-    }
-    __syncthreads();
-    const int base = warp > 0 ? warp_tmp[warp - 1] : 0;
-    *total = warp_tmp[NT / 32 - 1];
-    __syncthreads();
-    return base + incl - x;
-}
-
-// ----------------------------------------------------------------------------
-// Tile kernel: kTileVerts medium vertices (small_max < degree <= hub_threshold)
-// per CTA, taken from the medium-vertex list; one thread per vertex.  Their
-// edges are staged in shared memory, deduplicated per vertex with a shared
-// hash set, hashed, and inserted in the block table with a full signature
-// compare on every tag match.
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTileThreads, 2) tile_round_kernel(const RoundParams p) {
-    __shared__ int64_t s_row[kTileVerts + 1];
-    __shared__ int32_t s_eoff[kTileVerts + 1];
-    __shared__ int32_t s_vid[kTileVerts];
-    __shared__ uint64_t s_pair[kStage];
-    __shared__ uint16_t s_seg[kStage];
-    __shared__ uint32_t s_set[kSetCap];  // bits 15..0: staged index + 1; bits 31..16: compare stamp
-    __shared__ uint64_t s_acc[kTileVerts];
-    __shared__ uint32_t s_cnt[kTileVerts];
-    __shared__ uint64_t s_pos[kTileVerts];
-    __shared__ uint32_t s_hi[kTileVerts];
-    __shared__ int32_t s_own[kTileVerts];
-    __shared__ uint8_t s_state[kTileVerts];
-    __shared__ uint16_t s_qj[kTileVerts];
-    __shared__ uint32_t s_qr[kTileVerts];
-    __shared__ uint8_t s_qres[kTileVerts];
-    __shared__ int s_warp[32];
-    __shared__ int s_qn;
-
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kTileVerts;
-    const int nv = (int)min((int64_t)kTileVerts, p.n_med - base);
-
-    int cdeg = 0;
-    uint8_t st = kSkip;
-    int32_t vid = 0;
-    int64_t rs = 0;
-    if (tid < nv) {
-        vid = p.med_v[base + tid];
-        rs = p.row[vid];
-        const int64_t d = p.row[(int64_t)vid + 1] - rs;
-        if (d > p.small_max && d <= p.hub_threshold && vertex_refines(p, vid)) {
-            st = kPending;
-            cdeg = (int)d;
-        }
-    }
-    s_vid[tid] = vid;
-    s_row[tid] = rs;
-    s_state[tid] = st;
-    int total;
-    const int eo = block_exclusive_scan<kTileThreads>(cdeg, s_warp, &total);
-    s_eoff[tid] = eo;
-    if (tid == 0) s_eoff[nv] = total;
-    __syncthreads();
-
-    const int n_sub = total == 0 ? 1 : (total + kSplit - 1) / kSplit;
-    for (int sub = 0; sub < n_sub; ++sub) {
-        // vertices whose edge prefix falls in [sub*kSplit, (sub+1)*kSplit)
-        int jlo, jhi;
-        {
-            int lo = 0, hi = nv;
-            const int key = sub * kSplit;
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (s_eoff[mid] < key) lo = mid + 1; else hi = mid; }
-            jlo = lo;
-            if (sub == n_sub - 1) {
-                jhi = nv;
-            } else {
-                int lo2 = jlo, hi2 = nv;
-                const int key2 = (sub + 1) * kSplit;
-                while (lo2 < hi2) { int mid = (lo2 + hi2) >> 1; if (s_eoff[mid] < key2) lo2 = mid + 1; else hi2 = mid; }
-                jhi = lo2;
-            }
-        }
-        if (jlo >= jhi) continue;  // uniform over the CTA
-        const int elo = s_eoff[jlo];
-        const int ehi = jhi == nv ? total : s_eoff[jhi];
-        const int E = ehi - elo;
-        if (E > kStage) {  // cannot happen with hub_threshold <= kMaxHubThreshold
-            if (tid == 0) set_error(p.ctr, kErrStage);
-            continue;
-        }
-
-        for (int i = tid; i < kSetCap; i += kTileThreads) s_set[i] = 0u;
-        if (tid >= jlo && tid < jhi) { s_acc[tid] = 0ull; s_cnt[tid] = 0u; }
-        __syncthreads();
-
-        {
-            // Stage: coalesced streaming loads of neighbours and labels, then the
-            // gather of their previous blocks; four edges per thread in flight.
-            for (int base = 0; base < E; base += 4 * kTileThreads) {
-                int le[4], jj[4];
-                int64_t ge[4];
-                int32_t w[4], l[4], b[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    le[u] = base + u * kTileThreads + tid;
-                    jj[u] = jlo;
-                    ge[u] = 0;
-                    if (le[u] < E) {
-                        const int e = elo + le[u];
-                        int lo = jlo, hi = jhi;
-                        while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s_eoff[mid] <= e) lo = mid; else hi = mid; }
-                        jj[u] = lo;
-                        ge[u] = s_row[lo] + (e - s_eoff[lo]);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (le[u] < E) {
-                        w[u] = __ldcs(p.col + ge[u]);
-                        l[u] = p.lab ? __ldcs(p.lab + ge[u]) : 0;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (le[u] < E) b[u] = __ldg(gather_base(p) + (w[u] & 0x7fffffff));
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (le[u] < E) {
-                        s_pair[le[u]] = pack_pair(l[u], (uint32_t)w[u], b[u]);
-                        s_seg[le[u]] = (uint16_t)jj[u];
-                    }
-                }
-            }
-            __syncthreads();
-
-            // Drop duplicate pairs per vertex (set semantics): the first copy of
-            // each pair gets bit 15 of its segment word.
-            for (int le = tid; le < E; le += kTileThreads) {
-                const uint64_t pr = s_pair[le];
-                const uint32_t j = s_seg[le];
-                uint32_t slot = set_slot(pr, j) & (kSetCap - 1);
-                while (true) {
-                    uint32_t cur = s_set[slot];
-                    if (cur == 0u) {
-                        const uint32_t old = atomicCAS(&s_set[slot], 0u, (uint32_t)(le + 1));
-                        if (old == 0u) {
-                            s_seg[le] = (uint16_t)(j | 0x8000u);
-                            break;
-                        }
-                        cur = old;
-                    }
-                    const int idx = (int)(cur & 0xffffu) - 1;
-                    if (s_pair[idx] == pr && (s_seg[idx] & 0x7fffu) == j) break;
-                    slot = (slot + 1) & (kSetCap - 1);
-                }
-            }
-            __syncthreads();
-            // Order-independent hash of each vertex's distinct pairs: one warp
-            // per vertex sums the pair mixes of its flagged edges.
-            for (int j = jlo + warp; j < jhi; j += kTileThreads / 32) {
-                const int a = s_eoff[j] - elo;
-                const int b = (j + 1 == jhi ? ehi : s_eoff[j + 1]) - elo;
-                uint64_t acc = 0;
-                uint32_t cnt = 0;
-                for (int le = a + lane; le < b; le += 32) {
-                    if (s_seg[le] & 0x8000u) {
-                        acc += pair_mix(s_pair[le]);
-                        ++cnt;
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    acc += __shfl_xor_sync(kFull, (unsigned long long)acc, o);
-                    cnt += __shfl_xor_sync(kFull, cnt, o);
-                }
-                if (lane == 0) {
-                    s_acc[j] = acc;
-                    s_cnt[j] = cnt;
-                }
-            }
-            __syncthreads();
-        }
-
-        // Hash each vertex's key.
-        if (tid >= jlo && tid < jhi && s_state[tid] == kPending) {
-            const int32_t own = p.prev[s_vid[tid]];
-            const uint64_t h = vertex_hash(own, s_cnt[tid], s_acc[tid], p.hash_mode);
-            s_pos[tid] = h & p.mask;
-            s_hi[tid] = table_hi(h, p.epoch);
-            s_own[tid] = own;
-        }
-
-        // Find-or-insert with full signature compare on every tag match.
-        for (uint32_t stamp = 1;; ++stamp) {
-            if (tid == 0) s_qn = 0;
-            __syncthreads();
-            if (tid >= jlo && tid < jhi && s_state[tid] == kPending) {
-                uint64_t pos = s_pos[tid];
-                uint32_t rep = 0;
-                const int r = probe_table(p, &pos, s_hi[tid], (uint32_t)s_vid[tid], &rep);
-                s_pos[tid] = pos;
-                if (r == 0) {
-                    s_state[tid] = kDone;
-                } else if (r == 1) {
-                    const unsigned b = __activemask();
-                    const int leader = __ffs(b) - 1;
-                    int q0 = 0;
-                    if (lane == leader) q0 = atomicAdd(&s_qn, __popc(b));
-                    q0 = __shfl_sync(b, q0, leader);
-                    const int q = q0 + __popc(b & ((1u << lane) - 1u));
-                    s_qj[q] = (uint16_t)tid;
-                    s_qr[q] = rep;
-                } else {
-                    set_error(p.ctr, kErrTableFull);
-                    s_state[tid] = kDone;
-                }
-            }
-            __syncthreads();
-            const int qn = s_qn;
-            if (qn == 0) break;
-            if (stamp >= 0xffffu) {  // cannot happen within the probe limit
-                if (tid == 0) set_error(p.ctr, kErrTableFull);
-                break;
-            }
-            // Compare: one warp per queued vertex.  The representative r is a
-            // small or medium vertex (hubs enter the table after this kernel), so
-            // its pairs are re-derived from the CSR and looked up in the shared
-            // set of our vertex; every distinct pair of ours must be hit once.
-            for (int q = warp; q < qn; q += kTileThreads / 32) {
-                const int j = s_qj[q];
-                const uint32_t r = s_qr[q];
-                bool ok = same_graph(p, r, s_vid[j]) && (__ldg(p.prev + r) == s_own[j]);
-                if (ok) {
-                    const int64_t rb = p.row[r], re = p.row[r + 1];
-                    int nf = 0;
-                    for (int64_t e0 = rb; e0 < re; e0 += 32) {
-                        const int64_t e = e0 + lane;
-                        bool found = true;
-                        if (e < re) {
-                            const int32_t w = __ldg(p.col + e);
-                            const int32_t l = p.lab ? __ldg(p.lab + e) : 0;
-                            const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
-                            uint32_t slot = set_slot(pr, (uint32_t)j) & (kSetCap - 1);
-                            found = false;
-                            while (true) {
-                                const uint32_t cur = s_set[slot];
-                                if (cur == 0u) break;
-                                const int idx = (int)(cur & 0xffffu) - 1;
-                                if (s_pair[idx] == pr && (s_seg[idx] & 0x7fffu) == (uint32_t)j) {
-                                    const uint32_t old = atomicMax(&s_set[slot], (stamp << 16) | (cur & 0xffffu));
-                                    if ((old >> 16) < stamp) ++nf;
-                                    found = true;
-                                    break;
-                                }
-                                slot = (slot + 1) & (kSetCap - 1);
-                            }
-                        }
-                        ok = ok && found;
-                    }
-                    ok = __all_sync(kFull, ok);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(kFull, nf, o);
-                    ok = ok && ((uint32_t)nf == s_cnt[j]);
-                }
-                if (lane == 0) s_qres[q] = ok ? 1 : 0;
-            }
-            __syncthreads();
-            if (tid < qn) {
-                const int j = s_qj[tid];
-                if (s_qres[tid]) {
-                    join_slot(p, s_pos[j], s_hi[j], (uint32_t)s_vid[j]);
-                    s_state[j] = kDone;
-                } else {
-                    s_pos[j] = (s_pos[j] + 1) & p.mask;
-                }
-            }
-            __syncthreads();
-        }
-        __syncthreads();
-    }
-}
 
 // ----------------------------------------------------------------------------
 // Hub chunks: kHubChunk edges of one hub per CTA.  Chunk-local dedup in shared
@@ -484,7 +183,7 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
     const int h = blockIdx.x;
     const int32_t v = p.hub_v[h];
     if (!vertex_refines(p, v)) return;
-    const int32_t own = p.prev[v];
+    const int32_t own = own_of(p, v);
     const uint32_t cnt = p.hub_cnt[h];
     const uint64_t hv = vertex_hash(own, cnt, p.hub_acc[h], p.hash_mode);
     const uint32_t hi = table_hi(hv, p.epoch);
@@ -511,7 +210,7 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
             return;
         }
         const uint32_t r = s_rep;
-        bool ok = same_graph(p, r, v) && (__ldg(p.prev + r) == own);
+        bool ok = same_graph(p, r, v) && (own_of(p, r) == own);
         const int64_t rb = p.row[r], re = p.row[r + 1];
         if (ok && re - rb > p.hub_threshold) {
             // representative is a hub: compare distinct counts, then look its
@@ -768,6 +467,18 @@ __global__ void fill_i32_kernel(int32_t* out, int64_t n, int32_t value) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = value;
 }
 
+__global__ void iota_i32_kernel(int32_t* out, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (int32_t)i;
+}
+
+__global__ void levels_differ_kernel(const int32_t* a, const int32_t* b, int64_t n, Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool d = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) d |= a[i] != b[i];
+    if (__any_sync(kFull, d) && (threadIdx.x & 31) == 0) atomicOr(&ctr->diff, 1);
+}
+
 int grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -783,16 +494,6 @@ void launch_clear_round(const RoundParams& p, cudaStream_t s) {
         cudaMemsetAsync(p.hub_acc, 0, sizeof(uint64_t) * (size_t)p.n_hubs, s);
         cudaMemsetAsync(p.hub_cnt, 0, sizeof(uint32_t) * (size_t)p.n_hubs, s);
     }
-}
-
-void launch_tile_round(const RoundParams& p, cudaStream_t s) {
-    if (p.n_med <= 0) return;
-#ifndef KB_MEDIUM_TILE
-    launch_medium_round(p, s);
-    return;
-#endif
-    const int64_t blocks = (p.n_med + kTileVerts - 1) / kTileVerts;
-    tile_round_kernel<<<(unsigned)blocks, kTileThreads, 0, s>>>(p);
 }
 
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s) {
@@ -848,6 +549,16 @@ void launch_localize(int32_t* row, int64_t n, const int32_t* vgraph, const uint3
 void launch_vertex_graph(const int64_t* voff, int32_t G, int64_t n, int32_t* vgraph, cudaStream_t s) {
     if (G <= 0) return;
     vertex_graph_kernel<<<(unsigned)G, 256, 0, s>>>(voff, G, n, vgraph);
+}
+
+void launch_iota_i32(int32_t* out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    iota_i32_kernel<<<grid_for(n, 256), 256, 0, s>>>(out, n);
+}
+
+void launch_levels_differ(const int32_t* a, const int32_t* b, int64_t n, Counters* ctr, cudaStream_t s) {
+    if (n <= 0) return;
+    levels_differ_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, b, n, ctr);
 }
 
 void launch_fill_i32(int32_t* out, int64_t n, int32_t value, cudaStream_t s) {

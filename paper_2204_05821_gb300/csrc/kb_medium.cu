@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kWarps * 32) medium_round_kernel(const RoundPa
         tv = p.med_v[t0 + lane];
         trs = p.row[tv];
         tre = p.row[(int64_t)tv + 1];
-        town = p.prev[tv];
+        town = own_of(p, tv);
         const int64_t d = tre - trs;
         take = d > dlo && d <= dhi && vertex_refines(p, tv);
     }
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kWarps * 32) medium_round_kernel(const RoundPa
             }
             rep = __shfl_sync(kFull, rep, 0);
             pos = __shfl_sync(kFull, (unsigned long long)pos, 0);
-            bool ok = same_graph(p, rep, v) && __ldg(p.prev + rep) == own;
+            bool ok = same_graph(p, rep, v) && own_of(p, rep) == own;
             if (ok) {
                 for (int i = lane; i < c / 32; i += 32) mark[i] = 0u;
                 __syncwarp();
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) medium_cta_kernel(const RoundParams 
             s_v[lane] = v;
             s_rs[lane] = rs;
             s_re[lane] = re;
-            s_own[lane] = p.prev[v];
+            s_own[lane] = own_of(p, v);
             take = re - rs > dlo && re - rs <= dhi && vertex_refines(p, v);
         }
         const unsigned todo = __ballot_sync(kFull, take);
@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kThreads) medium_cta_kernel(const RoundParams 
                 break;
             }
             const uint32_t rep = s_rep;
-            bool ok = same_graph(p, rep, v) && __ldg(p.prev + rep) == own;
+            bool ok = same_graph(p, rep, v) && own_of(p, rep) == own;
             if (ok) {
                 for (int i = tid; i < c / 32; i += kThreads) s_mark[i] = 0u;
                 __syncthreads();

@@ -85,6 +85,7 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     if (!g || !opt || !count) return KB_ERR_INVALID_ARG;
     if (g->n < 0 || g->m < 0 || g->n > kMaxVertices) return KB_ERR_INVALID_ARG;
     if (opt->direction != KB_DIR_OUT) return KB_ERR_INVALID_ARG;
+    if (opt->subject != KB_SUBJECT_PREVIOUS) return KB_ERR_INVALID_ARG;
     if (opt->hash_mode < 0 || opt->hash_mode > 1) return KB_ERR_INVALID_ARG;
     if (opt->hub_threshold < 0 || opt->hub_threshold > kb::kMaxHubThreshold) return KB_ERR_INVALID_ARG;
     if (g->n == 0) {
@@ -151,7 +152,7 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     p.n_med = host_cnts[0];
 
     kb::launch_small_round(p, false, s);
-    kb::launch_tile_round(p, s);
+    kb::launch_medium_round(p, s);
     kb::launch_renumber(p, reinterpret_cast<uint32_t*>(base + kOffPrefix), reinterpret_cast<uint32_t*>(base + kOffScan),
                         out, s);
     NA_CUDA(cudaGetLastError());

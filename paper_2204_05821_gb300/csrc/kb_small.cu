@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
     auto prefetch = [&](int64_t w0) {
         const int64_t vv = w0 + lane;
         if (vv < ve) {
-            pf_own = p.prev ? p.prev[vv] : 0;
+            pf_own = (!kLevel0 && p.own_key) ? p.own_key[vv] : (p.prev ? p.prev[vv] : 0);
             if (!kLevel0) {
                 pf_a = p.row[vv];
                 pf_b = p.row[vv + 1];
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
             }
             // full signature compare with the representative, on this lane;
             // its key and its row offsets are loaded together
-            const int32_t* keys = (l0 && !kLevel0) ? p.vlab : p.prev;
+            const int32_t* keys = (l0 && !kLevel0) ? p.vlab : ((!kLevel0 && p.own_key) ? p.own_key : p.prev);
             const int32_t rkey = keys ? __ldg(keys + rep) : 0;
             int64_t rb = 0, re = 0;
             if (!l0) {

@@ -92,3 +92,11 @@ def test_autotune_keeps_results(ctx):
     L, C, lc = oracle.refine_graph(g, 0, True, True, k=10)
     res = ctx.refine(dg, 10, kb.Options())
     assert np.array_equal(res.levels.cpu().numpy(), L) and np.array_equal(res.counts, C)
+
+
+def test_batch_rejects_cse_subjects(ctx):
+    g = graphgen.make(graphgen.CONFIG_TINY)
+    union, voff = graphgen.disjoint_union([g, g])
+    dg = kb.DeviceGraph.from_numpy(union, "cuda:0")
+    with pytest.raises(kb.KbError):
+        ctx.refine_batch(dg, voff, np.array([2, 2], dtype=np.int32), kb.Options(subject=kb.SUBJECT_ALL))

@@ -33,7 +33,7 @@ def gpu_levels(ctx, g, d, vl, el, k, early_stop=True, **kw):
 
 
 def assert_same(ctx, g, d, vl, el, k, early_stop=True, **kw):
-    L, C, lc = oracle.refine_graph(g, d, vl, el, k=k, early_stop=early_stop)
+    L, C, lc = oracle.refine_graph(g, d, vl, el, k=k, early_stop=early_stop, subject=kw.get("subject", 0))
     got, gc, glc = gpu_levels(ctx, g, d, vl, el, k, early_stop, **kw)
     for i in range(k + 1):
         if not np.array_equal(got[i], L[i]):
@@ -148,14 +148,14 @@ def test_locality_order_resume(ctx, power_law):
 
 def assert_fixpoint(ctx, g, d, vl, el, max_rounds=None, initial=None, **kw):
     mr = g.n + 1 if max_rounds is None else max_rounds
-    L, C, lc = oracle.refine_graph(g, d, vl, el, k=mr, early_stop=True, initial=initial)
+    L, C, lc = oracle.refine_graph(g, d, vl, el, k=mr, early_stop=True, initial=initial, subject=kw.get("subject", 0))
     dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
     init = torch.from_numpy(initial).to("cuda:0") if initial is not None else None
     final, cnt, rounds, stable = ctx.refine_fixpoint(
         dg, mr, kb.Options(direction=d, use_vertex_labels=vl, use_edge_labels=el, **kw), initial=init)
     assert np.array_equal(final.cpu().numpy(), L[lc])
     assert cnt == C[lc] and rounds == lc
-    assert stable == (lc < mr or (lc >= 1 and C[lc] == C[lc - 1]))
+    assert stable == (lc < mr or (lc >= 1 and np.array_equal(L[lc], L[lc - 1])))
     return lc
 
 
@@ -179,6 +179,44 @@ def test_fixpoint_cutoff_and_closed_forms(ctx, er_tiny):
     assert_fixpoint(ctx, er_tiny, 0, True, True, max_rounds=0)
 
 
+# ---------------------------------------------------------------- generic CSE rounds
+
+
+@pytest.mark.parametrize("subject", [kb.SUBJECT_ALL, kb.SUBJECT_LABEL, kb.SUBJECT_ID])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_cse_rounds(ctx, er_tiny, power_law, d, subject):
+    # Def. "cse" chained (Def. "chaining-parameterization"): subject T, label or id
+    for g in (er_tiny, power_law):
+        for vl, el in ((True, True), (False, True), (True, False)):
+            assert_same(ctx, g, d, vl, el, 5, early_stop=False, subject=subject)
+        assert_same(ctx, g, d, True, True, 8, early_stop=True, subject=subject)  # whole-level stop
+    assert_same(ctx, er_tiny, d, True, True, 4, subject=subject, hash_mode=1, hub_threshold=17)
+    assert_same(ctx, power_law, d, True, False, 4, subject=subject, reorder=2)
+
+
+def test_cse_models_of_the_paper(ctx):
+    # Eq. (gsm:schaetzle) (T, id, T)^k and Eq. (gsm:kaushik) ((OC, T, OC)^-1)^k
+    g, tables = load()
+    for name, opts in (("sch", kb.Options(direction=kb.DIR_OUT, use_vertex_labels=False, use_edge_labels=True,
+                                          subject=kb.SUBJECT_ALL, early_stop=False)),
+                       ("kau", kb.Options(direction=kb.DIR_IN, use_vertex_labels=True, use_edge_labels=False,
+                                          subject=kb.SUBJECT_LABEL, early_stop=False))):
+        res = ctx.refine(kb.DeviceGraph.from_numpy(g, "cuda:0"), 2, opts)
+        got = res.levels.cpu().numpy()
+        for i, expected in tables[name]["levels"].items():
+            assert partition(got[i]) == expected
+
+
+def test_cse_fixpoint_and_rejections(ctx, er_tiny):
+    for subject in (kb.SUBJECT_ALL, kb.SUBJECT_LABEL):
+        assert_fixpoint(ctx, er_tiny, 0, True, True, max_rounds=40, subject=subject)
+    # a level-1 merge of differently labelled vertices: levels need not refine
+    g = graphgen.from_edges(3, [0, 1], [2, 2], [0, 0], [7, 8, 9])
+    assert_same(ctx, g, 0, True, True, 3, subject=kb.SUBJECT_ALL)
+    with pytest.raises(kb.KbError):
+        gpu_levels(ctx, er_tiny, 0, True, True, 3, subject=4)
+
+
 # ---------------------------------------------------------------- random small graphs and edge cases
 
 
@@ -189,7 +227,7 @@ def test_random_tiny_graphs(ctx):
         d = int(rng.integers(0, 3))
         assert_same(ctx, g, d, bool(rng.integers(0, 2)), bool(rng.integers(0, 2)), int(rng.integers(0, 7)),
                     hash_mode=int(rng.integers(0, 2)), hub_threshold=int(rng.choice([0, 1, 2, 5])),
-                    reorder=int(rng.choice([1, 2])))
+                    reorder=int(rng.choice([1, 2])), subject=int(rng.choice([0, 0, 1, 2, 3])))
 
 
 def test_edge_cases(ctx):
