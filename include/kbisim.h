@@ -225,8 +225,8 @@ kb_status kb_refine_fixpoint(kb_context* ctx, const kb_graph* g, const kb_option
  *   count              HOST; the number of summary edges, set also when the
  *                      outputs are too small (then KB_ERR_INVALID_ARG, outputs
  *                      untouched)
- * Scratch: about 24 B x next_pow2(1.25 m) + m/4 B from the stream-ordered
- * allocator, released before return.  Synchronises. */
+ * Scratch: about 24 B x next_pow2(1.25 m) + m/4 B of library-owned device memory,
+ * kept for later calls (grow-only) and released by kb_destroy.  Synchronises. */
 kb_status kb_summary(kb_context* ctx, const kb_graph* g, int direction, int use_edge_labels,
                      const int32_t* src_level, const int32_t* dst_level, int32_t* out_src,
                      int32_t* out_label, int32_t* out_dst, int64_t capacity, int64_t* count);

@@ -52,6 +52,9 @@ struct kb_context {
     // fixpoint refinement: the last two levels
     void* fix_buf = nullptr;
     size_t fix_buf_bytes = 0;
+    // summary graph: triple table, first edges, edge bitmap and its ranks
+    void* sum_buf = nullptr;
+    size_t sum_buf_bytes = 0;
     cudaStream_t cap_stream = nullptr;  // non-default stream used only to capture CUDA graphs
     // timing
     bool timing = false;
@@ -689,8 +692,8 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
 }
 
 // Summary graph of (src_level, dst_level): distinct triples in order of first
-// occurrence (see kb_summary in kbisim.h).  Scratch comes from the
-// stream-ordered allocator and is released before returning.
+// occurrence (see kb_summary in kbisim.h).  Scratch is library-owned and
+// grow-only (released by kb_destroy), like the refinement workspace.
 kb_status summary_impl(kb_context* ctx, const kb_graph* g, int direction, int use_edge_labels,
                        const int32_t* src_level, const int32_t* dst_level, int32_t* out_src, int32_t* out_label,
                        int32_t* out_dst, int64_t capacity, int64_t* count) {
@@ -716,11 +719,8 @@ kb_status summary_impl(kb_context* ctx, const kb_graph* g, int direction, int us
                  sz_prefix = 4 * (size_t)(nw + 1), sz_scan = 4 * kb::scan_tmp_words(nw);
     const size_t total = align_up(sz_table) + align_up(sz_first) + align_up(sz_bitmap) + align_up(sz_prefix) +
                          align_up(sz_scan);
-    char* base = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&base), total, s) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, KB_ERR_OOM, "cannot allocate %zu bytes for the summary graph", total);
-    }
+    KB_TRY(ensure_buffer(ctx, &ctx->sum_buf, &ctx->sum_buf_bytes, total));
+    char* base = reinterpret_cast<char*>(ctx->sum_buf);
     kb::SummaryParams q{};
     q.n = g->n;
     q.m = m;
@@ -768,7 +768,6 @@ kb_status summary_impl(kb_context* ctx, const kb_graph* g, int direction, int us
         return KB_OK;
     };
     st = run();
-    cudaFreeAsync(base, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && st == KB_OK) st = fail(ctx, KB_ERR_CUDA, "summary graph failed");
     return st;
 }
@@ -1479,6 +1478,7 @@ kb_status kb_destroy(kb_context* ctx) {
     cudaFree(ctx->batch_ws);
     cudaFree(ctx->tune_buf);
     cudaFree(ctx->fix_buf);
+    cudaFree(ctx->sum_buf);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);

@@ -8,8 +8,8 @@
 // triple itself is the key, so no compare against a representative is
 // needed); each slot also keeps its smallest edge index.  Output order is
 // first occurrence in the edge list: the first edges are marked in an edge
-// bitmap, ranked by a popcount prefix scan, and every slot writes its triple
-// at the rank of its first edge.
+// bitmap, ranked by a popcount prefix scan, and every first edge writes its
+// triple at its rank.
 //
 //   insert  CTA tiles of kSumTile consecutive edges: two binary searches give
 //           the tile's source range, every edge finds its source inside it;
@@ -17,7 +17,8 @@
 //           comes first) to probe the table, so repeated triples cost one
 //           atomic per warp;
 //   mark    one bit per occupied slot, at its first edge;
-//   emit    the triple of every occupied slot at its rank.
+//   emit    the edges again, in order: every first occurrence re-derives its
+//           triple and writes it at its rank (consecutive writes per warp).
 #include <cuda_runtime.h>
 
 #include "kb_device.cuh"
@@ -119,21 +120,36 @@ __global__ void summary_mark_kernel(const SummaryParams q) {
     }
 }
 
-__global__ void summary_emit_kernel(const SummaryParams q, const uint32_t* prefix, int32_t* out_src,
-                                    int32_t* out_label, int32_t* out_dst) {
-    const int64_t cap = (int64_t)q.mask + 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += stride) {
-        const unsigned long long hi = q.table[2 * i + 1];
-        if (hi == 0ull) continue;
-        const unsigned long long lo = q.table[2 * i];
-        const unsigned long long e = q.first[i];
-        if (e >= (unsigned long long)q.m) continue;
-        const uint32_t w = q.bitmap[e >> 5];
-        const uint32_t r = prefix[e >> 5] + (uint32_t)__popc(w & ((1u << (e & 31)) - 1u));
-        out_src[r] = (int32_t)(uint32_t)lo;
-        out_label[r] = (int32_t)(uint32_t)(lo >> 32);
-        out_dst[r] = (int32_t)(uint32_t)hi;
+// Walks the edges again in their order: a first occurrence re-derives its
+// triple and writes it at its rank, so a warp's writes are consecutive.
+__global__ void __launch_bounds__(kSumThreads) summary_emit_kernel(const SummaryParams q, const uint32_t* prefix,
+                                                                   int32_t* out_src, int32_t* out_label,
+                                                                   int32_t* out_dst) {
+    __shared__ int64_t s_v[2];
+    const int lane = threadIdx.x & 31;
+    const int64_t tiles = (q.m + kSumTile - 1) / kSumTile;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int64_t e0 = t * kSumTile;
+        const int64_t e1 = min(q.m, e0 + kSumTile) - 1;
+        __syncthreads();
+        if (threadIdx.x < 2) s_v[threadIdx.x] = source_in(q.row, 0, q.n - 1, threadIdx.x ? e1 : e0);
+        __syncthreads();
+        const int64_t vlo = s_v[0], vhi = s_v[1];
+#pragma unroll
+        for (int u = 0; u < kSumPer; ++u) {
+            const int64_t e = e0 + u * kSumThreads + threadIdx.x;
+            if (e >= q.m) continue;
+            const uint32_t w = q.bitmap[e >> 5];
+            if (!((w >> lane) & 1u)) continue;  // e & 31 == lane: tiles and warps are 32-aligned
+            const int64_t v = source_in(q.row, vlo, vhi, e);
+            const int64_t y0 = q.col[e];
+            const int64_t x = q.dir == 0 ? v : y0;
+            const int64_t y = q.dir == 0 ? y0 : v;
+            const uint32_t r = prefix[e >> 5] + (uint32_t)__popc(w & ((1u << lane) - 1u));
+            out_src[r] = q.lsrc[x];
+            out_label[r] = q.lab ? q.lab[e] : 0;
+            out_dst[r] = q.ldst[y];
+        }
     }
 }
 
@@ -156,7 +172,10 @@ void launch_summary_mark(const SummaryParams& q, cudaStream_t s) {
 
 void launch_summary_emit(const SummaryParams& q, const uint32_t* prefix, int32_t* out_src, int32_t* out_label,
                          int32_t* out_dst, cudaStream_t s) {
-    summary_emit_kernel<<<grid_of((int64_t)q.mask + 1, 256), 256, 0, s>>>(q, prefix, out_src, out_label, out_dst);
+    if (q.m <= 0) return;
+    const int64_t tiles = (q.m + kSumTile - 1) / kSumTile;
+    summary_emit_kernel<<<grid_of(tiles * kSumThreads, kSumThreads), kSumThreads, 0, s>>>(q, prefix, out_src,
+                                                                                       out_label, out_dst);
 }
 
 }  // namespace kb
