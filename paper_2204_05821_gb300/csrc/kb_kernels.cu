@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int le = base + u * kHubThreads + tid;
-            if (le < E) b[u] = __ldg(gather_base(p) + (w[u] & 0x7fffffff));
+            if (le < E) b[u] = gather_block(p, w[u]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kHubFinalThreads) hub_final_kernel(const Round
             for (int i = tid; i < d; i += kHubFinalThreads) {
                 const int32_t w = __ldg(p.col + rb + i);
                 const int32_t l = p.lab ? __ldg(p.lab + rb + i) : 0;
-                const uint64_t pr = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
+                const uint64_t pr = pack_pair(l, (uint32_t)w, gather_block(p, w));
                 s_pair[i] = pr;
                 if (!hub_set_contains(gset, gcap, pr)) all = false;
             }

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kWarps * 32) medium_round_kernel(const RoundPa
             int32_t b[U];
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (e0 + u * 32 + lane < re) b[u] = __ldg(gather_base(p) + (w[u] & 0x7fffffff));
+                if (e0 + u * 32 + lane < re) b[u] = gather_block(p, w[u]);
             // the next batch's neighbours and labels, issued before the gather is consumed
             int32_t w2[U], l2[U];
             const int64_t e1 = e0 + 32 * U;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kWarps * 32) medium_round_kernel(const RoundPa
                     if (e < rend) {
                         const int32_t ww = __ldg(p.col + e);
                         const int32_t ll = p.lab ? __ldg(p.lab + e) : 0;
-                        const uint64_t pr = pack_pair(ll, (uint32_t)ww, __ldg(gather_base(p) + (ww & 0x7fffffff)));
+                        const uint64_t pr = pack_pair(ll, (uint32_t)ww, gather_block(p, ww));
                         uint32_t slot = med_slot(pair_mix(pr), cmask);
                         found = false;
                         while (true) {
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) medium_cta_kernel(const RoundParams 
             int32_t b[U];
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (e0 + u * kThreads + tid < re) b[u] = __ldg(gather_base(p) + (w[u] & 0x7fffffff));
+                if (e0 + u * kThreads + tid < re) b[u] = gather_block(p, w[u]);
             int32_t w2[U], l2[U];
             const int64_t e1 = e0 + kThreads * U;
 #pragma unroll
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) medium_cta_kernel(const RoundParams 
                     if (e < rend) {
                         const int32_t ww = __ldg(p.col + e);
                         const int32_t ll = p.lab ? __ldg(p.lab + e) : 0;
-                        const uint64_t pr = pack_pair(ll, (uint32_t)ww, __ldg(gather_base(p) + (ww & 0x7fffffff)));
+                        const uint64_t pr = pack_pair(ll, (uint32_t)ww, gather_block(p, ww));
                         uint32_t slot = med_slot(pair_mix(pr), cmask);
                         found = false;
                         while (true) {

@@ -34,10 +34,17 @@ namespace {
 
 constexpr int kSmallThreads = 256;
 #ifndef KB_SMALL_MIN_BLOCKS
-#define KB_SMALL_MIN_BLOCKS 5  // caps registers at 48: 40 warps per SM
+#define KB_SMALL_MIN_BLOCKS 6  // caps registers at 40: 48 warps per SM (a few bytes spill)
 #endif
 constexpr int kSmallWarps = kSmallThreads / 32;
-constexpr int kMapCap = 2048;  // joins a CTA can aggregate (>= 2 x its vertices at the default task size)
+// Joins a CTA can aggregate (1 x its vertices at the default task size; a
+// join that finds no room goes to global memory at once).  The map is kept
+// small on purpose: shared memory comes out of the SM's L1, and the L1 also
+// tracks the kernel's many outstanding random loads.
+#ifndef KB_MAP_CAP
+#define KB_MAP_CAP 1024
+#endif
+constexpr int kMapCap = KB_MAP_CAP;
 constexpr uint64_t kMapEmpty = ~0ull;
 constexpr uint64_t kEmptyKeyBit = 1ull << 63;  // map key of an empty-signature join: bit 63 | own
 
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
                 const int64_t e = aj + (lane - sj);
                 const int32_t w = __ldcs(p.col + e);
                 const int32_t l = p.lab ? __ldcs(p.lab + e) : 0;
-                pr = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
+                pr = pack_pair(l, (uint32_t)w, gather_block(p, w));
                 const unsigned act = E == 32 ? kFull : ((1u << E) - 1u);
                 const unsigned m = __match_any_sync(act, (unsigned long long)pr) & __match_any_sync(act, (unsigned)j);
                 if (__ffs(m) - 1 == lane) {
@@ -270,7 +277,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
                         if (e0 + u < re) {
                             const int32_t w = __ldg(p.col + e0 + u);
                             const int32_t l = p.lab ? __ldg(p.lab + e0 + u) : 0;
-                            x[u] = pack_pair(l, (uint32_t)w, __ldg(gather_base(p) + (w & 0x7fffffff)));
+                            x[u] = pack_pair(l, (uint32_t)w, gather_block(p, w));
                         }
                     }
 #pragma unroll
