@@ -1457,6 +1457,8 @@ kb_status kb_create(kb_context** out, int device, void* stream) {
         return KB_ERR_CUDA;
     }
     for (auto& e : ctx->ev) cudaEventCreate(&e);
+    kb::set_medium_kernel_attributes();
+    cudaGetLastError();
     *out = ctx;
     return KB_OK;
 }

@@ -173,6 +173,9 @@ __device__ __forceinline__ uint32_t table_hi(uint64_t h, uint32_t epoch) {
 void launch_clear_round(const RoundParams& p, cudaStream_t s);
 void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s);
 void launch_medium_round(const RoundParams& p, cudaStream_t s);  // kb_medium.cu
+// Per-device kernel attributes (shared-memory carveouts); call once per device
+// before the first launch and outside any stream capture.
+void set_medium_kernel_attributes();
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s);
 void launch_hub_final(const RoundParams& p, cudaStream_t s);
 // Canonical renumbering: prefix of block minima, then ids.

@@ -50,6 +50,8 @@ kb_status scratch_address(int device, unsigned char** out) {
             return KB_ERR_CUDA;
         }
         g_scratch_ptr[device] = ptr;
+        kb::set_medium_kernel_attributes();  // once per device, on the first call
+        cudaGetLastError();
     }
     *out = reinterpret_cast<unsigned char*>(g_scratch_ptr[device]);
     return KB_OK;
