@@ -231,6 +231,31 @@ kb_status kb_summary(kb_context* ctx, const kb_graph* g, int direction, int use_
                      const int32_t* src_level, const int32_t* dst_level, int32_t* out_src,
                      int32_t* out_label, int32_t* out_dst, int64_t capacity, int64_t* count);
 
+/* Incremental refinement after a change of the graph (edges inserted, deleted
+ * or relabelled; vertex labels may change too).  The paper leaves incremental
+ * k-bisimulation as future work (Sec. "Conclusion and Future Work").  Each
+ * round re-keys only a work set -- the vertices of every previous-level block
+ * that holds a dirty vertex (changed edge list, block changed at the previous
+ * level, or an edge to such a vertex) -- and keeps the old grouping of all
+ * others; every level is renumbered canonically, so the output equals
+ * kb_refine on the new graph.
+ *   g          the NEW graph (DEVICE CSR as for kb_refine)
+ *   opt        the options the old levels were computed with (subject must be
+ *              KB_SUBJECT_PREVIOUS; the locality order is not used)
+ *   changed    DEVICE int32[n_changed]: every vertex whose edge list in the
+ *              processed direction changed (out: sources of inserted, deleted or
+ *              relabelled edges; in: their targets; both: both ends); duplicates
+ *              are fine
+ *   levels     DEVICE int32[(k+1)*n], in: kb_refine's levels of the graph before
+ *              the change (same n, same options); out: the levels of g
+ *   counts, levels_computed  as for kb_refine
+ *   work       HOST int64[k+1] or NULL: vertices re-keyed per level (level 0: n)
+ * KB_ERR_INVALID_ARG when an old level or a changed id lies outside [0, n).
+ * Scratch: about 29 B x n of library-owned device memory.  Synchronises. */
+kb_status kb_refine_update(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k,
+                           const int32_t* changed, int64_t n_changed, int32_t* levels,
+                           int64_t* counts, int* levels_computed, int64_t* work);
+
 /* kb_refine with HOST buffers: g's arrays and `levels` (int32[(k+1)*n]) are host
  * memory (pinned memory copies fastest).  The library copies the graph to the
  * device, refines, and copies every level back.  Synchronises. */

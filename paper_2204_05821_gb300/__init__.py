@@ -282,6 +282,25 @@ class Context:
             self._check(st)
         return int(cnt.value)
 
+    def refine_update(self, graph: DeviceGraph, levels, changed, options: Options = None):
+        """kb_refine_update: ``levels`` (a [k+1, n] int32 device tensor holding the
+        levels of the graph before the change, same options) is updated in place
+        to the levels of ``graph``; ``changed`` is an int32 device tensor of the
+        vertices whose edge lists changed.  Returns ``(Result, work)`` with the
+        vertices re-keyed per level."""
+        options = options or Options()
+        k = int(levels.shape[0]) - 1
+        counts = np.zeros(k + 1, dtype=np.int64)
+        work = np.zeros(k + 1, dtype=np.int64)
+        lc = ctypes.c_int(0)
+        g, o = graph.to_c(), options.to_c()
+        ch = ctypes.c_void_p(changed.data_ptr()) if changed is not None and changed.numel() else None
+        nch = int(changed.numel()) if changed is not None else 0
+        self._check(self._lib.kb_refine_update(self._h, ctypes.byref(g), ctypes.byref(o), k, ch, nch,
+                                               ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts), ctypes.byref(lc),
+                                               _np_ptr(work)))
+        return Result(levels, counts, int(lc.value)), work
+
     def refine_host(self, row_offsets, col, elabel, vlabel, k: int, options: Options = None, out=None) -> Result:
         """kb_refine_host: numpy (ideally pinned) host arrays in and out."""
         options = options or Options()

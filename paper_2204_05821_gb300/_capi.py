@@ -104,6 +104,8 @@ SIGNATURES = [
     ("kb_refine_host", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
     ("kb_refine_fixpoint", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _P, _I, _P, _P, _P, _P]),
     ("kb_summary", _I, [_P, ctypes.POINTER(KbGraph), _I, _I, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("kb_refine_update", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, ctypes.c_int64, _P, _P,
+                              _P, _P]),
     ("kb_set_timing", _I, [_P, _I]),
     ("kb_get_timing", _I, [_P, _P, _I, _P, _P, _P]),
     ("kb_refine_batch", _I, [_P, ctypes.POINTER(KbGraph), _P, _I64, _P, ctypes.POINTER(KbOptions), _P, _P, _P]),

@@ -55,6 +55,10 @@ struct kb_context {
     // summary graph: triple table, first edges, edge bitmap and its ranks
     void* sum_buf = nullptr;
     size_t sum_buf_bytes = 0;
+    // incremental refinement: bitmaps, block flags, kept minima, id ranges
+    void* upd_buf = nullptr;
+    size_t upd_buf_bytes = 0;
+    unsigned long long* d_work = nullptr;  // |W| of the current round
     cudaStream_t cap_stream = nullptr;  // non-default stream used only to capture CUDA graphs
     // timing
     bool timing = false;
@@ -673,6 +677,131 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         }
         prev_count = c;
     }
+    KB_CUDA(ctx, cudaStreamSynchronize(s));
+    return KB_OK;
+}
+
+// Incremental refinement (kb_refine_update): levels holds the levels of the
+// graph before the change (same options); each round re-keys only the work set
+// and keeps the old grouping elsewhere (see kb_update.cu), then renumbers.
+kb_status update_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k, const int32_t* changed,
+                      int64_t n_changed, int32_t* levels, int64_t* counts, int* levels_computed, int64_t* work) {
+    KB_TRY(check_graph(ctx, g, opt, k));
+    if (opt->subject != KB_SUBJECT_PREVIOUS)
+        return fail(ctx, KB_ERR_INVALID_ARG, "incremental refinement takes subject = KB_SUBJECT_PREVIOUS only");
+    if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
+    if (n_changed < 0 || (n_changed > 0 && !changed)) return fail(ctx, KB_ERR_INVALID_ARG, "bad changed list");
+    const int64_t n = g->n;
+    if (n > 0 && !levels) return fail(ctx, KB_ERR_INVALID_ARG, "levels is NULL");
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    reset_timing(ctx);
+    if (levels_computed) *levels_computed = 0;
+    if (n == 0) {
+        for (int i = 0; i <= k; ++i) counts[i] = 0;
+        if (work)
+            for (int i = 0; i <= k; ++i) work[i] = 0;
+        return KB_OK;
+    }
+    cudaStream_t s = ctx->stream;
+    Prepared R;
+    // no locality order: the dirty pass reads neighbour ids, not ranks
+    KB_TRY(prepare(ctx, g, opt, R, -1));
+    kb::RoundParams& p = R.p;
+    auto row = [&](int i) { return levels + (size_t)i * (size_t)n; };
+
+    // scratch: changed, dirty, moved and work-set bitmaps, block flags, kept
+    // minima, the old row of the current level, the new level 0, id ranges
+    const int64_t nw = (n >> 5) + 1;
+    const size_t szb = align_up(sizeof(uint32_t) * (size_t)nw), sz4 = align_up(sizeof(int32_t) * (size_t)n);
+    KB_TRY(ensure_buffer(ctx, &ctx->upd_buf, &ctx->upd_buf_bytes, 4 * szb + align_up((size_t)n) + 3 * sz4 + 4 * sz4));
+    if (!ctx->d_work && cudaMalloc(reinterpret_cast<void**>(&ctx->d_work), sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, KB_ERR_OOM, "cannot allocate a counter");
+    }
+    char* b = reinterpret_cast<char*>(ctx->upd_buf);
+    uint32_t* changed_bits = reinterpret_cast<uint32_t*>(b);
+    uint32_t* dirty = reinterpret_cast<uint32_t*>(b + szb);
+    uint32_t* moved = reinterpret_cast<uint32_t*>(b + 2 * szb);
+    uint32_t* wmask = reinterpret_cast<uint32_t*>(b + 3 * szb);
+    uint8_t* flag = reinterpret_cast<uint8_t*>(b + 4 * szb);
+    char* b2 = b + 4 * szb + align_up((size_t)n);
+    uint32_t* kmin = reinterpret_cast<uint32_t*>(b2);
+    int32_t* keep = reinterpret_cast<int32_t*>(b2 + sz4);
+    int32_t* level0 = reinterpret_cast<int32_t*>(b2 + 2 * sz4);
+    int32_t* ranges = reinterpret_cast<int32_t*>(b2 + 3 * sz4);
+
+    // the old levels must be partitions with ids in [0, n); the changed ids too
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    for (int i = 0; i <= k; ++i) kb::launch_check_ids(n, row(i), ctx->d_ctr, s);
+    KB_CUDA(ctx, cudaMemsetAsync(changed_bits, 0, szb, s));
+    kb::launch_set_bits(n, n_changed, changed, changed_bits, ctx->d_ctr, s);
+    KB_CUDA(ctx, cudaGetLastError());
+    KB_TRY(read_counters(ctx));
+    if (ctx->h_ctr->err & kb::kErrInvalid)
+        return fail(ctx, KB_ERR_INVALID_ARG, "old levels or changed vertices hold ids outside [0, n)");
+
+    // level 0 from scratch; its moved vertices start the dirty set
+    const int32_t* init_key = opt->use_vertex_labels ? g->vertex_labels : nullptr;
+    if (init_key) {
+        KB_TRY(launch_level0(ctx, R, init_key, level0, s));
+        KB_TRY(read_counters(ctx));
+        KB_TRY(device_error(ctx));
+        counts[0] = ctx->h_ctr->count;
+    } else {
+        kb::launch_fill_i32(level0, n, 0, s);
+        if (p.perm) kb::launch_fill_i32(p.gat, n, 0, s);
+        counts[0] = 1;
+    }
+    KB_CUDA(ctx, cudaMemsetAsync(wmask, 0xff, szb, s));
+    kb::launch_moved(n, wmask, row(0), level0, ranges, moved, s);
+    KB_CUDA(ctx, cudaMemcpyAsync(row(0), level0, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (work) work[0] = n;
+
+    for (int i = 1; i <= k; ++i) {
+        Timer T(ctx);
+        // dirty = changed | moved | predecessors of moved; W = their previous-level blocks
+        kb::launch_or_words(nw, changed_bits, moved, dirty, s);
+        kb::launch_dirty_from_moved(n, R.P.m_proc, p.row, p.col, moved, dirty, s);
+        KB_CUDA(ctx, cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), s));
+        kb::launch_work_set(n, row(i - 1), dirty, flag, wmask, ctx->d_work, s);
+        KB_CUDA(ctx, cudaMemcpyAsync(keep, row(i), sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        kb::launch_keep_min(n, wmask, keep, kmin, s);
+        KB_TRY(next_epoch(ctx, R, s));
+        p.ehigh = 0xffffffffu - (uint32_t)i;
+        p.prev = row(i - 1);
+        p.vmask = wmask;
+        p.keep_old = keep;
+        p.kmin = kmin;
+        KB_TRY(launch_round_body(ctx, R, s, &T));
+        kb::launch_keep_bits(n, wmask, keep, kmin, p.bitmap, s);
+        T.begin(KB_KERNEL_RENUMBER);
+        kb::launch_renumber(p, R.prefix, R.scan_tmp, row(i), s);
+        T.end();
+        kb::launch_moved(n, wmask, keep, row(i), ranges, moved, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_TRY(read_counters(ctx));
+        ctx->round_ms.push_back(T.collect());
+        KB_TRY(device_error(ctx));
+        counts[i] = ctx->h_ctr->count;
+        if (work) {
+            unsigned long long w = 0;
+            KB_CUDA(ctx, cudaMemcpy(&w, ctx->d_work, sizeof(w), cudaMemcpyDeviceToHost));
+            work[i] = (int64_t)w;
+        }
+        if (levels_computed) *levels_computed = i;
+        if (opt->early_stop && counts[i] == counts[i - 1]) {
+            if (i < k) kb::launch_copy_rows(levels, n, i, i + 1, k, s);
+            for (int j = i + 1; j <= k; ++j) {
+                counts[j] = counts[i];
+                if (work) work[j] = 0;
+            }
+            KB_CUDA(ctx, cudaGetLastError());
+            break;
+        }
+    }
+    p.vmask = nullptr;
+    p.keep_old = nullptr;
+    p.kmin = nullptr;
     KB_CUDA(ctx, cudaStreamSynchronize(s));
     return KB_OK;
 }
@@ -1481,6 +1610,8 @@ kb_status kb_destroy(kb_context* ctx) {
     cudaFree(ctx->tune_buf);
     cudaFree(ctx->fix_buf);
     cudaFree(ctx->sum_buf);
+    cudaFree(ctx->upd_buf);
+    cudaFree(ctx->d_work);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -1523,6 +1654,12 @@ kb_status kb_refine_from(kb_context* ctx, const kb_graph* g, const kb_options* o
     if (!ctx) return KB_ERR_INVALID_ARG;
     if (!start && g && g->n > 0) return fail(ctx, KB_ERR_INVALID_ARG, "start is NULL");
     return refine_impl(ctx, g, opt, start, i_start, k, levels, counts, levels_computed);
+}
+
+kb_status kb_refine_update(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k, const int32_t* changed,
+                           int64_t n_changed, int32_t* levels, int64_t* counts, int* levels_computed, int64_t* work) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    return update_impl(ctx, g, opt, k, changed, n_changed, levels, counts, levels_computed, work);
 }
 
 kb_status kb_summary(kb_context* ctx, const kb_graph* g, int direction, int use_edge_labels,

@@ -36,6 +36,7 @@ __device__ __forceinline__ void join_slot(const RoundParams& p, uint64_t pos, ui
 }
 
 __device__ __forceinline__ bool vertex_active(const RoundParams& p, int64_t v) {
+    if (p.vmask && !((p.vmask[v >> 5] >> (v & 31)) & 1u)) return false;
     return !p.gactive || p.gactive[p.vgraph[v]];
 }
 

@@ -60,6 +60,13 @@ struct RoundParams {
     // id (< n) per vertex; nullptr keys by the own previous block (stratified
     // bisimulation).
     const int32_t* own_key;
+    // Incremental refinement (kb_refine_update): only vertices with their bit
+    // set in vmask are re-keyed; every other vertex keeps its old grouping at
+    // this level: keep_old is the level's old row and kmin[b] the smallest
+    // such vertex of old block b.  nullptr when every vertex is re-keyed.
+    const uint32_t* vmask;
+    const int32_t* keep_old;
+    const uint32_t* kmin;
     int32_t hub_threshold;
     int32_t small_max;    // min(kSmallDegree, hub_threshold)
     int32_t warp_verts;   // vertices per warp task of the small-vertex kernel
@@ -245,6 +252,19 @@ void launch_summary_emit(const SummaryParams& q, const uint32_t* prefix, int32_t
 void launch_iota_i32(int32_t* out, int64_t n, cudaStream_t s);
 // ctr->diff |= (a != b) over n entries (kb_kernels.cu)
 void launch_levels_differ(const int32_t* a, const int32_t* b, int64_t n, Counters* ctr, cudaStream_t s);
+// Incremental refinement (kb_update.cu)
+void launch_dirty_from_moved(int64_t n, int64_t m, const int64_t* row, const int32_t* col, const uint32_t* moved,
+                             uint32_t* dirty, cudaStream_t s);
+void launch_or_words(int64_t nw, const uint32_t* a, const uint32_t* b, uint32_t* out, cudaStream_t s);
+void launch_work_set(int64_t n, const int32_t* prev, const uint32_t* dirty, uint8_t* flag, uint32_t* wmask,
+                     unsigned long long* count, cudaStream_t s);
+void launch_keep_min(int64_t n, const uint32_t* wmask, const int32_t* old, uint32_t* kmin, cudaStream_t s);
+void launch_keep_bits(int64_t n, const uint32_t* wmask, const int32_t* old, const uint32_t* kmin, uint32_t* bitmap,
+                      cudaStream_t s);
+void launch_moved(int64_t n, const uint32_t* wmask, const int32_t* old, const int32_t* cur, int32_t* ranges,
+                  uint32_t* moved, cudaStream_t s);
+void launch_check_ids(int64_t n, const int32_t* a, Counters* ctr, cudaStream_t s);
+void launch_set_bits(int64_t n, int64_t count, const int32_t* ids, uint32_t* bits, Counters* ctr, cudaStream_t s);
 void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,
                      cudaStream_t s);
 // Copy row src of the level store to the rows [first, last] of levels.

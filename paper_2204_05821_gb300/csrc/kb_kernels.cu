@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
     const uint64_t ext = p.chunk_ext[c];
     const int64_t e0 = (int64_t)(ext >> 16);
     const int E = (int)(ext & 0xffffu);
-    if (batched(p) && !vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
+    if ((batched(p) || p.vmask) && !vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
     if (tid == 0) {
         s_nuniq = 0;
         s_nnew = 0;
@@ -386,16 +386,18 @@ __global__ void __launch_bounds__(kScanThreads) popc_scan_kernel(const uint32_t*
 __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const uint32_t* prefix, int32_t* out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
-        if (!vertex_active(p, v)) {
-            const int32_t g = p.vgraph[v];
-            const int32_t b = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
-            out[v] = b;
-            if (p.perm) p.gat[p.perm[v]] = b;
-            continue;
-        }
-        const uint32_t bw = p.bitmap[v >> 5];
         uint32_t mn = (uint32_t)v;
-        if (!((bw >> (v & 31)) & 1u)) {
+        if (!vertex_active(p, v)) {
+            if (!p.vmask) {  // a batched graph that stopped: its ids shift with the graphs before it
+                const int32_t g = p.vgraph[v];
+                const int32_t b = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
+                out[v] = b;
+                if (p.perm) p.gat[p.perm[v]] = b;
+                continue;
+            }
+            mn = p.kmin[p.keep_old[v]];  // incremental: the smallest kept member of its old block
+            if ((int64_t)mn >= p.n) mn = (uint32_t)v;
+        } else if (!((p.bitmap[v >> 5] >> (v & 31)) & 1u)) {
             const uint32_t sl = (uint32_t)p.slot_of[v];
             if (sl & 0x80000000u)
                 mn = (uint32_t)p.emin[(sl & 0x7fffffffu) % (uint32_t)p.n];
