@@ -519,9 +519,6 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
 // Advance the table epoch (entries of other epochs read as empty); the table
 // is cleared once every 255 rounds.
 kb_status next_epoch(kb_context* ctx, Prepared& R, cudaStream_t s) {
-#ifdef KB_DIRECT_CAS
-    if (R.epoch > 0) KB_CUDA(ctx, cudaMemsetAsync(R.p.table, 0, sizeof(uint64_t) * (size_t)R.P.cap, s));
-#endif
     if (R.epoch == 255) {
         KB_CUDA(ctx, cudaMemsetAsync(R.p.table, 0, sizeof(uint64_t) * (size_t)R.P.cap, s));
         R.epoch = 0;

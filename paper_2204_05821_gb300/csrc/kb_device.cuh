@@ -78,28 +78,6 @@ __device__ __forceinline__ void join_empty(const RoundParams& p, int32_t own, ui
 __device__ __forceinline__ int probe_table(const RoundParams& p, uint64_t* pos_io, uint32_t hi, uint32_t v,
                                            uint32_t* rep, bool toggle = true) {
     uint64_t pos = *pos_io;
-#ifdef KB_DIRECT_CAS
-    // the table is cleared before every round: an empty slot is 0, so one CAS
-    // both claims an empty slot and returns the occupant of a full one
-    for (int it = 0; it < kProbeLimit; ++it) {
-        const uint64_t want = ((uint64_t)hi << 32) | v;
-        const uint64_t cur = atomicCAS(reinterpret_cast<unsigned long long*>(&p.table[pos]), 0ull,
-                                       (unsigned long long)want);
-        if (cur == 0ull) {
-            p.slot_of[v] = (int32_t)pos;
-            if (toggle) toggle_min(p.bitmap, v);
-            *pos_io = pos;
-            return 0;
-        }
-        if ((uint32_t)(cur >> 32) == hi) {
-            *rep = (uint32_t)cur;
-            *pos_io = pos;
-            return 1;
-        }
-        pos = (pos + 1) & p.mask;
-    }
-    return 2;
-#endif
     for (int it = 0; it < kProbeLimit; ++it) {
         uint64_t cur = volatile_load(&p.table[pos]);
         if ((uint32_t)(cur >> 56) != p.epoch) {

@@ -119,11 +119,7 @@ __host__ __device__ __forceinline__ const int32_t* gather_base(const RoundParams
 
 // The previous block of neighbour word w (bit 31: direction).
 __device__ __forceinline__ int32_t gather_block(const RoundParams& p, int32_t w) {
-#ifdef KB_GATHER_CG
-    return __ldcg(gather_base(p) + (w & 0x7fffffff));
-#else
     return __ldg(gather_base(p) + (w & 0x7fffffff));
-#endif
 }
 
 // ---------------------------------------------------------------- hashing
