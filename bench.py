@@ -280,7 +280,7 @@ def run_ours(args, rank, world, local):
     for _ in range(args.steps):
         r = step()
         rounds += r.levels_computed
-        _, fam = ctx.timing()
+        round_ms, fam = ctx.timing()
         for name, (ms, cnt) in fam.items():
             fam_ms[name] = fam_ms.get(name, 0.0) + ms
             fam_n[name] = fam_n.get(name, 0) + cnt
@@ -304,24 +304,40 @@ def run_ours(args, rank, world, local):
     counts_last = [int(x) for x in r.counts]
     del r
 
-    # roofline of the dominant kernel family (algorithmic bytes per launch)
+    # roofline of the dominant kernel family (algorithmic bytes per launch).
+    # A round skips the blocks that cannot change (a vertex alone in its
+    # previous block; from the second round on, the edgeless vertices, whose
+    # blocks were formed by a round), so a launch's units are the edges and
+    # vertices of the others: averaged over the rounds of the last step.
     hub_thr, small_max = (args.hub_threshold or 1024), 32
     deg = (wl["row_offsets"][1:] - wl["row_offsets"][:-1])
-    small = deg <= small_max
-    hub = deg > hub_thr
-    med = ~small & ~hub
-    small_edges = int(deg[small].sum().item())
-    med_edges = int(deg[med].sum().item())
-    hub_edges = m - small_edges - med_edges
-    n_small, n_med, n_hubs = int(small.sum().item()), int(med.sum().item()), int(hub.sum().item())
-    del deg, small, hub, med
+    cls_small = deg <= small_max
+    cls_hub = deg > hub_thr
+    cls_med = ~cls_small & ~cls_hub
+    vertex_classes = {"small_le32": [int(cls_small.sum().item()), int(deg[cls_small].sum().item())],
+                      "medium": [int(cls_med.sum().item()), int(deg[cls_med].sum().item())],
+                      "hub_gt%d" % hub_thr: [int(cls_hub.sum().item()), int(deg[cls_hub].sum().item())]}
+    lc = max(1, rounds // max(1, args.steps))
+    units = {"small_edges": 0, "med_edges": 0, "hub_edges": 0, "n_small": 0, "n_med": 0, "n_hubs": 0}
+    for i in range(1, lc + 1):
+        prev = levels[i - 1].long()
+        active = torch.bincount(prev, minlength=n)[prev] > 1
+        if i >= 2:
+            active &= deg > 0
+        for name, cls in (("small", cls_small), ("med", cls_med), ("hub", cls_hub)):
+            sel = active & cls
+            units[name + "_edges"] += int(deg[sel].sum().item())
+            units["n_" + ("hubs" if name == "hub" else name)] += int(sel.sum().item())
+        del prev, active, sel
+    units = {key: val / lc for key, val in units.items()}
+    del deg, cls_small, cls_hub, cls_med
     algo_bytes = {
         # 12 B per edge (neighbour id 4, edge label 4, gathered block 4) and per
         # vertex 24 B (row offset 8, own block 4, slot write 4, table entry 8)
-        "small": 12 * small_edges + 24 * n_small,
-        "medium": 12 * med_edges + 28 * n_med,
-        "hub_chunk": 12 * hub_edges,
-        "hub_final": 24 * n_hubs,
+        "small": 12 * units["small_edges"] + 24 * units["n_small"],
+        "medium": 12 * units["med_edges"] + 28 * units["n_med"],
+        "hub_chunk": 12 * units["hub_edges"],
+        "hub_final": 24 * units["n_hubs"],
         # per vertex: slot 4, table entry 8, level write 4; bitmap read twice
         "renumber": 16 * n + n // 4,
         "other": n // 8,
@@ -335,10 +351,12 @@ def run_ours(args, rank, world, local):
                 "algorithmic_bytes_per_launch": algo_bytes.get(dom, 0),
                 "kernel_share": {kname: fam_ms[kname] / sum(fam_ms.values()) for kname in fam_ms},
                 "per_launch_ms": {kname: fam_ms[kname] / max(1, fam_n[kname]) for kname in fam_ms}}
-    # our kernels per family event: renumbering is 4 kernels; per call add the
-    # setup kernels (validation, classification, hub search) and level 0 (5)
-    per_event = {"small": 1, "medium": 1, "hub_chunk": 1, "hub_final": 1, "renumber": 4, "other": 0}
-    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 8 * args.steps
+    # our kernels per family event: renumbering is 4 kernels and the singleton
+    # pass, "other" the per-hub set clearing; per call add the setup kernels
+    # (validation, classification, hub search, chunk extents) and level 0
+    # (small kernel, renumbering, singleton pass)
+    per_event = {"small": 1, "medium": 1, "hub_chunk": 1, "hub_final": 1, "renumber": 5, "other": 1}
+    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 10 * args.steps
 
     # end to end through the host-buffer entry point, pinned host memory
     e2e = None
@@ -434,12 +452,13 @@ def run_ours(args, rank, world, local):
                 "warmup": args.warmup, "ms_per_step": 1000 * elapsed / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
                 "config": dict(describe(args.workload, cfg, k, "out"),
-                               vertex_classes={"small_le32": [n_small, small_edges], "medium": [n_med, med_edges],
-                                               "hub_gt%d" % hub_thr: [n_hubs, hub_edges]},
+                               vertex_classes=vertex_classes,
+                               units_per_round=units,
                                counts_last_step=counts_last,
                                l2="inputs larger than L2 (CSR %.1f GB); no flush" % ((8 * (n + 1) + 8 * m) / 1e9),
                                parallelism="replicas" if world > 1 else "single GPU",
-                               rounds_per_step=rounds / args.steps),
+                               rounds_per_step=rounds / args.steps,
+                               kernel_ms_per_round_last_step=[round(x, 2) for x in round_ms]),
                 "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
                 "batch": batch_info, "serve": serve_info, "next_rows": next_rows}
         if not args.no_cpu_baseline and world == 1:

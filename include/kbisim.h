@@ -116,7 +116,15 @@ typedef struct {
  *                      labels, no edge labels, in.  Such levels need not refine one
  *                      another: early stop then compares whole levels (one extra pass).
  *                      Single-graph calls only (KB_ERR_INVALID_ARG in batched, served
- *                      and allocation-free refinement). */
+ *                      and allocation-free refinement).
+ *   rekey_all          0 (default): single-graph stratified rounds (subject
+ *                      KB_SUBJECT_PREVIOUS) skip the blocks that cannot change, since
+ *                      keys hold the own previous block: a block of one vertex stays
+ *                      one vertex, and a block formed by a round from vertices
+ *                      without edges (keys (own block, empty set)) stays as it is;
+ *                      such vertices keep their block without being re-keyed.
+ *                      1: re-key every vertex every round.  Results are identical
+ *                      either way. */
 typedef struct {
     int32_t direction;
     int32_t use_vertex_labels;
@@ -129,7 +137,8 @@ typedef struct {
     int32_t small_task_vertices;
     int32_t reorder;
     int32_t subject;
-    int32_t reserved[5];
+    int32_t rekey_all;
+    int32_t reserved[4];
 } kb_options;
 
 enum { KB_SUBJECT_PREVIOUS = 0, KB_SUBJECT_ALL = 1, KB_SUBJECT_LABEL = 2, KB_SUBJECT_ID = 3 };

@@ -51,6 +51,7 @@ class Options:
     small_task_vertices: int = 0
     reorder: int = 0  # 0 automatic, 1 off, 2 on
     subject: int = 0  # SUBJECT_PREVIOUS, SUBJECT_ALL, SUBJECT_LABEL or SUBJECT_ID (generic CSE rounds)
+    rekey_all: bool = False  # True: re-key every vertex every round (no skipping of frozen blocks)
 
     @classmethod
     def schaetzle(cls, **kw) -> "Options":
@@ -75,6 +76,7 @@ class Options:
         o.small_task_vertices = int(self.small_task_vertices)
         o.reorder = int(self.reorder)
         o.subject = int(self.subject)
+        o.rekey_all = int(bool(self.rekey_all))
         return o
 
 
@@ -191,7 +193,8 @@ class Context:
         import torch
 
         key = (graph.row_offsets.data_ptr(), graph.n, graph.m, options.direction, options.hub_threshold,
-               options.load_factor, options.use_edge_labels, options.reorder, k)
+               options.load_factor, options.use_edge_labels, options.reorder, options.subject,
+               bool(options.rekey_all), k)
         if self._ws is not None and self._ws_key == key:
             return
         need = self.workspace_size(graph, k, options)

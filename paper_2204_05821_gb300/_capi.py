@@ -50,7 +50,8 @@ class KbOptions(ctypes.Structure):
         ("small_task_vertices", ctypes.c_int32),
         ("reorder", ctypes.c_int32),
         ("subject", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("rekey_all", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 

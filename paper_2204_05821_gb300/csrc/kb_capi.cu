@@ -114,6 +114,7 @@ struct Plan {
     uint64_t cap = 0;
     bool reorder = false;  // locality order of the gather (RoundParams::perm)
     int subject = 0;       // kb_options::subject (generic CSE rounds when > 0)
+    bool freeze = false;   // frozen blocks skip the rounds (RoundParams::frozen)
     // hubs (host copies, ascending vertex id)
     std::vector<int32_t> hub_v;
     std::vector<int64_t> chunk_off, set_off;
@@ -122,7 +123,8 @@ struct Plan {
     size_t o_rowp = 0, o_colp = 0, o_labp = 0, o_cursor = 0, o_inpref = 0, o_i64tmp = 0;
     size_t csr_bytes = 0;
     size_t o_emin = 0, o_med = 0, o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
-           o_chunkhub = 0, o_chunkext = 0, o_perm = 0, o_gat = 0, o_colr = 0, o_hist = 0, o_ownkey = 0, o_acc = 0, o_cnt = 0, o_sets = 0;
+           o_chunkhub = 0, o_chunkext = 0, o_perm = 0, o_gat = 0, o_colr = 0, o_hist = 0, o_ownkey = 0, o_acc = 0, o_cnt = 0, o_sets = 0,
+           o_frozen = 0, o_fmin = 0, o_edgeless = 0, o_shared = 0;
     size_t total = 0;
 };
 
@@ -169,6 +171,10 @@ void layout_round(Plan& P) {
     P.o_colr = take(P.reorder && !needs_in_csr(P.dir) ? sizeof(int32_t) * (size_t)P.m_proc : 0);
     P.o_hist = take(P.reorder ? sizeof(unsigned long long) * 512 : 0);
     P.o_ownkey = take(P.subject ? sizeof(int32_t) * (size_t)P.n : 0);
+    P.o_frozen = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_fmin = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_edgeless = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_shared = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.total = off;
 }
 
@@ -297,6 +303,10 @@ kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, P
     P.subject = opt->subject;
     P.reorder = rounds >= 0 && P.n > 0 && P.m_proc > 0 &&
                 (opt->reorder == 2 || (opt->reorder == 0 && rounds >= 24 && P.m_proc >= ((int64_t)1 << 22)));
+    // single-graph stratified rounds only: batched, served and incremental
+    // refinement plan with rounds < 0, and generic CSE keys need not hold the
+    // own previous block
+    P.freeze = rounds >= 0 && P.subject == KB_SUBJECT_PREVIOUS && opt->rekey_all == 0;
     P.labels = opt->use_edge_labels && g->edge_labels != nullptr;
     int thr = opt->hub_threshold ? opt->hub_threshold : ctx->tuned_hub_threshold;
     P.thr = thr > 0 ? thr : kb::kDefaultHubThreshold;
@@ -385,6 +395,11 @@ struct Prepared {
     int64_t total_chunks = 0;
     size_t set_bytes = 0;
     uint32_t epoch = 0;
+    // frozen blocks for the next round and their minima, edgeless vertices
+    // (Plan::freeze; RoundParams::frozen)
+    uint32_t* frozen = nullptr;
+    uint32_t* frozen_min = nullptr;
+    uint32_t* edgeless = nullptr;
 };
 
 // Validate, plan, acquire the workspace, bind the round parameters, list the
@@ -513,6 +528,19 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
     R.set_bytes = sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0);
     KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
     R.epoch = 0;
+    if (P.freeze) {
+        // nothing frozen before the starting level; shared starts empty
+        const size_t bw = sizeof(uint32_t) * (size_t)((n >> 5) + 1);
+        R.frozen = reinterpret_cast<uint32_t*>(ws + P.o_frozen);
+        R.frozen_min = reinterpret_cast<uint32_t*>(ws + P.o_fmin);
+        R.edgeless = reinterpret_cast<uint32_t*>(ws + P.o_edgeless);
+        p.shared = reinterpret_cast<uint32_t*>(ws + P.o_shared);
+        KB_CUDA(ctx, cudaMemsetAsync(R.frozen, 0, bw, s));
+        KB_CUDA(ctx, cudaMemsetAsync(R.frozen_min, 0, bw, s));
+        KB_CUDA(ctx, cudaMemsetAsync(p.shared, 0, bw, s));
+        kb::launch_edgeless_bits(n, p.row, R.edgeless, s);
+        KB_CUDA(ctx, cudaGetLastError());
+    }
     return KB_OK;
 }
 
@@ -534,8 +562,13 @@ kb_status launch_level0(kb_context* ctx, Prepared& R, const int32_t* key, int32_
     KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
     KB_CUDA(ctx, cudaMemsetAsync(R.p.bitmap, 0, sizeof(uint32_t) * (size_t)((R.p.n >> 5) + 1), s));
     R.p.prev = key;
+    R.p.frozen = nullptr;
+    R.p.frozen_min = nullptr;
     kb::launch_small_round(R.p, true, s);
     kb::launch_renumber(R.p, R.prefix, R.scan_tmp, out, s);
+    // a starting level may mix edgeless vertices with others in one block:
+    // only its singletons are frozen in the first round
+    if (R.p.shared) kb::launch_freeze(R.p.n, R.p.bitmap, R.p.shared, nullptr, R.frozen, R.frozen_min, s);
     KB_CUDA(ctx, cudaGetLastError());
     return KB_OK;
 }
@@ -546,7 +579,10 @@ kb_status launch_round_body(kb_context* ctx, Prepared& R, cudaStream_t s, Timer*
     if (T) T->begin(KB_KERNEL_OTHER);
     KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
     kb::launch_clear_round(p, s);
-    if (R.set_bytes) KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, R.set_bytes, s));
+    if (p.frozen)
+        kb::launch_clear_hub_sets(p, (int64_t)(R.set_bytes / sizeof(uint64_t)), s);
+    else if (R.set_bytes)
+        KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, R.set_bytes, s));
     if (T) T->end();
     if (T) T->begin(KB_KERNEL_SMALL);
     kb::launch_small_round(p, false, s);
@@ -646,10 +682,15 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         p.ehigh = 0xffffffffu - (uint32_t)(i - i_start);
         p.prev = rows.row(i - 1);
         p.own_key = R.P.subject ? reinterpret_cast<const int32_t*>(R.ws + R.P.o_ownkey) : nullptr;
+        p.frozen = R.frozen;
+        p.frozen_min = R.frozen_min;
         int32_t* out = rows.row(i);
         KB_TRY(launch_round_body(ctx, R, s, &T));
         T.begin(KB_KERNEL_RENUMBER);
         kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
+        // a block formed by this round that holds an edgeless vertex holds only
+        // edgeless vertices with one previous block: frozen from now on
+        if (p.shared) kb::launch_freeze(n, p.bitmap, p.shared, R.edgeless, R.frozen, R.frozen_min, s);
         T.end();
         // CSE levels need not refine each other: compare whole levels
         if (R.P.subject) kb::launch_levels_differ(out, p.prev, n, ctx->d_ctr, s);

@@ -46,9 +46,14 @@ __device__ __forceinline__ bool vertex_level0(const RoundParams& p, int64_t v) {
     return p.gmode && p.gmode[p.vgraph[v]] == 1;
 }
 
-// Active and refining by signature (not in level-0 mode).
+// In a frozen block (RoundParams::frozen): it keeps its previous block.
+__device__ __forceinline__ bool vertex_frozen(const RoundParams& p, int64_t v) {
+    return p.frozen && ((__ldg(p.frozen + (v >> 5)) >> (v & 31)) & 1u);
+}
+
+// Active and refining by signature (not in level-0 mode, not frozen).
 __device__ __forceinline__ bool vertex_refines(const RoundParams& p, int64_t v) {
-    return vertex_active(p, v) && !vertex_level0(p, v);
+    return vertex_active(p, v) && !vertex_level0(p, v) && !vertex_frozen(p, v);
 }
 
 // In multi-graph runs a representative must belong to the same graph.

@@ -67,6 +67,19 @@ struct RoundParams {
     const uint32_t* vmask;
     const int32_t* keep_old;
     const uint32_t* kmin;
+    // Frozen blocks (stratified rounds, whose keys hold the own previous block):
+    // a block that cannot change this round, because it has one member (a
+    // vertex alone in its previous block stays alone) or because all its
+    // members have no edges and it was formed by a signature round (their keys
+    // are then (own block, empty set) alike).  Bit v of frozen: v is skipped by
+    // the round kernels; frozen_min holds the minima of frozen blocks and
+    // starts the round's bitmap of minima; a skipped vertex that is not a
+    // minimum keeps its slot_of entry of the round that formed its block.  The
+    // renumbering sets bit b of shared for every block minimum b that another
+    // vertex points to.  All nullptr when every vertex is re-keyed.
+    const uint32_t* frozen;
+    const uint32_t* frozen_min;
+    uint32_t* shared;
     int32_t hub_threshold;
     int32_t small_max;    // min(kSmallDegree, hub_threshold)
     int32_t warp_verts;   // vertices per warp task of the small-vertex kernel
@@ -172,8 +185,19 @@ __device__ __forceinline__ uint32_t table_hi(uint64_t h, uint32_t epoch) {
 }
 
 // ---------------------------------------------------------------- launchers
-// Signature rounds (kb_kernels.cu)
+// Signature rounds (kb_kernels.cu).  The round's bitmap of block minima starts
+// as p.frozen_min (or empty).
 void launch_clear_round(const RoundParams& p, cudaStream_t s);
+// Empty the hub sets of the hubs that refine this round.
+void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream_t s);
+// After the renumbering: the frozen blocks of the next round.  single = block
+// minima no other vertex points to (bitmap & ~shared); frozen = single, plus
+// the edgeless vertices when edgeless != nullptr; frozen_min = single plus the
+// edgeless minima; shared is emptied for the next round.
+void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless, uint32_t* frozen,
+                   uint32_t* frozen_min, cudaStream_t s);
+// Bit v set iff v has no edges in the processed CSR.
+void launch_edgeless_bits(int64_t n, const int64_t* row, uint32_t* bits, cudaStream_t s);
 void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s);
 void launch_medium_round(const RoundParams& p, cudaStream_t s);  // kb_medium.cu
 // Per-device kernel attributes (shared-memory carveouts); call once per device

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
     const uint64_t ext = p.chunk_ext[c];
     const int64_t e0 = (int64_t)(ext >> 16);
     const int E = (int)(ext & 0xffffu);
-    if ((batched(p) || p.vmask) && !vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
+    if ((batched(p) || p.vmask || p.frozen) && !vertex_refines(p, p.hub_v[h])) return;  // uniform over the CTA
     if (tid == 0) {
         s_nuniq = 0;
         s_nnew = 0;
@@ -383,10 +383,23 @@ __global__ void __launch_bounds__(kScanThreads) popc_scan_kernel(const uint32_t*
     }
 }
 
+// Shared-block marks (RoundParams::shared) go through a small direct-mapped
+// cache of the minima this CTA marked already: a block with millions of
+// members (all edgeless vertices with one label) would otherwise send one
+// atomic per member to a single word.
+constexpr int kMarkCache = 1024;
+constexpr uint32_t kNoMark = 0xffffffffu;
+
 __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const uint32_t* prefix, int32_t* out) {
+    __shared__ uint32_t s_mark[kMarkCache];
+    if (p.shared) {
+        for (int i = threadIdx.x; i < kMarkCache; i += blockDim.x) s_mark[i] = kNoMark;
+        __syncthreads();
+    }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
         uint32_t mn = (uint32_t)v;
+        uint32_t mark = kNoMark;
         if (!vertex_active(p, v)) {
             if (!p.vmask) {  // a batched graph that stopped: its ids shift with the graphs before it
                 const int32_t g = p.vgraph[v];
@@ -404,11 +417,93 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
             else
                 mn = (uint32_t)(p.table[(uint64_t)sl & p.mask] & 0xffffffffu);
             if ((int64_t)mn >= p.n) mn = (uint32_t)v;  // only after a reported device error
+            mark = mn;  // v is not the minimum: its block has another member
         }
         const uint32_t mw = p.bitmap[mn >> 5];
         const int32_t b = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
         out[v] = b;
         if (p.perm) p.gat[p.perm[v]] = b;
+        if (p.shared) {
+            // one lane per distinct minimum in the warp, then the CTA's cache,
+            // then an L2 read: an atomic on a bit already set costs far more
+            // than the read (batched and incremental runs, which leave the
+            // loop early above, have no shared marks)
+            const unsigned grp = __match_any_sync(__activemask(), mark);
+            if (mark != kNoMark && (int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+                const uint32_t c = (mark * 2654435761u) >> 22;
+                if (s_mark[c] != mark) {
+                    s_mark[c] = mark;
+                    const uint32_t bit = 1u << (mark & 31);
+                    if (!(__ldcg(p.shared + (mark >> 5)) & bit)) atomicOr(&p.shared[mark >> 5], bit);
+                }
+            }
+        }
+    }
+}
+
+// the frozen blocks of the next round (see launch_freeze)
+__global__ void freeze_kernel(int64_t nw, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
+                              uint32_t* frozen, uint32_t* frozen_min) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
+        const uint32_t b = bitmap[i];
+        const uint32_t single = b & ~shared[i];
+        const uint32_t e = edgeless ? edgeless[i] : 0u;
+        frozen[i] = single | e;
+        frozen_min[i] = single | (b & e);
+        shared[i] = 0u;
+    }
+}
+
+__global__ void edgeless_bits_kernel(int64_t n, const int64_t* row, uint32_t* bits) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;  // blockDim is a multiple of 32: a warp covers one word
+        const bool e = v < n && row[v + 1] == row[v];
+        const unsigned w = __ballot_sync(kFull, e);
+        if ((threadIdx.x & 31) == 0 && (v >> 5) <= (n >> 5)) bits[v >> 5] = w;
+    }
+}
+
+// Refill the sets of the hubs that refine this round with the empty pair, in
+// tiles of kClearTile consecutive slots of all sets together (one hub's set
+// can hold 10^8 slots; large tiles keep the per-tile search for the first hub
+// rare).  Sets hold at least 64 slots, so a tile overlaps at most
+// kClearTile / 64 + 1 hubs; they start at multiples of 4 slots, so a 16-byte
+// store never straddles two sets.
+constexpr int kClearTile = 65536;
+constexpr int kClearHubs = kClearTile / 64 + 1;
+
+__global__ void __launch_bounds__(256) clear_hub_sets_kernel(const RoundParams p) {
+    __shared__ int s_h0;
+    __shared__ int64_t s_end[kClearHubs];
+    __shared__ uint8_t s_ref[kClearHubs];
+    const int64_t total = p.hub_set_off[p.n_hubs];
+    const int64_t t0 = (int64_t)blockIdx.x * kClearTile;
+    const int64_t t1 = min(total, t0 + kClearTile);
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = p.n_hubs - 1;  // first hub whose set ends after t0
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (p.hub_set_off[mid + 1] > t0) hi = mid; else lo = mid + 1;
+        }
+        s_h0 = lo;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kClearHubs; i += blockDim.x) {
+        const int h = s_h0 + i;
+        const bool in = h < p.n_hubs && p.hub_set_off[h] < t1;
+        s_end[i] = in ? p.hub_set_off[h + 1] : t1;
+        s_ref[i] = in && vertex_refines(p, p.hub_v[h]);
+        if (!in) break;  // later entries keep their stale values: the walk below stops at this one
+    }
+    __syncthreads();
+    ulonglong2* sets2 = reinterpret_cast<ulonglong2*>(p.hub_sets);
+    const ulonglong2 e = make_ulonglong2(kEmptyPair, kEmptyPair);
+    int j = 0;
+    for (int64_t s = t0 + 2 * threadIdx.x; s < t1; s += 2 * blockDim.x) {
+        while (j < kClearHubs - 1 && s_end[j] <= s) ++j;
+        if (s_ref[j]) sets2[s >> 1] = e;
     }
 }
 
@@ -491,11 +586,30 @@ int grid_for(int64_t n, int threads) {
 }  // namespace
 
 void launch_clear_round(const RoundParams& p, cudaStream_t s) {
-    cudaMemsetAsync(p.bitmap, 0, sizeof(uint32_t) * (size_t)((p.n >> 5) + 1), s);
+    const size_t bytes = sizeof(uint32_t) * (size_t)((p.n >> 5) + 1);
+    if (p.frozen_min)
+        cudaMemcpyAsync(p.bitmap, p.frozen_min, bytes, cudaMemcpyDeviceToDevice, s);
+    else
+        cudaMemsetAsync(p.bitmap, 0, bytes, s);
     if (p.n_hubs > 0) {
         cudaMemsetAsync(p.hub_acc, 0, sizeof(uint64_t) * (size_t)p.n_hubs, s);
         cudaMemsetAsync(p.hub_cnt, 0, sizeof(uint32_t) * (size_t)p.n_hubs, s);
     }
+}
+
+void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream_t s) {
+    if (p.n_hubs <= 0 || total_slots <= 0) return;
+    clear_hub_sets_kernel<<<(unsigned)((total_slots + kClearTile - 1) / kClearTile), 256, 0, s>>>(p);
+}
+
+void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless, uint32_t* frozen,
+                   uint32_t* frozen_min, cudaStream_t s) {
+    const int64_t nw = (n >> 5) + 1;
+    if (n > 0) freeze_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, bitmap, shared, edgeless, frozen, frozen_min);
+}
+
+void launch_edgeless_bits(int64_t n, const int64_t* row, uint32_t* bits, cudaStream_t s) {
+    if (n > 0) edgeless_bits_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, row, bits);
 }
 
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s) {

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
         bool l0 = kLevel0;
         const int64_t cur_a = pf_a, cur_b = pf_b;
         const int32_t cur_own = pf_own;
-        if (lane < nvw && vertex_active(p, v)) {
+        if (lane < nvw && vertex_active(p, v) && !vertex_frozen(p, v)) {
             if (!kLevel0 && vertex_level0(p, v)) {
                 l0 = true;
                 own = p.vlab ? p.vlab[v] : 0;

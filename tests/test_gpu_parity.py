@@ -292,6 +292,70 @@ def test_subtile_boundaries(ctx):
     assert_same(ctx, g, 0, True, True, 4, hash_mode=1)
 
 
+# ---------------------------------------------------------------- singleton blocks
+
+
+def test_singletons_random_tiny(ctx):
+    # rounds skip vertices alone in their previous block; re-keying them gives
+    # the same levels, and both equal the oracle
+    rng = np.random.Generator(np.random.PCG64(33))
+    for _ in range(100):
+        g = graphgen.tiny_random(rng, n_max=40, m_max=120, n_labels=int(rng.integers(1, 6)))
+        d = int(rng.integers(0, 3))
+        kw = dict(hash_mode=int(rng.integers(0, 2)), hub_threshold=int(rng.choice([0, 1, 2, 5])))
+        k = int(rng.integers(1, 7))
+        vl, el = bool(rng.integers(0, 2)), bool(rng.integers(0, 2))
+        for rekey in (False, True):
+            assert_same(ctx, g, d, vl, el, k, early_stop=bool(rng.integers(0, 2)), rekey_all=rekey, **kw)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_singletons_power_law(ctx, power_law, d):
+    # hubs and most vertices of a power-law graph are alone in their block
+    # after one or two rounds: the hub, medium and small paths all skip them
+    for rekey in (False, True):
+        assert_same(ctx, power_law, d, True, True, 6, early_stop=False, rekey_all=rekey)
+        assert_same(ctx, power_law, d, True, True, 5, hub_threshold=40, rekey_all=rekey)
+        assert_same(ctx, power_law, d, False, True, 5, hub_threshold=8, hash_mode=1, rekey_all=rekey)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_frozen_edgeless_blocks(ctx, d):
+    # two thirds of the vertices without out-edges, in a few label classes;
+    # edges concentrated on a small head so many vertices also lack in-edges
+    rng = np.random.Generator(np.random.PCG64(34 + d))
+    n = 30_000
+    src = rng.integers(0, n // 3, size=40_000)
+    dst = np.minimum(rng.zipf(1.6, size=40_000) - 1, n - 1)
+    g = graphgen.from_edges(n, src, dst, rng.integers(0, 3, size=src.shape[0]), rng.integers(0, 5, size=n))
+    for rekey in (False, True):
+        assert_same(ctx, g, d, True, True, 7, early_stop=False, rekey_all=rekey)
+        assert_same(ctx, g, d, False, True, 5, rekey_all=rekey)
+    L, C, _ = oracle.refine_graph(g, d, True, True, k=7, early_stop=False)
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    for j in (1, 2):
+        res = ctx.refine_from(dg, torch.from_numpy(L[j]).to("cuda:0"), j, 7, kb.Options(direction=d, early_stop=False))
+        assert np.array_equal(res.levels.cpu().numpy()[j:], L[j:])
+
+
+def test_singletons_from_start_partition(ctx, er_tiny):
+    dg = kb.DeviceGraph.from_numpy(er_tiny, "cuda:0")
+    n = er_tiny.n
+    # every vertex alone at the start: every later level is the identity
+    start = torch.arange(n, dtype=torch.int32, device="cuda:0")
+    res = ctx.refine_from(dg, start, 0, 4, kb.Options(early_stop=False))
+    assert np.array_equal(res.levels.cpu().numpy(), np.tile(np.arange(n, dtype=np.int32), (5, 1)))
+    assert list(res.counts) == [n] * 5
+    # half the vertices alone, the rest in three blocks
+    init = np.arange(n, dtype=np.int32)
+    init[n // 2:] = n + (np.arange(n - n // 2) % 3)
+    L, C, _ = oracle.refine_graph(er_tiny, 0, False, True, k=5, early_stop=False, initial=init)
+    for rekey in (False, True):
+        res = ctx.refine_from(dg, torch.from_numpy(init).to("cuda:0"), 0, 5,
+                              kb.Options(early_stop=False, rekey_all=rekey))
+        assert np.array_equal(res.levels.cpu().numpy(), L) and np.array_equal(res.counts, C)
+
+
 # ---------------------------------------------------------------- resume, initial partition, host buffers
 
 
