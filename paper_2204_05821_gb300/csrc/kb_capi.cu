@@ -400,6 +400,7 @@ struct Prepared {
     uint32_t* frozen = nullptr;
     uint32_t* frozen_min = nullptr;
     uint32_t* edgeless = nullptr;
+    bool compact = false;  // small-kernel windows skip frozen vertices (many frozen)
 };
 
 // Validate, plan, acquire the workspace, bind the round parameters, list the
@@ -564,11 +565,11 @@ kb_status launch_level0(kb_context* ctx, Prepared& R, const int32_t* key, int32_
     R.p.prev = key;
     R.p.frozen = nullptr;
     R.p.frozen_min = nullptr;
-    kb::launch_small_round(R.p, true, s);
+    kb::launch_small_round(R.p, true, false, s);
     kb::launch_renumber(R.p, R.prefix, R.scan_tmp, out, s);
     // a starting level may mix edgeless vertices with others in one block:
     // only its singletons are frozen in the first round
-    if (R.p.shared) kb::launch_freeze(R.p.n, R.p.bitmap, R.p.shared, nullptr, R.frozen, R.frozen_min, s);
+    if (R.p.shared) kb::launch_freeze(R.p.n, R.p.bitmap, R.p.shared, nullptr, R.frozen, R.frozen_min, ctx->d_ctr, s);
     KB_CUDA(ctx, cudaGetLastError());
     return KB_OK;
 }
@@ -585,7 +586,7 @@ kb_status launch_round_body(kb_context* ctx, Prepared& R, cudaStream_t s, Timer*
         KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, R.set_bytes, s));
     if (T) T->end();
     if (T) T->begin(KB_KERNEL_SMALL);
-    kb::launch_small_round(p, false, s);
+    kb::launch_small_round(p, false, R.compact, s);
     if (T) T->end();
     if (p.n_med) {
         if (T) T->begin(KB_KERNEL_MEDIUM);
@@ -668,6 +669,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         KB_TRY(read_counters(ctx));
         KB_TRY(device_error(ctx));
         prev_count = ctx->h_ctr->count;
+        R.compact = R.P.freeze && ctx->h_ctr->frozen * 4 > n;
     } else {
         kb::launch_fill_i32(row0, n, 0, s);
         if (p.perm) kb::launch_fill_i32(p.gat, n, 0, s);
@@ -690,12 +692,14 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
         // a block formed by this round that holds an edgeless vertex holds only
         // edgeless vertices with one previous block: frozen from now on
-        if (p.shared) kb::launch_freeze(n, p.bitmap, p.shared, R.edgeless, R.frozen, R.frozen_min, s);
+        if (p.shared) kb::launch_freeze(n, p.bitmap, p.shared, R.edgeless, R.frozen, R.frozen_min, ctx->d_ctr, s);
         T.end();
         // CSE levels need not refine each other: compare whole levels
         if (R.P.subject) kb::launch_levels_differ(out, p.prev, n, ctx->d_ctr, s);
         KB_CUDA(ctx, cudaGetLastError());
         KB_TRY(read_counters(ctx));
+        // compacted small-kernel windows pay once a quarter of the vertices are frozen
+        R.compact = R.P.freeze && ctx->h_ctr->frozen * 4 > n;
         ctx->round_ms.push_back(T.collect());
         KB_TRY(device_error(ctx));
         const int64_t c = ctx->h_ctr->count;

@@ -40,6 +40,7 @@ struct Counters {
     int32_t err;
     int32_t diff;   // set when two compared levels differ (launch_levels_differ)
     int64_t count;  // blocks at the level just assigned
+    int64_t frozen; // vertices frozen for the next round (launch_freeze)
 };
 
 // Everything one refinement round reads and writes.
@@ -193,12 +194,15 @@ void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream
 // After the renumbering: the frozen blocks of the next round.  single = block
 // minima no other vertex points to (bitmap & ~shared); frozen = single, plus
 // the edgeless vertices when edgeless != nullptr; frozen_min = single plus the
-// edgeless minima; shared is emptied for the next round.
+// edgeless minima; shared is emptied for the next round; ctr->frozen counts
+// the frozen vertices.
 void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless, uint32_t* frozen,
-                   uint32_t* frozen_min, cudaStream_t s);
+                   uint32_t* frozen_min, Counters* ctr, cudaStream_t s);
 // Bit v set iff v has no edges in the processed CSR.
 void launch_edgeless_bits(int64_t n, const int64_t* row, uint32_t* bits, cudaStream_t s);
-void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s);
+// compact: windows are packed from the vertices that refine (worth it when
+// many are frozen), else from consecutive vertices.
+void launch_small_round(const RoundParams& p, bool level0, bool compact, cudaStream_t s);
 void launch_medium_round(const RoundParams& p, cudaStream_t s);  // kb_medium.cu
 // Per-device kernel attributes (shared-memory carveouts); call once per device
 // before the first launch and outside any stream capture.

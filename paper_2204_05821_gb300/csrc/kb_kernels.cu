@@ -443,8 +443,9 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
 
 // the frozen blocks of the next round (see launch_freeze)
 __global__ void freeze_kernel(int64_t nw, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
-                              uint32_t* frozen, uint32_t* frozen_min) {
+                              uint32_t* frozen, uint32_t* frozen_min, Counters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long cnt = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
         const uint32_t b = bitmap[i];
         const uint32_t single = b & ~shared[i];
@@ -452,7 +453,11 @@ __global__ void freeze_kernel(int64_t nw, const uint32_t* bitmap, uint32_t* shar
         frozen[i] = single | e;
         frozen_min[i] = single | (b & e);
         shared[i] = 0u;
+        cnt += __popc(single | e);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->frozen), cnt);
 }
 
 __global__ void edgeless_bits_kernel(int64_t n, const int64_t* row, uint32_t* bits) {
@@ -603,9 +608,9 @@ void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream
 }
 
 void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless, uint32_t* frozen,
-                   uint32_t* frozen_min, cudaStream_t s) {
+                   uint32_t* frozen_min, Counters* ctr, cudaStream_t s) {
     const int64_t nw = (n >> 5) + 1;
-    if (n > 0) freeze_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, bitmap, shared, edgeless, frozen, frozen_min);
+    if (n > 0) freeze_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, bitmap, shared, edgeless, frozen, frozen_min, ctr);
 }
 
 void launch_edgeless_bits(int64_t n, const int64_t* row, uint32_t* bits, cudaStream_t s) {

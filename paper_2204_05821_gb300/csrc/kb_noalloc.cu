@@ -153,7 +153,7 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     if (host_cnts[1] > 0) return KB_ERR_INVALID_ARG;  // a vertex above the hub threshold
     p.n_med = host_cnts[0];
 
-    kb::launch_small_round(p, false, s);
+    kb::launch_small_round(p, false, false, s);
     kb::launch_medium_round(p, s);
     kb::launch_renumber(p, reinterpret_cast<uint32_t*>(base + kOffPrefix), reinterpret_cast<uint32_t*>(base + kOffScan),
                         out, s);

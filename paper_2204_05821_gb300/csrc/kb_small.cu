@@ -103,7 +103,7 @@ __device__ __forceinline__ void flush_join(const RoundParams& p, uint64_t key, u
     }
 }
 
-template <bool kLevel0>
+template <bool kLevel0, bool kCompact>
 __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_round_kernel(const RoundParams p) {
     __shared__ uint64_t s_pairs[kSmallThreads];
     __shared__ JoinMap M;
@@ -119,32 +119,71 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
     const int64_t vb = cta_base + (int64_t)(threadIdx.x >> 5) * p.warp_verts;
     const int64_t ve = min(p.n, vb + p.warp_verts);
 
-    // The next window's row offsets and own blocks are loaded while the
-    // current window works (its start is known once the current one is packed).
-    int64_t pf_a = 0, pf_b = 0;
-    int32_t pf_own = 0;
-    auto prefetch = [&](int64_t w0) {
-        const int64_t vv = w0 + lane;
-        if (vv < ve) {
-            pf_own = (!kLevel0 && p.own_key) ? p.own_key[vv] : (p.prev ? p.prev[vv] : 0);
+    // A window holds up to 32 vertices of the task, one per lane: consecutive
+    // ones, or (kCompact, when many vertices are frozen) the next ones that
+    // refine this round among the next kLook, so that frozen and inactive
+    // vertices take no lane.  The next window is picked, and its row offsets
+    // and own blocks loaded, while the current one works (its start is known
+    // once the current one is packed).
+    constexpr int kLook = kCompact ? 128 : 32;
+    const int span = (int)(ve - vb);  // task vertices (at most 65536)
+    // next window: this lane's vertex as an offset from vb (-1: none), and
+    // packed: vertices picked (bits 0..5), more than 32 candidates in the span
+    // (bit 6), offset of the first vertex after the span (bits 7..)
+    int pf_off = -1;
+    int pf_win = 0;
+    int64_t pf_a = 0;
+    int32_t pf_d = 0, pf_own = 0;
+    auto pick = [&](int c) {
+        if (!kCompact) {  // the next 32 vertices
+            pf_off = c + lane < span ? c + lane : -1;
+        } else {  // the next 32 that refine, among the next kLook
+            unsigned bk[kLook / 32];
+#pragma unroll
+            for (int k = 0; k < kLook / 32; ++k) {
+                const int u = c + 32 * k + lane;
+                bk[k] = __ballot_sync(kFull, u < span && vertex_active(p, vb + u) && !vertex_frozen(p, vb + u));
+            }
+            int rem = lane, total = 0;
+            pf_off = -1;
+#pragma unroll
+            for (int k = 0; k < kLook / 32; ++k) {
+                const int ck = __popc(bk[k]);
+                if (pf_off < 0 && rem < ck) pf_off = c + 32 * k + __fns(bk[k], 0, rem + 1);
+                if (pf_off < 0) rem -= ck;
+                total += ck;
+            }
+            pf_win = min(total, 32) | (total > 32 ? 64 : 0) | (min(span, c + kLook) << 7);
+        }
+        if (pf_off >= 0) {
+            const int64_t pv = vb + pf_off;
+            pf_own = (!kLevel0 && p.own_key) ? p.own_key[pv] : (p.prev ? p.prev[pv] : 0);
             if (!kLevel0) {
-                pf_a = p.row[vv];
-                pf_b = p.row[vv + 1];
+                pf_a = p.row[pv];
+                pf_d = (int32_t)min(p.row[pv + 1] - pf_a, (int64_t)0x7fffffff);
             }
         }
     };
-    prefetch(vb);
-    for (int64_t v0 = vb; v0 < ve;) {
-        const int nvw = (int)min((int64_t)32, ve - v0);
-        const int64_t v = v0 + lane;
+    pick(0);
+    for (int wc = 0; wc < span;) {
+        const int64_t v0 = vb + wc;  // first vertex of a window of consecutive vertices (not kCompact)
+        const int nvw = kCompact ? pf_win & 63 : min(span - wc, 32);
+        const int64_t v = kCompact ? vb + pf_off : v0 + lane;  // meaningful for lanes < nvw
+        if (kCompact && nvw == 0) {  // nothing to key in this span
+            wc = pf_win >> 7;
+            if (wc < span) pick(wc);
+            continue;
+        }
+        const bool more = (pf_win & 64) != 0;
+        const int span_end = pf_win >> 7;
         int cd = 0;
         bool small = false;
         int64_t a = 0;
         int32_t own = 0;
         bool l0 = kLevel0;
-        const int64_t cur_a = pf_a, cur_b = pf_b;
-        const int32_t cur_own = pf_own;
-        if (lane < nvw && vertex_active(p, v) && !vertex_frozen(p, v)) {
+        const int64_t cur_a = pf_a;
+        const int32_t cur_d = pf_d, cur_own = pf_own;
+        if (lane < nvw && (kCompact || (vertex_active(p, v) && !vertex_frozen(p, v)))) {
             if (!kLevel0 && vertex_level0(p, v)) {
                 l0 = true;
                 own = p.vlab ? p.vlab[v] : 0;
@@ -155,9 +194,8 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
             } else {
                 own = cur_own;
                 a = cur_a;
-                const int64_t d = cur_b - a;
-                small = d <= p.small_max;
-                cd = small ? (int)d : 0;
+                small = cur_d <= p.small_max;
+                cd = small ? cur_d : 0;
             }
         }
         // pack whole vertices while their edges fit in 32 lanes
@@ -171,7 +209,16 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
         const int nfit = __popc(fit);  // incl is non-decreasing, so the fitting lanes are 0..nfit-1
         const int E = __shfl_sync(kFull, incl, nfit - 1);
         const int start = incl - cd;
-        if (v0 + nfit < ve) prefetch(v0 + nfit);
+        // the next window starts at the first vertex that did not fit, else
+        // after the last one picked, else after the span
+        if (!kCompact) {
+            wc += nfit;
+        } else {
+            const int o_nf = __shfl_sync(kFull, pf_off, nfit < 32 ? nfit : 31);
+            const int o_last = __shfl_sync(kFull, pf_off, 31);
+            wc = nfit < nvw ? o_nf : (more ? o_last + 1 : span_end);
+        }
+        if (wc < span) pick(wc);
 
         uint64_t pr = 0;
         int j = 0;
@@ -303,19 +350,28 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
                 pos = (pos + 1) & p.mask;
             }
         }
-        // new-block owners of this window: one atomicXor per bitmap word
-        {
+        // new-block owners of this window: one atomicXor per bitmap word (the
+        // window's vertices lie in at most kLook / 32 + 1 words)
+        if (!kCompact) {
             const uint32_t sh = (uint32_t)(v0 & 31);
             const int64_t w0 = v0 >> 5;
-            const bool in0 = ((v0 + lane) >> 5) == w0;
+            const bool in0 = (v >> 5) == w0;
             const unsigned m0 = __ballot_sync(kFull, inserted && in0);
             const unsigned m1 = __ballot_sync(kFull, inserted && !in0);
             if (lane == 0) {
                 if (m0) atomicXor(&p.bitmap[w0], m0 << sh);
                 if (m1) atomicXor(&p.bitmap[w0 + 1], m1 >> (32 - sh));
             }
+        } else {
+            unsigned todo = __ballot_sync(kFull, inserted);
+            while (todo) {
+                const int64_t w = __shfl_sync(kFull, (long long)(v >> 5), __ffs(todo) - 1);
+                const bool mine = inserted && (v >> 5) == w;
+                const unsigned bits = __reduce_or_sync(kFull, mine ? 1u << (v & 31) : 0u);
+                if (lane == 0) atomicXor(&p.bitmap[w], bits);
+                todo &= ~__ballot_sync(kFull, mine);
+            }
         }
-        v0 += nfit;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kMapCap; i += kSmallThreads) {
@@ -326,7 +382,7 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
 
 }  // namespace
 
-void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s) {
+void launch_small_round(const RoundParams& p, bool level0, bool compact, cudaStream_t s) {
     if (p.n <= 0) return;
     const int64_t wv = p.warp_verts > 0 ? p.warp_verts : kDefaultWarpVerts;
     const int64_t per_cta = wv * kSmallWarps;
@@ -334,9 +390,11 @@ void launch_small_round(const RoundParams& p, bool level0, cudaStream_t s) {
     RoundParams q = p;
     q.warp_verts = (int32_t)wv;
     if (level0)
-        small_round_kernel<true><<<(unsigned)blocks, kSmallThreads, 0, s>>>(q);
+        small_round_kernel<true, false><<<(unsigned)blocks, kSmallThreads, 0, s>>>(q);
+    else if (compact)
+        small_round_kernel<false, true><<<(unsigned)blocks, kSmallThreads, 0, s>>>(q);
     else
-        small_round_kernel<false><<<(unsigned)blocks, kSmallThreads, 0, s>>>(q);
+        small_round_kernel<false, false><<<(unsigned)blocks, kSmallThreads, 0, s>>>(q);
 }
 
 }  // namespace kb
