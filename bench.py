@@ -48,9 +48,9 @@ METRIC = "k-bisim edges/s per round"
 # must match.
 KERNEL_HEADERS = ("paper_2204_05821_gb300/csrc/kb_device.cuh", "paper_2204_05821_gb300/csrc/kb_internal.cuh")
 TRAFFIC_PER_ALGO_BYTE = {
-    "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "7c3f7b30d24d929477083331f45f902631c6fa56", 3.779),
-    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "ade7cfcef83da31509b0108579db54db7d525bee", 4.709),
-    "medium": ("paper_2204_05821_gb300/csrc/kb_medium.cu", "1aa8fc4834dfb4acbf3f4128fa7f9b971b8535ee", 2.054),
+    "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "45283f75d524238d1ecc312aa7a09d2bc0d3f16c", 2.481),
+    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "4c39faee6108619951a26d9486dc1f3c088b4893", 6.909),
+    "medium": ("paper_2204_05821_gb300/csrc/kb_medium.cu", "b84b91b2680bc39015fe4214f4b73893a0d48428", 2.066),
 }
 
 
@@ -329,9 +329,10 @@ def run_ours(args, rank, world, local):
             units[name + "_edges"] += int(deg[sel].sum().item())
             units["n_" + ("hubs" if name == "hub" else name)] += int(sel.sum().item())
         del prev, active, sel
-    units = {key: val / lc for key, val in units.items()}
     del deg, cls_small, cls_hub, cls_med
-    algo_bytes = {
+    # per step, then per launch of each family (the medium and hub kernels are
+    # launched only in rounds where some of their vertices refine)
+    step_bytes = {
         # 12 B per edge (neighbour id 4, edge label 4, gathered block 4) and per
         # vertex 24 B (row offset 8, own block 4, slot write 4, table entry 8)
         "small": 12 * units["small_edges"] + 24 * units["n_small"],
@@ -339,9 +340,11 @@ def run_ours(args, rank, world, local):
         "hub_chunk": 12 * units["hub_edges"],
         "hub_final": 24 * units["n_hubs"],
         # per vertex: slot 4, table entry 8, level write 4; bitmap read twice
-        "renumber": 16 * n + n // 4,
-        "other": n // 8,
+        "renumber": lc * (16 * n + n // 4),
+        "other": lc * (n // 8),
     }
+    algo_bytes = {kname: step_bytes[kname] / max(1.0, fam_n.get(kname, 0) / args.steps) for kname in step_bytes}
+    units = {key: val / lc for key, val in units.items()}
     dom = max(fam_ms, key=lambda kname: fam_ms[kname])
     peak, peak_kind = peaks()
     per_launch_ms = fam_ms[dom] / max(1, fam_n[dom])
@@ -351,12 +354,14 @@ def run_ours(args, rank, world, local):
                 "algorithmic_bytes_per_launch": algo_bytes.get(dom, 0),
                 "kernel_share": {kname: fam_ms[kname] / sum(fam_ms.values()) for kname in fam_ms},
                 "per_launch_ms": {kname: fam_ms[kname] / max(1, fam_n[kname]) for kname in fam_ms}}
-    # our kernels per family event: renumbering is 4 kernels and the singleton
-    # pass, "other" the per-hub set clearing; per call add the setup kernels
-    # (validation, classification, hub search, chunk extents) and level 0
-    # (small kernel, renumbering, singleton pass)
-    per_event = {"small": 1, "medium": 1, "hub_chunk": 1, "hub_final": 1, "renumber": 5, "other": 1}
-    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 10 * args.steps
+    # our kernels per family event: the medium family is a warp kernel and a
+    # CTA kernel, the hub-chunk family clears the refining hubs' sets first,
+    # renumbering is 4 kernels plus the freeze and refining-count passes,
+    # "other" is memsets only; per call add the setup kernels (validation,
+    # classification, hub search, chunk extents, edgeless bits) and level 0
+    # (small kernel, renumbering, freeze, count)
+    per_event = {"small": 1, "medium": 2, "hub_chunk": 2, "hub_final": 1, "renumber": 6, "other": 0}
+    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 12 * args.steps
 
     # end to end through the host-buffer entry point, pinned host memory
     e2e = None

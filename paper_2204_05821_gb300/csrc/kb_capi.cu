@@ -401,6 +401,8 @@ struct Prepared {
     uint32_t* frozen_min = nullptr;
     uint32_t* edgeless = nullptr;
     bool compact = false;  // small-kernel windows skip frozen vertices (many frozen)
+    bool med_on = true;    // some medium vertex refines this round
+    bool hub_on = true;    // some hub refines this round
 };
 
 // Validate, plan, acquire the workspace, bind the round parameters, list the
@@ -569,7 +571,10 @@ kb_status launch_level0(kb_context* ctx, Prepared& R, const int32_t* key, int32_
     kb::launch_renumber(R.p, R.prefix, R.scan_tmp, out, s);
     // a starting level may mix edgeless vertices with others in one block:
     // only its singletons are frozen in the first round
-    if (R.p.shared) kb::launch_freeze(R.p.n, R.p.bitmap, R.p.shared, nullptr, R.frozen, R.frozen_min, ctx->d_ctr, s);
+    if (R.p.shared) {
+        kb::launch_freeze(R.p.n, R.p.bitmap, R.p.shared, nullptr, R.frozen, R.frozen_min, ctx->d_ctr, s);
+        kb::launch_count_refining(R.p, R.frozen, ctx->d_ctr, s);
+    }
     KB_CUDA(ctx, cudaGetLastError());
     return KB_OK;
 }
@@ -577,24 +582,27 @@ kb_status launch_level0(kb_context* ctx, Prepared& R, const int32_t* key, int32_
 // One refinement round up to (not including) the renumbering.
 kb_status launch_round_body(kb_context* ctx, Prepared& R, cudaStream_t s, Timer* T) {
     kb::RoundParams& p = R.p;
+    // with frozen blocks, the medium and hub kernels run only while some of
+    // their vertices refine (after the first rounds, hubs are mostly alone in
+    // their blocks)
+    const bool med = p.n_med && (!p.frozen || R.med_on);
+    const bool hub = p.n_hubs && (!p.frozen || R.hub_on);
     if (T) T->begin(KB_KERNEL_OTHER);
     KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
     kb::launch_clear_round(p, s);
-    if (p.frozen)
-        kb::launch_clear_hub_sets(p, (int64_t)(R.set_bytes / sizeof(uint64_t)), s);
-    else if (R.set_bytes)
-        KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, R.set_bytes, s));
+    if (hub && !p.frozen && R.set_bytes) KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, R.set_bytes, s));
     if (T) T->end();
     if (T) T->begin(KB_KERNEL_SMALL);
     kb::launch_small_round(p, false, R.compact, s);
     if (T) T->end();
-    if (p.n_med) {
+    if (med) {
         if (T) T->begin(KB_KERNEL_MEDIUM);
         kb::launch_medium_round(p, s);
         if (T) T->end();
     }
-    if (p.n_hubs) {
+    if (hub) {
         if (T) T->begin(KB_KERNEL_HUB_CHUNK);
+        if (p.frozen) kb::launch_clear_hub_sets(p, (int64_t)(R.set_bytes / sizeof(uint64_t)), s);
         kb::launch_hub_chunk(p, R.total_chunks, s);
         if (T) T->end();
         if (T) T->begin(KB_KERNEL_HUB_FINAL);
@@ -670,6 +678,8 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         KB_TRY(device_error(ctx));
         prev_count = ctx->h_ctr->count;
         R.compact = R.P.freeze && ctx->h_ctr->frozen * 4 > n;
+        R.med_on = ctx->h_ctr->med_on > 0;
+        R.hub_on = ctx->h_ctr->hub_on > 0;
     } else {
         kb::launch_fill_i32(row0, n, 0, s);
         if (p.perm) kb::launch_fill_i32(p.gat, n, 0, s);
@@ -692,7 +702,10 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
         // a block formed by this round that holds an edgeless vertex holds only
         // edgeless vertices with one previous block: frozen from now on
-        if (p.shared) kb::launch_freeze(n, p.bitmap, p.shared, R.edgeless, R.frozen, R.frozen_min, ctx->d_ctr, s);
+        if (p.shared) {
+            kb::launch_freeze(n, p.bitmap, p.shared, R.edgeless, R.frozen, R.frozen_min, ctx->d_ctr, s);
+            kb::launch_count_refining(p, R.frozen, ctx->d_ctr, s);
+        }
         T.end();
         // CSE levels need not refine each other: compare whole levels
         if (R.P.subject) kb::launch_levels_differ(out, p.prev, n, ctx->d_ctr, s);
@@ -700,6 +713,8 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         KB_TRY(read_counters(ctx));
         // compacted small-kernel windows pay once a quarter of the vertices are frozen
         R.compact = R.P.freeze && ctx->h_ctr->frozen * 4 > n;
+        R.med_on = ctx->h_ctr->med_on > 0;
+        R.hub_on = ctx->h_ctr->hub_on > 0;
         ctx->round_ms.push_back(T.collect());
         KB_TRY(device_error(ctx));
         const int64_t c = ctx->h_ctr->count;

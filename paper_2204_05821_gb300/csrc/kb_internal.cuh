@@ -41,6 +41,8 @@ struct Counters {
     int32_t diff;   // set when two compared levels differ (launch_levels_differ)
     int64_t count;  // blocks at the level just assigned
     int64_t frozen; // vertices frozen for the next round (launch_freeze)
+    int64_t med_on; // medium vertices that refine next round (launch_count_refining)
+    int64_t hub_on; // hubs that refine next round (launch_count_refining)
 };
 
 // Everything one refinement round reads and writes.
@@ -198,6 +200,9 @@ void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream
 // the frozen vertices.
 void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless, uint32_t* frozen,
                    uint32_t* frozen_min, Counters* ctr, cudaStream_t s);
+// After launch_freeze: the medium vertices and hubs that are not frozen, into
+// ctr->med_on and ctr->hub_on (their kernels are skipped when none refine).
+void launch_count_refining(const RoundParams& p, const uint32_t* frozen, Counters* ctr, cudaStream_t s);
 // Bit v set iff v has no edges in the processed CSR.
 void launch_edgeless_bits(int64_t n, const int64_t* row, uint32_t* bits, cudaStream_t s);
 // compact: windows are packed from the vertices that refine (worth it when

@@ -460,6 +460,26 @@ __global__ void freeze_kernel(int64_t nw, const uint32_t* bitmap, uint32_t* shar
     if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->frozen), cnt);
 }
 
+__global__ void count_refining_kernel(const int32_t* med_v, int64_t n_med, const int32_t* hub_v, int64_t n_hubs,
+                                      const uint32_t* frozen, Counters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long cm = 0, ch = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_med + n_hubs; i += stride) {
+        const int32_t v = i < n_med ? med_v[i] : hub_v[i - n_med];
+        const bool on = !((frozen[v >> 5] >> (v & 31)) & 1u);
+        if (i < n_med) cm += on; else ch += on;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cm += __shfl_xor_sync(kFull, cm, o);
+        ch += __shfl_xor_sync(kFull, ch, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cm) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->med_on), cm);
+        if (ch) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->hub_on), ch);
+    }
+}
+
 __global__ void edgeless_bits_kernel(int64_t n, const int64_t* row, uint32_t* bits) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -611,6 +631,12 @@ void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const ui
                    uint32_t* frozen_min, Counters* ctr, cudaStream_t s) {
     const int64_t nw = (n >> 5) + 1;
     if (n > 0) freeze_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, bitmap, shared, edgeless, frozen, frozen_min, ctr);
+}
+
+void launch_count_refining(const RoundParams& p, const uint32_t* frozen, Counters* ctr, cudaStream_t s) {
+    const int64_t items = p.n_med + p.n_hubs;
+    if (items > 0)
+        count_refining_kernel<<<grid_for(items, 256), 256, 0, s>>>(p.med_v, p.n_med, p.hub_v, p.n_hubs, frozen, ctr);
 }
 
 void launch_edgeless_bits(int64_t n, const int64_t* row, uint32_t* bits, cudaStream_t s) {
