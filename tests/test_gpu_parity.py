@@ -338,6 +338,15 @@ def test_frozen_edgeless_blocks(ctx, d):
         assert np.array_equal(res.levels.cpu().numpy()[j:], L[j:])
 
 
+@pytest.mark.parametrize("task", [32, 33, 100, 1000])
+def test_frozen_blocks_task_sizes(ctx, power_law, task):
+    # warp tasks that do not start on a bitmap word: windows of consecutive
+    # vertices (round 1) and of refining vertices only (later rounds)
+    for d in (0, 2):
+        assert_same(ctx, power_law, d, True, True, 6, early_stop=False, small_task_vertices=task)
+    assert_same(ctx, power_law, 1, True, True, 5, small_task_vertices=task, hash_mode=1, hub_threshold=40)
+
+
 def test_singletons_from_start_partition(ctx, er_tiny):
     dg = kb.DeviceGraph.from_numpy(er_tiny, "cuda:0")
     n = er_tiny.n
