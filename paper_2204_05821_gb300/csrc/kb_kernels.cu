@@ -12,6 +12,9 @@
 //   3. renumber: the block table keeps the smallest member of every block; a
 //      bitmap marks those minima, its prefix count gives every block its
 //      canonical id (rank of its smallest member).
+//   4. freeze (stratified single-graph rounds): blocks that cannot change in
+//      the next round -- one member, or formed by a round from edgeless
+//      vertices -- are skipped by steps 1-2 there and keep their minima.
 #include <cuda_runtime.h>
 
 #include "kb_device.cuh"
