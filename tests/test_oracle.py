@@ -229,6 +229,42 @@ def test_invariants_er(d):
             assert pairs.shape[0] == C[i]
 
 
+def _degree(g, d):
+    out = np.diff(g.row_offsets)
+    inn = np.bincount(g.col, minlength=g.n)
+    return {0: out, 1: inn, 2: out + inn}[d]
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_frozen_blocks_never_change(d):
+    # What the GPU rounds skip: with the own previous block in every key (Sec. 3:
+    # i-bisimilar requires (i-1)-bisimilar), a vertex alone in its block stays
+    # alone, and a block formed by a round (level >= 1) that holds a vertex
+    # without edges holds only such vertices and is kept whole at every later
+    # level.
+    rng = np.random.Generator(np.random.PCG64(70 + d))
+    graphs = [graphgen.make(graphgen.scaled(graphgen.CONFIG_RDF, 0.0005, seed=23))]
+    graphs += [graphgen.tiny_random(rng, n_max=60, m_max=90, n_labels=3) for _ in range(40)]
+    checked = 0
+    for g in graphs:
+        L, _, _ = oracle.refine_graph(g, d, True, True, k=6, early_stop=False)
+        edgeless = _degree(g, d) == 0
+        for i in range(1, 7):
+            prev, cur = L[i - 1], L[i]
+            alone = np.bincount(prev)[prev] == 1
+            assert np.all(np.bincount(cur)[cur][alone] == 1)
+            if i >= 2:
+                # blocks of level i-1 holding an edgeless vertex hold only edgeless ones
+                mixed = np.zeros(prev.max() + 1, dtype=bool)
+                mixed[prev[~edgeless]] = True
+                assert not np.any(mixed[prev[edgeless]])
+                # and are kept whole: same partition of the edgeless vertices
+                pairs = np.unique(np.stack([prev[edgeless], cur[edgeless]], 1), axis=0)
+                assert pairs.shape[0] == np.unique(prev[edgeless]).size == np.unique(cur[edgeless]).size
+                checked += int(edgeless.sum())
+    assert checked > 0
+
+
 def test_early_stop_matches_full_run():
     for d in (0, 1, 2):
         g = graphgen.erdos_renyi(300, 400, 2, 2, seed=d)
