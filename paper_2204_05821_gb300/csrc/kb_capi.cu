@@ -1254,8 +1254,6 @@ kb_status sfail(kb_server* sv, kb_status st, const char* fmt, ...) {
         }                                                                    \
     } while (0)
 
-int64_t processed_edges(const ServeRequest& r) { return r.opt.direction == KB_DIR_BOTH ? 2 * r.m : r.m; }
-
 // Copy request r's graph into the arena at the tail as slot `slot`.
 kb_status place_request(kb_server* sv, ServeRequest& r, int slot) {
     kb_context* ctx = sv->ctx;
