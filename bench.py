@@ -42,8 +42,7 @@ METRIC = "k-bisim edges/s per round"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per algorithmic
 # byte of a kernel, from one ncu capture of it on the large recipe at a tenth
-# of the size (profiles/*_large_tenth.md), where its traffic grows in
-# proportion to its units.  Valid only for the kernel source it was measured
+# of the size, where its traffic grows in proportion to its units.  Valid only for the kernel source it was measured
 # on: the SHA-1 of the kernel's file followed by the two shared device headers
 # must match.
 KERNEL_HEADERS = ("paper_2204_05821_gb300/csrc/kb_device.cuh", "paper_2204_05821_gb300/csrc/kb_internal.cuh")
@@ -196,7 +195,7 @@ def cpu_baseline(cfg, target_s=12.0, max_reps=40):
         oracle.refine_graph(g, 0, True, True, k=1, early_stop=False)
         total += time.perf_counter() - t0
         reps += 1
-    return {"value": g.m * reps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": g.m * reps / total, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": "oracle (single-threaded C++ map refinement) on the same recipe scaled to n=%d, m=%d: "
                       "%d call(s) of one round after level 0, %.1f s in all" % (g.n, g.m, reps, total)}
 
@@ -228,7 +227,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": describe(args.workload, cfg, args.k, "out"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -319,6 +319,7 @@ def run_ours(args, rank, world, local):
                       "hub_gt%d" % hub_thr: [int(cls_hub.sum().item()), int(deg[cls_hub].sum().item())]}
     lc = max(1, rounds // max(1, args.steps))
     units = {"small_edges": 0, "med_edges": 0, "hub_edges": 0, "n_small": 0, "n_med": 0, "n_hubs": 0}
+    keyed = []  # per round: [vertices, edges] re-keyed (the others sit in frozen blocks)
     for i in range(1, lc + 1):
         prev = levels[i - 1].long()
         active = torch.bincount(prev, minlength=n)[prev] > 1
@@ -328,6 +329,7 @@ def run_ours(args, rank, world, local):
             sel = active & cls
             units[name + "_edges"] += int(deg[sel].sum().item())
             units["n_" + ("hubs" if name == "hub" else name)] += int(sel.sum().item())
+        keyed.append([int(active.sum().item()), int(deg[active].sum().item())])
         del prev, active, sel
     del deg, cls_small, cls_hub, cls_med
     # per step, then per launch of each family (the medium and hub kernels are
@@ -362,6 +364,17 @@ def run_ours(args, rank, world, local):
     # (small kernel, renumbering, freeze, count)
     per_event = {"small": 1, "medium": 2, "hub_chunk": 2, "hub_final": 1, "renumber": 6, "other": 0}
     launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 12 * args.steps
+    # Round 1 is the one round that keys every vertex and every edge (nothing
+    # is frozen before it): the full-work figure, with the whole round's
+    # algorithmic bytes taken as 12 B per edge (neighbour id, edge label,
+    # gathered block) and 40 B per vertex (row offset 8, own block 4, hash 8,
+    # table probe and minimum 8, bitmap and scan 8, level write 4).
+    r1_ms = round_ms[0] if round_ms else float("nan")
+    round1 = {"ms": r1_ms, "edges_per_s": m / (r1_ms / 1000.0),
+              "algorithmic_bytes": 12 * m + 40 * n,
+              "achieved_gbs": (12 * m + 40 * n) / (r1_ms / 1000.0) / 1e9,
+              "frac": (12 * m + 40 * n) / (r1_ms / 1000.0) / 1e9 / peak,
+              "peak": peak, "peak_source": peak_kind}
 
     # end to end through the host-buffer entry point, pinned host memory
     e2e = None
@@ -463,7 +476,9 @@ def run_ours(args, rank, world, local):
                                l2="inputs larger than L2 (CSR %.1f GB); no flush" % ((8 * (n + 1) + 8 * m) / 1e9),
                                parallelism="replicas" if world > 1 else "single GPU",
                                rounds_per_step=rounds / args.steps,
+                               keyed_vertices_edges_per_round=keyed,
                                kernel_ms_per_round_last_step=[round(x, 2) for x in round_ms]),
+                "round1": round1, "round1_edges_per_s": round1["edges_per_s"], "round1_frac": round1["frac"],
                 "roofline": roofline, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
                 "batch": batch_info, "serve": serve_info, "next_rows": next_rows}
         if not args.no_cpu_baseline and world == 1:

@@ -96,19 +96,133 @@ def _rows_from_degrees(deg: np.ndarray) -> np.ndarray:
     return row
 
 
-def zipf_labels(rng: np.random.Generator, count: int, n_labels: int, s: float) -> np.ndarray:
-    """Labels 0..n_labels-1 with P(label = j) proportional to (j+1)^-s."""
-    if n_labels <= 1:
-        return np.zeros(count, dtype=np.int32)
-    p = np.arange(1, n_labels + 1, dtype=np.float64) ** (-s)
-    cdf = np.cumsum(p)
-    cdf /= cdf[-1]
-    out = np.empty(count, dtype=np.int32)
-    chunk = 1 << 24
-    for a in range(0, count, chunk):
-        b = min(count, a + chunk)
-        out[a:b] = np.minimum(np.searchsorted(cdf, rng.random(b - a), side="right"), n_labels - 1)
-    return out
+# --------------------------------------------------------------------------
+# Counter-based random numbers, identical in numpy and torch
+# --------------------------------------------------------------------------
+#
+# Draw i of stream s under seed S is fmix64(key(S, s) + (i + 1) * W) mod 2^64:
+# a Weyl sequence with increment W = floor(2^64 / golden ratio) passed through
+# the 64-bit finalizer of MurmurHash3 (Austin Appleby, public domain).  Only
+# wrapping 64-bit integer multiply, add, xor and shifts are involved, so numpy
+# (uint64) and torch (int64, logical shifts emulated) give the same bits on
+# any machine, and a graph drawn on the GPU equals the one drawn on the host.
+_W = 0x9E3779B97F4A7C15
+_F1 = 0xFF51AFD7ED558CCD
+_F2 = 0xC4CEB9FE1A85EC53
+_MASK64 = (1 << 64) - 1
+_CHUNK = 1 << 24
+
+# streams of the power-law recipe
+_S_OUT, _S_PERM_OUT, _S_PERM_IN, _S_IN, _S_ELABEL, _S_VLABEL = range(6)
+
+
+def _fmix64(x: int) -> int:
+    x &= _MASK64
+    x ^= x >> 33
+    x = (x * _F1) & _MASK64
+    x ^= x >> 33
+    x = (x * _F2) & _MASK64
+    x ^= x >> 33
+    return x
+
+
+def stream_key(seed: int, stream: int) -> int:
+    """64-bit key of random stream ``stream`` under ``seed``."""
+    return _fmix64(_fmix64(int(seed) * _W + 0x632BE59BD9B4E019) ^ (int(stream) * 0xD6E8FEB86659FD93))
+
+
+def ctr_bits(key: int, a: int, b: int) -> np.ndarray:
+    """Draws a..b-1 of the stream with this key, as uint64 (numpy)."""
+    i = np.arange(a + 1, b + 1, dtype=np.uint64)
+    x = i * np.uint64(_W) + np.uint64(key)
+    x ^= x >> np.uint64(33)
+    x *= np.uint64(_F1)
+    x ^= x >> np.uint64(33)
+    x *= np.uint64(_F2)
+    x ^= x >> np.uint64(33)
+    return x
+
+
+def ctr_uniform(key: int, a: int, b: int) -> np.ndarray:
+    """Draws a..b-1 as float64 in [0, 1): the top 53 bits times 2^-53 (exact)."""
+    return (ctr_bits(key, a, b) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def _i64(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def _srl(x, s: int):
+    """Logical right shift of an int64 torch tensor."""
+    return (x >> s) & ((1 << (64 - s)) - 1)
+
+
+def ctr_bits_torch(key: int, a: int, b: int, device):
+    """:func:`ctr_bits` with torch on ``device``, as int64 holding the same bits."""
+    import torch
+
+    x = torch.arange(a + 1, b + 1, dtype=torch.int64, device=device) * _i64(_W) + _i64(key)
+    x ^= _srl(x, 33)
+    x *= _i64(_F1)
+    x ^= _srl(x, 33)
+    x *= _i64(_F2)
+    x ^= _srl(x, 33)
+    return x
+
+
+def ctr_uniform_torch(key: int, a: int, b: int, device):
+    import torch
+
+    return _srl(ctr_bits_torch(key, a, b, device), 11).to(torch.float64) * (2.0 ** -53)
+
+
+# --------------------------------------------------------------------------
+# Platform-independent power-law weights
+# --------------------------------------------------------------------------
+#
+# A graph is drawn by inverting cumulative distributions, so a weight that
+# differs in its last bit between two machines moves draws from one vertex to
+# another.  libm's pow and numpy's SIMD pow are not bit-identical across
+# platforms, so the weights r^-a are computed here with correctly rounded basic
+# operations only (numpy never fuses them): ln r from frexp and the series
+# ln f = 2 atanh((f-1)/(f+1)), exp by reduction to exp(t) 2^k and Taylor's
+# series, and every sum is a sequential cumulative sum.
+_LN2 = 0.6931471805599453
+
+
+def _det_log(x: np.ndarray) -> np.ndarray:
+    f, e = np.frexp(x)
+    low = f < 0.7071067811865476
+    f = np.where(low, f * 2.0, f)
+    e = np.where(low, e - 1, e).astype(np.float64)
+    s = (f - 1.0) / (f + 1.0)  # |s| < 0.172
+    s2 = s * s
+    acc = np.full_like(s, 1.0 / 29.0)
+    for j in range(13, -1, -1):
+        acc = acc * s2 + 1.0 / (2 * j + 1)
+    return e * _LN2 + 2.0 * s * acc
+
+
+def _det_exp(y: np.ndarray) -> np.ndarray:
+    k = np.rint(y / _LN2)
+    t = y - k * _LN2  # |t| <= ~0.35
+    fact = [1.0]
+    for j in range(1, 19):
+        fact.append(fact[-1] * j)
+    acc = np.full_like(t, 1.0 / fact[18])
+    for j in range(17, -1, -1):
+        acc = acc * t + 1.0 / fact[j]
+    return np.ldexp(acc, k.astype(np.int64))
+
+
+def det_pow(x: np.ndarray, a: float) -> np.ndarray:
+    """x^a for positive float64 x, bit-identical on every platform (relative
+    error about 1e-15)."""
+    return _det_exp(a * _det_log(np.asarray(x, dtype=np.float64)))
+
+
+def _seqsum(x: np.ndarray) -> float:
+    return float(np.cumsum(x)[-1]) if x.shape[0] else 0.0
 
 
 def _capped_powerlaw_degrees(n: int, m: int, gamma: float, cap: float) -> np.ndarray:
@@ -116,25 +230,75 @@ def _capped_powerlaw_degrees(n: int, m: int, gamma: float, cap: float) -> np.nda
     scaled to sum m, with the largest clipped at ``cap`` and the remainder
     rescaled so the total stays m."""
     r = np.arange(1, n + 1, dtype=np.float64)
-    w = r ** (-1.0 / (gamma - 1.0))
-    d = w * (m / w.sum())
+    w = det_pow(r, -1.0 / (gamma - 1.0))
+    d = w * (m / _seqsum(w))
     for _ in range(50):
         over = d > cap
         if not over.any():
             break
         d[over] = cap
         free = ~over
-        rest = m - cap * over.sum()
-        d[free] *= rest / d[free].sum()
+        rest = m - cap * float(np.count_nonzero(over))
+        d[free] *= rest / _seqsum(d[free])
     return d
 
 
-def _sample_ranks(rng: np.random.Generator, cdf: np.ndarray, count: int) -> np.ndarray:
-    out = np.empty(count, dtype=np.int64)
-    chunk = 1 << 24
-    for a in range(0, count, chunk):
-        b = min(count, a + chunk)
-        out[a:b] = np.minimum(np.searchsorted(cdf, rng.random(b - a), side="right"), cdf.shape[0] - 1)
+def _cdf(weights: np.ndarray) -> np.ndarray:
+    c = np.cumsum(weights)
+    c /= c[-1]
+    return c
+
+
+def _zipf_cdf(n_labels: int, s: float) -> np.ndarray:
+    return _cdf(det_pow(np.arange(1, max(1, n_labels) + 1, dtype=np.float64), -s))
+
+
+def _pool_map(fn, spans):
+    """Run fn(a, b) over spans on host threads (numpy releases the GIL in the
+    loops used here); every span writes only its own slice."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    workers = max(1, min(len(spans), os.cpu_count() or 1))
+    if workers == 1:
+        for a, b in spans:
+            fn(a, b)
+        return
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(lambda ab: fn(*ab), spans))
+
+
+def _spans(count: int):
+    return [(a, min(count, a + _CHUNK)) for a in range(0, count, _CHUNK)]
+
+
+def _inverse_cdf(cdf: np.ndarray, key: int, count: int, out: np.ndarray) -> None:
+    """out[i] = the bin of draw i: the first j with cdf[j] > u_i (clipped)."""
+    last = cdf.shape[0] - 1
+
+    def work(a, b):
+        out[a:b] = np.minimum(np.searchsorted(cdf, ctr_uniform(key, a, b), side="right"), last)
+
+    _pool_map(work, _spans(count))
+
+
+def _random_permutation(key: int, n: int) -> np.ndarray:
+    """A uniformly random permutation of 0..n-1: the stable argsort of n
+    random 63-bit keys."""
+    keys = np.empty(n, dtype=np.int64)
+
+    def work(a, b):
+        keys[a:b] = (ctr_bits(key, a, b) >> np.uint64(1)).astype(np.int64)
+
+    _pool_map(work, _spans(n))
+    return np.argsort(keys, kind="stable")
+
+
+def zipf_labels(seed: int, stream: int, count: int, n_labels: int, s: float) -> np.ndarray:
+    """Labels 0..n_labels-1 with P(label = j) proportional to (j+1)^-s."""
+    out = np.zeros(count, dtype=np.int32)
+    if n_labels > 1:
+        _inverse_cdf(_zipf_cdf(n_labels, s), stream_key(seed, stream), count, out)
     return out
 
 
@@ -170,27 +334,40 @@ def chung_lu(
 ) -> Graph:
     """Power-law directed multigraph (static Chung-Lu model).
 
-    Out-degrees are one multinomial draw of m edges over the capped out-weights;
-    every edge's target is drawn independently from the capped in-weights
-    ("preferential by in-degree").  Out-rank and in-rank are mapped to vertex
-    ids by two independent random permutations, so hub ids carry no locality.
-    Vertices that draw no out-edges are the "literal" sinks of RDF data.
+    Out-degrees are one multinomial draw of m edges over the capped
+    out-weights (m independent draws of a source rank, counted); every edge's
+    target is drawn independently from the capped in-weights ("preferential by
+    in-degree").  Out-rank and in-rank are mapped to vertex ids by two
+    independent random permutations, so hub ids carry no locality.  Vertices
+    that draw no out-edges are the "literal" sinks of RDF data.  All draws come
+    from the counter-based streams above: :func:`chung_lu_torch` with the same
+    arguments returns the identical graph.
     """
-    rng = np.random.Generator(np.random.PCG64(seed))
-    d_out = _capped_powerlaw_degrees(n, m, gamma_out, max_out_deg)
-    deg_rank = rng.multinomial(m, d_out / d_out.sum()).astype(np.int64)
-    perm_out = rng.permutation(n)
+    cdf_out = _cdf(_capped_powerlaw_degrees(n, m, gamma_out, max_out_deg))
+    ranks = np.empty(m, dtype=np.int32)
+    _inverse_cdf(cdf_out, stream_key(seed, _S_OUT), m, ranks)
+    deg_rank = np.bincount(ranks, minlength=n).astype(np.int64)
+    del ranks, cdf_out
+    perm_out = _random_permutation(stream_key(seed, _S_PERM_OUT), n)
     deg = np.empty(n, dtype=np.int64)
     deg[perm_out] = deg_rank
+    del perm_out, deg_rank
     row = _rows_from_degrees(deg)
+    del deg
 
-    d_in = _capped_powerlaw_degrees(n, m, gamma_in, max_in_deg)
-    cdf_in = np.cumsum(d_in)
-    cdf_in /= cdf_in[-1]
-    perm_in = rng.permutation(n).astype(np.int32)
-    col = perm_in[_sample_ranks(rng, cdf_in, m)]
-    el = zipf_labels(rng, m, n_elabels, zipf_e)
-    vl = zipf_labels(rng, n, n_vlabels, zipf_v)
+    cdf_in = _cdf(_capped_powerlaw_degrees(n, m, gamma_in, max_in_deg))
+    perm_in = _random_permutation(stream_key(seed, _S_PERM_IN), n).astype(np.int32)
+    col = np.empty(m, dtype=np.int32)
+    _inverse_cdf(cdf_in, stream_key(seed, _S_IN), m, col)
+    del cdf_in
+
+    def remap(a, b):
+        col[a:b] = perm_in[col[a:b]]
+
+    _pool_map(remap, _spans(m))
+    del perm_in
+    el = zipf_labels(seed, _S_ELABEL, m, n_elabels, zipf_e)
+    vl = zipf_labels(seed, _S_VLABEL, n, n_vlabels, zipf_v)
     return Graph(n=n, m=m, row_offsets=row, col=col, elabel=el, vlabel=vl)
 
 
@@ -208,40 +385,37 @@ def chung_lu_torch(
     seed: int,
     device="cuda",
 ):
-    """The same recipe as :func:`chung_lu`, drawn with torch on ``device`` so
-    that billion-edge graphs are generated in seconds.  Returns a dict of torch
-    tensors (row_offsets int64, col int32, elabel int32, vlabel int32).  The
-    random stream differs from the numpy version; each is its own seeded
-    workload."""
+    """:func:`chung_lu` drawn with torch on ``device``, so that billion-edge
+    graphs are generated in seconds: the same counter-based streams, the same
+    host-computed cumulative distributions, the same inverse-CDF searches and
+    stable sorts, hence the identical graph.  Returns a dict of torch tensors
+    (row_offsets int64, col int32, elabel int32, vlabel int32)."""
     import torch
 
-    g = torch.Generator(device=device)
-    g.manual_seed(seed)
     chunk = 1 << 27
 
-    # Cumulative distributions are summed on the host: a floating-point scan on
-    # the device may combine partial sums in a different order from run to run,
-    # which would move a few draws across bin boundaries.
-    def capped_cdf(gamma, cap):
-        c = np.cumsum(_capped_powerlaw_degrees(n, m, gamma, cap))
-        c /= c[-1]
-        return torch.from_numpy(c).to(device)
-
-    def draw(cdf, count, out, transform):
+    def draw(cdf_np, key, count, put):
+        cdf = torch.from_numpy(cdf_np).to(device)
         for a in range(0, count, chunk):
             b = min(count, a + chunk)
-            u = torch.rand(b - a, generator=g, device=device, dtype=torch.float64)
-            idx = torch.searchsorted(cdf, u, right=True).clamp_(max=cdf.shape[0] - 1)
-            transform(a, b, idx)
+            u = ctr_uniform_torch(key, a, b, device)
+            put(a, b, torch.searchsorted(cdf, u, right=True).clamp_(max=cdf.shape[0] - 1))
+            del u
 
-    cdf_out = capped_cdf(gamma_out, max_out_deg)
+    def permutation(key):
+        keys = torch.empty(n, dtype=torch.int64, device=device)
+        for a in range(0, n, chunk):
+            b = min(n, a + chunk)
+            keys[a:b] = _srl(ctr_bits_torch(key, a, b, device), 1)
+        return torch.sort(keys, stable=True).indices
+
     deg_rank = torch.zeros(n, dtype=torch.int64, device=device)
 
     def acc_deg(a, b, idx):
         deg_rank.add_(torch.bincount(idx, minlength=n))
 
-    draw(cdf_out, m, None, acc_deg)
-    perm_out = torch.randperm(n, generator=g, device=device)
+    draw(_cdf(_capped_powerlaw_degrees(n, m, gamma_out, max_out_deg)), stream_key(seed, _S_OUT), m, acc_deg)
+    perm_out = permutation(stream_key(seed, _S_PERM_OUT))
     deg = torch.empty(n, dtype=torch.int64, device=device)
     deg[perm_out] = deg_rank
     del deg_rank, perm_out
@@ -249,32 +423,26 @@ def chung_lu_torch(
     torch.cumsum(deg, 0, out=row[1:])
     del deg
 
-    cdf_in = capped_cdf(gamma_in, max_in_deg)
-    perm_in = torch.randperm(n, generator=g, device=device).to(torch.int32)
+    perm_in = permutation(stream_key(seed, _S_PERM_IN)).to(torch.int32)
     col = torch.empty(m, dtype=torch.int32, device=device)
 
     def put_col(a, b, idx):
         col[a:b] = perm_in[idx]
 
-    draw(cdf_in, m, None, put_col)
+    draw(_cdf(_capped_powerlaw_degrees(n, m, gamma_in, max_in_deg)), stream_key(seed, _S_IN), m, put_col)
     del perm_in
 
-    def zipf_cdf(L, s):
-        c = np.cumsum(np.arange(1, L + 1, dtype=np.float64) ** (-s))
-        return torch.from_numpy(c / c[-1]).to(device)
+    def labels(count, n_labels, s, stream):
+        out = torch.zeros(count, dtype=torch.int32, device=device)
+        if n_labels > 1:
+            def put(a, b, idx):
+                out[a:b] = idx.to(torch.int32)
 
-    el = torch.empty(m, dtype=torch.int32, device=device)
+            draw(_zipf_cdf(n_labels, s), stream_key(seed, stream), count, put)
+        return out
 
-    def put_el(a, b, idx):
-        el[a:b] = idx.to(torch.int32)
-
-    draw(zipf_cdf(max(1, n_elabels), zipf_e), m, None, put_el)
-    vl = torch.empty(n, dtype=torch.int32, device=device)
-
-    def put_vl(a, b, idx):
-        vl[a:b] = idx.to(torch.int32)
-
-    draw(zipf_cdf(max(1, n_vlabels), zipf_v), n, None, put_vl)
+    el = labels(m, n_elabels, zipf_e, _S_ELABEL)
+    vl = labels(n, n_vlabels, zipf_v, _S_VLABEL)
     return {"n": n, "m": m, "row_offsets": row, "col": col, "elabel": el, "vlabel": vl}
 
 

@@ -43,7 +43,10 @@ typedef enum {
     KB_OK = 0,
     KB_ERR_INVALID_ARG = 1,   /* bad sizes, null pointers, non-monotone offsets, ids out of range */
     KB_ERR_OOM = 2,           /* device allocation failed or caller workspace too small */
-    KB_ERR_TABLE_FULL = 3,    /* block table probe limit hit (internal; retried with a larger table) */
+    KB_ERR_TABLE_FULL = 3,    /* a key needed more than 2^22 probes of the block table; nothing is
+                                 retried.  The table holds n / load_factor slots, so this needs a
+                                 clustered hash, e.g. hash_mode 1 on a previous block with millions
+                                 of distinct signatures */
     KB_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
     KB_ERR_CUDA = 5,          /* a CUDA runtime call failed */
     KB_ERR_DEVICE_CHECK = 6,  /* a device-side consistency check failed */
@@ -383,20 +386,23 @@ kb_status kb_server_get_stats(kb_server* server, kb_server_stats* stats);
  *   g        DEVICE CSR as for kb_refine, with n <= KB_NOALLOC_MAX_VERTICES and
  *            no vertex with more than hub_threshold (default 1024) edges
  *   opt      direction must be KB_DIR_OUT; use_edge_labels, hash_mode,
- *            hub_threshold and validate are honoured
+ *            hub_threshold, small_task_vertices (0 or 32..65536) and validate
+ *            are honoured
  *   prev     DEVICE int32[n], canonical ids of level i-1, each in [0, n)
  *   out      DEVICE int32[n], receives the canonical ids of level i
  *   count    HOST, receives the number of blocks of level i
  * Its scratch is one static device array of about 33 MB inside the library,
  * which every device that loads the library keeps until the process exits.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Every call shares the array, which
- * keeps the previous call's contents (each call resets what it uses), so calls
- * that overlap on the GPU -- from several streams or threads -- race; the
- * caller must serialise them.
+ * The first call on a device looks up the array's device address (and sets
+ * the round kernels' shared-memory attributes); make that first call before
+ * any stream capture.  Every call synchronises `stream` before returning.
+ * Every call shares the array, which keeps the previous call's contents
+ * (each call resets what it uses), so calls that overlap on the GPU -- from
+ * several streams or threads -- race; the caller must serialise them.
  * Errors: KB_ERR_INVALID_ARG for n above the limit, another direction, a
- * vertex above the hub threshold, an id of prev outside [0, n) or (with
- * validate) malformed CSR; KB_ERR_CUDA when a runtime call fails. */
+ * vertex whose degree lies outside [0, hub threshold], an id of prev outside
+ * [0, n), small_task_vertices out of range or (with validate) malformed CSR;
+ * `out` is then left untouched.  KB_ERR_CUDA when a runtime call fails. */
 #define KB_NOALLOC_MAX_VERTICES 1048576
 kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, const kb_options* opt,
                                   const int32_t* prev, int32_t* out, int64_t* count);

@@ -59,8 +59,6 @@ def _load():
             ]
             lib.oracle_summary.restype = ctypes.c_int64
             lib.oracle_summary.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
-            lib.oracle_count_distinct.restype = ctypes.c_int64
-            lib.oracle_count_distinct.argtypes = [ctypes.c_int64, P]
             _lib = lib
     return _lib
 
@@ -116,11 +114,6 @@ def summary(g, direction, use_edge_labels, src_level, dst_level):
     if cnt < 0:
         raise ValueError("oracle_summary takes direction out (0) or in (1)")
     return tuple(o[:cnt].copy() for o in out)
-
-
-def count_distinct(a) -> int:
-    a = np.ascontiguousarray(a, dtype=np.int32)
-    return int(_load().oracle_count_distinct(int(a.shape[0]), _ptr(a)))
 
 
 def signature(row_offsets, col, elabel, prev, v, direction=DIR_OUT, use_edge_labels=True, in_lists=None):

@@ -218,12 +218,4 @@ int64_t oracle_summary(int64_t n, const int64_t* row, const int32_t* col, const 
     return count;
 }
 
-// Number of distinct values of an int32 array (used to count the blocks of a
-// caller-supplied starting partition).
-int64_t oracle_count_distinct(int64_t n, const int32_t* a) {
-    std::map<int32_t, int> s;
-    for (int64_t v = 0; v < n; ++v) s[a[v]] = 1;
-    return (int64_t)s.size();
-}
-
 }  // extern "C"

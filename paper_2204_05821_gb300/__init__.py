@@ -461,19 +461,27 @@ def refine_round_noalloc(graph: DeviceGraph, prev, out, options: Options = None,
     """One refinement round (level i from level i-1, out-edges) through
     ``kb_refine_round_noalloc``: the library allocates no device memory for
     it, using a fixed static scratch array instead (n <= 2^20, no vertex above
-    the hub threshold).  ``prev`` and ``out`` are int32 CUDA tensors of length
-    n.  Returns the number of blocks of the new level."""
+    the hub threshold).  ``prev`` and ``out`` are contiguous int32 CUDA tensors
+    of length n on the graph's device.  Returns the number of blocks of the new
+    level."""
     import torch
 
     options = options or Options()
-    if stream is None:
-        stream = torch.cuda.current_stream(graph.device)
-    lib = _capi.load()
-    cnt = ctypes.c_int64(0)
-    g, o = graph.to_c(), options.to_c()
-    st = lib.kb_refine_round_noalloc(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(g), ctypes.byref(o),
-                                     ctypes.c_void_p(prev.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                     ctypes.byref(cnt))
+    for name, t in (("prev", prev), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("%s must be a torch tensor" % name)
+        if t.dtype != torch.int32 or not t.is_contiguous() or t.numel() != graph.n or t.device != graph.device:
+            raise ValueError("%s must be a contiguous int32 tensor of %d entries on %s (got %s, %d entries on %s)"
+                             % (name, graph.n, graph.device, t.dtype, t.numel(), t.device))
+    with torch.cuda.device(graph.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(graph.device)
+        lib = _capi.load()
+        cnt = ctypes.c_int64(0)
+        g, o = graph.to_c(), options.to_c()
+        st = lib.kb_refine_round_noalloc(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(g), ctypes.byref(o),
+                                         ctypes.c_void_p(prev.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.byref(cnt))
     if st != _capi.KB_OK:
         raise KbError(st, "kb_refine_round_noalloc")
     return int(cnt.value)

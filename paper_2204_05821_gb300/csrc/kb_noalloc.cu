@@ -66,6 +66,19 @@ __global__ void check_prev_kernel(int64_t n, const int32_t* prev, kb::Counters* 
     if (bad) atomicOr(&ctr->err, kb::kErrInvalid);
 }
 
+// Vertices this entry point cannot take: a degree above the hub threshold (no
+// hub path here) or a negative one (offsets not monotone, when validation is
+// off).  Counted into *bad.
+__global__ void check_degree_kernel(int64_t n, const int64_t* row, int32_t thr, unsigned long long* bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int64_t d = row[v + 1] - row[v];
+        if (d < 0 || d > thr) ++c;
+    }
+    if (c) atomicAdd(bad, c);
+}
+
 uint64_t next_pow2(uint64_t x) {
     uint64_t p = 1;
     while (p < x) p <<= 1;
@@ -90,6 +103,8 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     if (opt->subject != KB_SUBJECT_PREVIOUS) return KB_ERR_INVALID_ARG;
     if (opt->hash_mode < 0 || opt->hash_mode > 1) return KB_ERR_INVALID_ARG;
     if (opt->hub_threshold < 0 || opt->hub_threshold > kb::kMaxHubThreshold) return KB_ERR_INVALID_ARG;
+    if (opt->small_task_vertices != 0 && (opt->small_task_vertices < 32 || opt->small_task_vertices > 65536))
+        return KB_ERR_INVALID_ARG;
     if (g->n == 0) {
         *count = 0;
         return KB_OK;
@@ -136,13 +151,11 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     NA_CUDA(cudaMemsetAsync(p.emin, 0xff, sizeof(uint64_t) * (size_t)n, s));
     NA_CUDA(cudaMemsetAsync(p.bitmap, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
     if (opt->validate) kb::launch_validate(n, g->m, g->row_offsets, g->col_indices, ctr, s);
-    check_prev_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, prev, ctr);
-    if (g->m > 0) {
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+    check_prev_kernel<<<grid, 256, 0, s>>>(n, prev, ctr);
+    check_degree_kernel<<<grid, 256, 0, s>>>(n, p.row, thr, reinterpret_cast<unsigned long long*>(&cnts[1]));
+    if (g->m > 0)
         kb::launch_classify(n, p.row, p.small_max, thr, reinterpret_cast<int32_t*>(base + kOffMed), &cnts[0], s);
-        // vertices above the hub threshold are only counted (their ids land in
-        // the slot array, which the round overwrites)
-        kb::launch_classify(n, p.row, thr, 0x7fffffff, p.slot_of, &cnts[1], s);
-    }
     NA_CUDA(cudaGetLastError());
     int64_t host_cnts[2] = {0, 0};
     kb::Counters host_ctr{};
@@ -150,7 +163,7 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     NA_CUDA(cudaMemcpyAsync(&host_ctr, ctr, sizeof(host_ctr), cudaMemcpyDeviceToHost, s));
     NA_CUDA(cudaStreamSynchronize(s));
     if (host_ctr.err & kb::kErrInvalid) return KB_ERR_INVALID_ARG;
-    if (host_cnts[1] > 0) return KB_ERR_INVALID_ARG;  // a vertex above the hub threshold
+    if (host_cnts[1] > 0) return KB_ERR_INVALID_ARG;  // a degree outside [0, hub threshold]
     p.n_med = host_cnts[0];
 
     kb::launch_small_round(p, false, false, s);

@@ -100,3 +100,41 @@ def test_batch_rejects_cse_subjects(ctx):
     dg = kb.DeviceGraph.from_numpy(union, "cuda:0")
     with pytest.raises(kb.KbError):
         ctx.refine_batch(dg, voff, np.array([2, 2], dtype=np.int32), kb.Options(subject=kb.SUBJECT_ALL))
+
+
+def test_bench_batch_workload_subset_equals_oracle(ctx):
+    # The batching workload bench.py times (4,096 Erdos-Renyi graphs, edges
+    # lognormal in [1e3, 2e6], k uniform 1..10), refined in one kb_refine_batch
+    # call; a deterministic subset of its graphs -- the smallest, the largest,
+    # the ones with k = 1 and k = 10 at both ends of the size range, and random
+    # ones -- is compared with the oracle graph by graph, every level.
+    union, voff, ks = graphgen.batch_union_torch(device="cuda:0")
+    dg = kb.DeviceGraph(union["row_offsets"], union["col"], union["elabel"], union["vlabel"])
+    levels, counts, lc = ctx.refine_batch(dg, voff, ks, kb.Options())
+    torch.cuda.synchronize()
+    sizes = np.diff(voff)
+    order = np.argsort(sizes, kind="stable")
+    pick = {int(order[0]), int(order[1]), int(order[-1]), int(order[-2])}
+    for kk in (1, 10):
+        idx = np.nonzero(ks == kk)[0]
+        if idx.size:
+            pick |= {int(idx[np.argmin(sizes[idx])]), int(idx[np.argmax(sizes[idx])])}
+    rng = np.random.Generator(np.random.PCG64(77))
+    pick |= set(int(x) for x in rng.choice(len(ks), size=10, replace=False))
+    row = union["row_offsets"]
+    kmax = int(ks.max())
+    for j in sorted(pick):
+        a, b = int(voff[j]), int(voff[j + 1])
+        e0, e1 = int(row[a].item()), int(row[b].item())
+        g = graphgen.Graph(n=b - a, m=e1 - e0, row_offsets=(row[a:b + 1] - e0).cpu().numpy(),
+                           col=(union["col"][e0:e1] - a).cpu().numpy(), elabel=union["elabel"][e0:e1].cpu().numpy(),
+                           vlabel=union["vlabel"][a:b].cpu().numpy())
+        L, C, lcj = oracle.refine_graph(g, 0, True, True, k=int(ks[j]), early_stop=True)
+        got = levels[:, a:b].cpu().numpy()
+        for i in range(kmax + 1):
+            src = min(i, int(ks[j]))
+            assert np.array_equal(got[i], L[src]), (j, i, g.n, g.m)
+            assert counts[j, i] == C[src], (j, i)
+        assert lc[j] == lcj, (j, lc[j], lcj)
+    del levels, dg, union
+    torch.cuda.empty_cache()

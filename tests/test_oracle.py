@@ -316,6 +316,53 @@ def test_own_block_reading_is_harmless_without_labels():
         prev = cur
 
 
+def _in_lists(g):
+    src, dst, lab = g.edges()
+    lists = {}
+    for s, d, l in zip(src.tolist(), dst.tolist(), lab.tolist()):
+        lists.setdefault(d, []).append((s, l))
+    return lists
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_signature_keys_give_the_bruteforce_partition(d):
+    # oracle.signature (all three directions, the in-edge branch included):
+    # grouping vertices by (own block at level i-1, signature over level i-1)
+    # must give the brute-force relation R_i of the definitions.
+    rng = np.random.Generator(np.random.PCG64(31 + d))
+    for _ in range(60):
+        g = graphgen.tiny_random(rng)
+        el = bool(rng.integers(0, 2))
+        src, dst, lab = g.edges()
+        ids, _ = bruteforce.levels(g.n, src, dst, lab, g.vlabel, d, True, el, 4)
+        inl = _in_lists(g)
+        for i in range(1, 5):
+            prev = np.array(ids[i - 1])
+            keys = [(int(prev[v]), oracle.signature(g.row_offsets, g.col, g.elabel, prev, v, d, el, inl))
+                    for v in range(g.n)]
+            got = {}
+            assert [got.setdefault(key, len(got)) for key in keys] == ids[i], (d, el, i)
+
+
+def test_in_signature_is_the_reversed_out_signature():
+    # the in-direction signature of v in G is the out-direction signature of v
+    # in the reversed graph, with the direction bit set; BOTH is their union.
+    rng = np.random.Generator(np.random.PCG64(5))
+    for _ in range(40):
+        g = graphgen.tiny_random(rng, n_max=15, m_max=40)
+        src, dst, lab = g.edges()
+        r = graphgen.from_edges(g.n, dst, src, lab, g.vlabel)
+        prev = rng.integers(0, 3, size=g.n)
+        inl = _in_lists(g)
+        for v in range(g.n):
+            sin = oracle.signature(g.row_offsets, g.col, g.elabel, prev, v, oracle.DIR_IN, True, inl)
+            sout_r = oracle.signature(r.row_offsets, r.col, r.elabel, prev, v, oracle.DIR_OUT, True)
+            assert sin == tuple(sorted((1, l, b) for (_, l, b) in sout_r))
+            sout = oracle.signature(g.row_offsets, g.col, g.elabel, prev, v, oracle.DIR_OUT, True)
+            sboth = oracle.signature(g.row_offsets, g.col, g.elabel, prev, v, oracle.DIR_BOTH, True, inl)
+            assert sboth == tuple(sorted(set(sin) | set(sout)))
+
+
 # ---------------------------------------------------------------- the pins catch planted mistakes
 
 
