@@ -123,9 +123,13 @@ typedef struct {
  *   rekey_all          0 (default): single-graph stratified rounds (subject
  *                      KB_SUBJECT_PREVIOUS) skip the blocks that cannot change, since
  *                      keys hold the own previous block: a block of one vertex stays
- *                      one vertex, and a block formed by a round from vertices
- *                      without edges (keys (own block, empty set)) stays as it is;
- *                      such vertices keep their block without being re-keyed.
+ *                      one vertex; a block formed by a round from vertices without
+ *                      edges (keys (own block, empty set)) stays as it is; and a
+ *                      block none of whose members has an edge into a block of the
+ *                      previous level that the last round split keeps its members
+ *                      (their signatures are the previous ones with blocks renamed
+ *                      one to one); such vertices keep their block without being
+ *                      re-keyed.
  *                      1: re-key every vertex every round.  Results are identical
  *                      either way. */
 typedef struct {
@@ -276,7 +280,9 @@ kb_status kb_refine_host(kb_context* ctx, const kb_graph* g, const kb_options* o
 
 /* Per-round and per-kernel timing of the last refine call, in milliseconds,
  * measured with CUDA events on the context stream when enabled.
- *   kb_set_timing(ctx, 1) enables event recording (small overhead).
+ *   kb_set_timing(ctx, 1) enables event recording (small overhead); 2 also
+ *   records the work of every round (kb_get_round_work; one extra pass over
+ *   the row offsets per round); 0 disables both.
  *   round_ms[i] for i < n_rounds: device time of refinement round i+1.
  *   kernel_ms[j] / kernel_launches[j] for j < KB_KERNEL_COUNT: summed device time
  *   and launches of each kernel family inside the rounds. */
@@ -292,6 +298,24 @@ enum {
 kb_status kb_set_timing(kb_context* ctx, int enable);
 kb_status kb_get_timing(const kb_context* ctx, float* round_ms, int max_rounds, int* n_rounds,
                         float* kernel_ms, int64_t* kernel_launches);
+
+/* Work of the rounds of the last kb_refine / kb_refine_from / kb_refine_fixpoint
+ * call on this context made with kb_set_timing(ctx, 2): the vertices each
+ * round re-keyed and their edges in
+ * the processed direction, per kernel family (small: at most 32 edges, medium:
+ * up to hub_threshold, hub: more).  Single-graph stratified rounds (subject
+ * KB_SUBJECT_PREVIOUS, rekey_all 0) skip the blocks that cannot change: keys
+ * hold the own previous block (Sec. 3: i-bisimilar vertices are
+ * (i-1)-bisimilar), so a block of one vertex, a block of edgeless vertices
+ * formed by a round, and a block none of whose members has an edge to a
+ * vertex whose smallest block member the last round changed keep their
+ * members without being re-keyed.
+ *   vertices, edges  HOST int64[3 * max_rounds] or NULL; entry 3*i + f is round
+ *                    i+1 (the first signature round after the starting level),
+ *                    family f = 0 small, 1 medium, 2 hub
+ *   n_rounds         HOST: rounds recorded */
+kb_status kb_get_round_work(const kb_context* ctx, int64_t* vertices, int64_t* edges, int max_rounds,
+                            int* n_rounds);
 
 /* Batched refinement of G independent graphs given as one disjoint union.
  *   union_graph            DEVICE CSR over all vertices; edges never cross graphs

@@ -352,8 +352,21 @@ class Context:
         return float(lf.value), int(thr.value), float(ms.value)
 
     # -- timing
-    def set_timing(self, enable: bool = True):
-        self._check(self._lib.kb_set_timing(self._h, int(bool(enable))))
+    def set_timing(self, enable=True):
+        """0/False: off; 1/True: CUDA events per round and kernel family;
+        2: also the vertices and edges every round re-keys (round_work())."""
+        self._check(self._lib.kb_set_timing(self._h, int(enable)))
+
+    def round_work(self):
+        """Per round of the last refinement call (``kb_get_round_work``): a
+        dict of vertices and edges re-keyed by the small, medium and hub
+        kernels, e.g. {"small": (v, e), "medium": (v, e), "hub": (v, e)}."""
+        nr = ctypes.c_int(0)
+        v = np.zeros(3 * 4096, dtype=np.int64)
+        e = np.zeros(3 * 4096, dtype=np.int64)
+        self._check(self._lib.kb_get_round_work(self._h, _np_ptr(v), _np_ptr(e), 4096, ctypes.byref(nr)))
+        fam = ("small", "medium", "hub")
+        return [{fam[f]: (int(v[3 * i + f]), int(e[3 * i + f])) for f in range(3)} for i in range(nr.value)]
 
     def timing(self):
         """(round_ms list, {kernel family: (ms, launches)}) of the last call."""

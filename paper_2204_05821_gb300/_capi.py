@@ -109,6 +109,7 @@ SIGNATURES = [
                               _P, _P]),
     ("kb_set_timing", _I, [_P, _I]),
     ("kb_get_timing", _I, [_P, _P, _I, _P, _P, _P]),
+    ("kb_get_round_work", _I, [_P, _P, _P, _I, _P]),
     ("kb_refine_batch", _I, [_P, ctypes.POINTER(KbGraph), _P, _I64, _P, ctypes.POINTER(KbOptions), _P, _P, _P]),
     ("kb_autotune", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
     ("kb_server_config_default", KbServerConfig, []),

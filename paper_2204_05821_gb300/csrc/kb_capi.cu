@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -60,9 +61,15 @@ struct kb_context {
     size_t upd_buf_bytes = 0;
     unsigned long long* d_work = nullptr;  // |W| of the current round
     cudaStream_t cap_stream = nullptr;  // non-default stream used only to capture CUDA graphs
-    // timing
+    // timing: CUDA events per kernel family; with work, also the vertices and
+    // edges every round re-keys (one extra pass over the row offsets a round)
     bool timing = false;
+    bool work = false;
     std::vector<float> round_ms;
+    // per round of the last kb_refine / kb_refine_from / kb_refine_fixpoint
+    // call: vertices and processed edges re-keyed by the small, medium and hub
+    // kernels
+    std::vector<std::array<int64_t, 6>> round_keyed;
     float kernel_ms[KB_KERNEL_COUNT] = {};
     int64_t kernel_launches[KB_KERNEL_COUNT] = {};
     cudaEvent_t ev[2 * 10 + 2] = {};  // pairs for the round timer; the last two time whole calls
@@ -124,7 +131,7 @@ struct Plan {
     size_t csr_bytes = 0;
     size_t o_emin = 0, o_med = 0, o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
            o_chunkhub = 0, o_chunkext = 0, o_perm = 0, o_gat = 0, o_colr = 0, o_hist = 0, o_ownkey = 0, o_acc = 0, o_cnt = 0, o_sets = 0,
-           o_frozen = 0, o_fmin = 0, o_edgeless = 0, o_shared = 0;
+           o_frozen = 0, o_fmin = 0, o_edgeless = 0, o_shared = 0, o_minof = 0, o_bm2 = 0, o_moved = 0, o_mark = 0;
     size_t total = 0;
 };
 
@@ -175,6 +182,10 @@ void layout_round(Plan& P) {
     P.o_fmin = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_edgeless = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_shared = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_minof = take(P.freeze ? sizeof(uint32_t) * (size_t)P.n : 0);
+    P.o_bm2 = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_moved = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_mark = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.total = off;
 }
 
@@ -400,6 +411,13 @@ struct Prepared {
     uint32_t* frozen = nullptr;
     uint32_t* frozen_min = nullptr;
     uint32_t* edgeless = nullptr;
+    // clean blocks (frozen blocks on): the two bitmaps of block minima used in
+    // turn (this level's and the previous level's), moved vertices and marked
+    // (dirty) blocks; RoundParams::minof
+    uint32_t* bm[2] = {nullptr, nullptr};
+    int bm_cur = 0;
+    uint32_t* moved = nullptr;
+    uint32_t* mark = nullptr;
     bool compact = false;  // small-kernel windows skip frozen vertices (many frozen)
     bool med_on = true;    // some medium vertex refines this round
     bool hub_on = true;    // some hub refines this round
@@ -538,6 +556,12 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
         R.frozen_min = reinterpret_cast<uint32_t*>(ws + P.o_fmin);
         R.edgeless = reinterpret_cast<uint32_t*>(ws + P.o_edgeless);
         p.shared = reinterpret_cast<uint32_t*>(ws + P.o_shared);
+        p.minof = reinterpret_cast<uint32_t*>(ws + P.o_minof);
+        R.bm[0] = p.bitmap;
+        R.bm[1] = reinterpret_cast<uint32_t*>(ws + P.o_bm2);
+        R.bm_cur = 0;
+        R.moved = reinterpret_cast<uint32_t*>(ws + P.o_moved);
+        R.mark = reinterpret_cast<uint32_t*>(ws + P.o_mark);
         KB_CUDA(ctx, cudaMemsetAsync(R.frozen, 0, bw, s));
         KB_CUDA(ctx, cudaMemsetAsync(R.frozen_min, 0, bw, s));
         KB_CUDA(ctx, cudaMemsetAsync(p.shared, 0, bw, s));
@@ -572,7 +596,8 @@ kb_status launch_level0(kb_context* ctx, Prepared& R, const int32_t* key, int32_
     // a starting level may mix edgeless vertices with others in one block:
     // only its singletons are frozen in the first round
     if (R.p.shared) {
-        kb::launch_freeze(R.p.n, R.p.bitmap, R.p.shared, nullptr, R.frozen, R.frozen_min, ctx->d_ctr, s);
+        kb::launch_freeze_clean(R.p.n, R.p.bitmap, R.p.shared, nullptr, out, nullptr, R.frozen, R.frozen_min,
+                                ctx->d_ctr, s);
         kb::launch_count_refining(R.p, R.frozen, ctx->d_ctr, s);
     }
     KB_CUDA(ctx, cudaGetLastError());
@@ -648,6 +673,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         return KB_OK;
     }
     cudaStream_t s = ctx->stream;
+    ctx->round_keyed.clear();
     Prepared R;
     KB_TRY(prepare(ctx, g, opt, R, k - i_start));
     kb::RoundParams& p = R.p;
@@ -683,6 +709,12 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     } else {
         kb::launch_fill_i32(row0, n, 0, s);
         if (p.perm) kb::launch_fill_i32(p.gat, n, 0, s);
+        if (p.minof) {
+            // P_0 = {V}: one block, whose smallest member is vertex 0
+            kb::launch_fill_i32(reinterpret_cast<int32_t*>(p.minof), n, 0, s);
+            KB_CUDA(ctx, cudaMemsetAsync(p.bitmap, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
+            kb::launch_fill_i32(reinterpret_cast<int32_t*>(p.bitmap), 1, 1, s);
+        }
     }
     if (counts) counts[i_start] = prev_count;
     if (last_count) *last_count = prev_count;
@@ -696,14 +728,27 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         p.own_key = R.P.subject ? reinterpret_cast<const int32_t*>(R.ws + R.P.o_ownkey) : nullptr;
         p.frozen = R.frozen;
         p.frozen_min = R.frozen_min;
+        if (p.minof) {
+            // the minima of level i-1 stay readable while level i's are built
+            p.bitmap_prev = R.bm[R.bm_cur];
+            R.bm_cur ^= 1;
+            p.bitmap = R.bm[R.bm_cur];
+            p.moved = R.moved;
+        }
         int32_t* out = rows.row(i);
         KB_TRY(launch_round_body(ctx, R, s, &T));
+        if (ctx->work) kb::launch_round_work(p, s);
         T.begin(KB_KERNEL_RENUMBER);
         kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
-        // a block formed by this round that holds an edgeless vertex holds only
-        // edgeless vertices with one previous block: frozen from now on
+        // the next round's frozen blocks: singletons; a block formed by this
+        // round that holds an edgeless vertex holds only edgeless vertices with
+        // one previous block; and clean blocks, none of whose members has an
+        // edge to a vertex whose smallest block member this round changed
         if (p.shared) {
-            kb::launch_freeze(n, p.bitmap, p.shared, R.edgeless, R.frozen, R.frozen_min, ctx->d_ctr, s);
+            KB_CUDA(ctx, cudaMemsetAsync(R.mark, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
+            kb::launch_dirty_blocks(p, R.edgeless, R.moved, out, kb::kMaxHubThreshold, R.mark, s);
+            kb::launch_freeze_clean(n, p.bitmap, p.shared, R.edgeless, out, R.mark, R.frozen, R.frozen_min,
+                                    ctx->d_ctr, s);
             kb::launch_count_refining(p, R.frozen, ctx->d_ctr, s);
         }
         T.end();
@@ -711,6 +756,11 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         if (R.P.subject) kb::launch_levels_differ(out, p.prev, n, ctx->d_ctr, s);
         KB_CUDA(ctx, cudaGetLastError());
         KB_TRY(read_counters(ctx));
+        if (ctx->work) {
+            const Counters& hc = *ctx->h_ctr;
+            ctx->round_keyed.push_back(
+                {hc.keyed_v[0], hc.keyed_v[1], hc.keyed_v[2], hc.keyed_e[0], hc.keyed_e[1], hc.keyed_e[2]});
+        }
         // compacted small-kernel windows pay once a quarter of the vertices are frozen
         R.compact = R.P.freeze && ctx->h_ctr->frozen * 4 > n;
         R.med_on = ctx->h_ctr->med_on > 0;
@@ -1773,7 +1823,9 @@ kb_status kb_refine_host(kb_context* ctx, const kb_graph* g, const kb_options* o
 
 kb_status kb_set_timing(kb_context* ctx, int enable) {
     if (!ctx) return KB_ERR_INVALID_ARG;
+    if (enable < 0 || enable > 2) return fail(ctx, KB_ERR_INVALID_ARG, "timing mode must be 0, 1 or 2");
     ctx->timing = enable != 0;
+    ctx->work = enable == 2;
     return KB_OK;
 }
 
@@ -1788,6 +1840,19 @@ kb_status kb_get_timing(const kb_context* ctx, float* round_ms, int max_rounds, 
         if (kernel_ms) kernel_ms[f] = ctx->kernel_ms[f];
         if (kernel_launches) kernel_launches[f] = ctx->kernel_launches[f];
     }
+    return KB_OK;
+}
+
+kb_status kb_get_round_work(const kb_context* ctx, int64_t* vertices, int64_t* edges, int max_rounds,
+                            int* n_rounds) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    const int nr = (int)ctx->round_keyed.size();
+    if (n_rounds) *n_rounds = nr;
+    for (int i = 0; i < nr && i < max_rounds; ++i)
+        for (int f = 0; f < 3; ++f) {
+            if (vertices) vertices[3 * i + f] = ctx->round_keyed[(size_t)i][(size_t)f];
+            if (edges) edges[3 * i + f] = ctx->round_keyed[(size_t)i][(size_t)f + 3];
+        }
     return KB_OK;
 }
 

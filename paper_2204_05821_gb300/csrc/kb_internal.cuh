@@ -40,9 +40,14 @@ struct Counters {
     int32_t err;
     int32_t diff;   // set when two compared levels differ (launch_levels_differ)
     int64_t count;  // blocks at the level just assigned
-    int64_t frozen; // vertices frozen for the next round (launch_freeze)
+    int64_t frozen; // vertices frozen for the next round (launch_freeze_clean)
     int64_t med_on; // medium vertices that refine next round (launch_count_refining)
     int64_t hub_on; // hubs that refine next round (launch_count_refining)
+    int64_t moved;  // re-keyed vertices whose smallest block member changed (renumbering)
+    // vertices re-keyed this round and their edges in the processed
+    // direction, per kernel family: small, medium, hub
+    int64_t keyed_v[3];
+    int64_t keyed_e[3];
 };
 
 // Everything one refinement round reads and writes.
@@ -83,6 +88,15 @@ struct RoundParams {
     const uint32_t* frozen;
     const uint32_t* frozen_min;
     uint32_t* shared;
+    // Clean blocks (with frozen blocks).  minof[v] is the smallest member of
+    // v's block whenever v is not that member; the renumbering writes it for
+    // every re-keyed vertex, and a frozen vertex keeps it.  moved (when set)
+    // receives bit v for every re-keyed vertex whose smallest block member
+    // changed this round (read against bitmap_prev, the previous level's block
+    // minima, and minof), counted in ctr->moved; under the locality order the
+    // bit goes to v's position, which is what the neighbour ids hold.
+    uint32_t* minof;
+    uint32_t* moved;
     int32_t hub_threshold;
     int32_t small_max;    // min(kSmallDegree, hub_threshold)
     int32_t warp_verts;   // vertices per warp task of the small-vertex kernel
@@ -116,7 +130,7 @@ struct RoundParams {
     int32_t n_graphs;
     const uint8_t* gmode;      // [G] 1: the graph computes its level 0 this round (serving), or nullptr
     const int32_t* vlab;       // [n] vertex labels read by graphs in level-0 mode, or nullptr (all 0)
-    const uint32_t* bitmap_prev;  // block minima of the previous level (kept by inactive graphs)
+    const uint32_t* bitmap_prev;  // block minima of the previous level (batched: kept by inactive graphs)
     const uint32_t* gbase_prev;   // [G+1] rank of every graph's first vertex at the previous level
     uint32_t* gbase_cur;          // [G+1] the same at this level (written by the renumbering)
 };
@@ -193,14 +207,30 @@ __device__ __forceinline__ uint32_t table_hi(uint64_t h, uint32_t epoch) {
 void launch_clear_round(const RoundParams& p, cudaStream_t s);
 // Empty the hub sets of the hubs that refine this round.
 void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream_t s);
-// After the renumbering: the frozen blocks of the next round.  single = block
-// minima no other vertex points to (bitmap & ~shared); frozen = single, plus
-// the edgeless vertices when edgeless != nullptr; frozen_min = single plus the
-// edgeless minima; shared is emptied for the next round; ctr->frozen counts
-// the frozen vertices.
-void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless, uint32_t* frozen,
-                   uint32_t* frozen_min, Counters* ctr, cudaStream_t s);
-// After launch_freeze: the medium vertices and hubs that are not frozen, into
+// Clean blocks (RoundParams::minof).  After the renumbering of level i
+// (`level`, whose minima are in p.bitmap, moved vertices in `moved`): mark =
+// blocks of level i holding a vertex with an edge to a moved vertex (bit =
+// level-i id; a vertex above max_scan edges counts as such).  Only vertices
+// that are neither alone in their block (bitmap & ~shared) nor edgeless are
+// scanned, and nothing when more than an eighth of the vertices moved.
+void launch_dirty_blocks(const RoundParams& p, const uint32_t* edgeless, const uint32_t* moved, const int32_t* level,
+                         int32_t max_scan, uint32_t* mark, cudaStream_t s);
+// After the renumbering (single-graph stratified rounds): the frozen blocks
+// of the next round.  A vertex is frozen when it is alone in its block (a
+// minimum in bitmap that no other vertex marked in shared), edgeless
+// (edgeless != null: from the first signature round on, a block holding an
+// edgeless vertex holds only edgeless vertices with one previous block), or
+// in a level-i block without a mark bit (mark != null, unless more than an
+// eighth of the vertices moved).  frozen_min receives the minima of frozen
+// blocks; shared keeps exactly their marks; ctr->frozen counts the frozen
+// vertices.
+void launch_freeze_clean(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
+                         const int32_t* level, const uint32_t* mark, uint32_t* frozen, uint32_t* frozen_min,
+                         Counters* ctr, cudaStream_t s);
+// The vertices this round re-keys (not in p.frozen) and their edges, per
+// kernel family, into ctr->keyed_v / keyed_e (work accounting only).
+void launch_round_work(const RoundParams& p, cudaStream_t s);
+// After launch_freeze_clean: the medium vertices and hubs that are not frozen, into
 // ctr->med_on and ctr->hub_on (their kernels are skipped when none refine).
 void launch_count_refining(const RoundParams& p, const uint32_t* frozen, Counters* ctr, cudaStream_t s);
 // Bit v set iff v has no edges in the processed CSR.

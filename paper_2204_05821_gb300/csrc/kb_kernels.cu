@@ -444,23 +444,255 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
     }
 }
 
-// the frozen blocks of the next round (see launch_freeze)
-__global__ void freeze_kernel(int64_t nw, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
-                              uint32_t* frozen, uint32_t* frozen_min, Counters* ctr) {
+// Canonical ids of a single-graph stratified round with frozen blocks
+// (RoundParams::minof): assign_kernel's work with every lane of a warp on one
+// bitmap word (a warp-uniform loop), so that the moved vertices (re-keyed
+// vertices whose smallest block member changed: v itself or minof[v] at the
+// previous level, read before minof[v] is rewritten) leave as one word per
+// warp.  Frozen vertices keep minof, and their blocks keep their shared marks
+// (the freeze pass carries them over), so only re-keyed vertices mark.  moved
+// may be null (the starting level).
+__global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p, const uint32_t* prefix, int32_t* out,
+                                                             uint32_t* moved) {
+    __shared__ uint32_t s_mark[kMarkCache];
+    for (int i = threadIdx.x; i < kMarkCache; i += blockDim.x) s_mark[i] = kNoMark;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long cnt = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) {
-        const uint32_t b = bitmap[i];
-        const uint32_t single = b & ~shared[i];
-        const uint32_t e = edgeless ? edgeless[i] : 0u;
-        frozen[i] = single | e;
-        frozen_min[i] = single | (b & e);
-        shared[i] = 0u;
-        cnt += __popc(single | e);
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < p.n; base += stride) {
+        const int64_t v = base + lane;
+        bool mv = false;
+        uint32_t mark = kNoMark;
+        if (v < p.n) {
+            const bool fz = vertex_frozen(p, v);
+            uint32_t mn = (uint32_t)v;
+            if (!((p.bitmap[v >> 5] >> (v & 31)) & 1u)) {
+                if (fz) {
+                    mn = p.minof[v];  // a frozen block keeps its members and smallest member
+                } else {
+                    const uint32_t sl = (uint32_t)p.slot_of[v];
+                    if (sl & 0x80000000u)
+                        mn = (uint32_t)p.emin[(sl & 0x7fffffffu) % (uint32_t)p.n];
+                    else
+                        mn = (uint32_t)(p.table[(uint64_t)sl & p.mask] & 0xffffffffu);
+                    mark = mn;  // v is not the minimum: its block has another member
+                }
+                if ((int64_t)mn >= p.n) {  // only after a reported device error
+                    mn = (uint32_t)v;
+                    mark = kNoMark;
+                }
+            }
+            const uint32_t mw = p.bitmap[mn >> 5];
+            const int32_t b = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
+            out[v] = b;
+            if (p.perm) p.gat[p.perm[v]] = b;
+            if (!fz) {
+                if (moved) {
+                    const uint32_t pm = ((p.bitmap_prev[v >> 5] >> (v & 31)) & 1u) ? (uint32_t)v : p.minof[v];
+                    mv = pm != mn;
+                }
+                if (mn != (uint32_t)v) p.minof[v] = mn;
+            }
+        }
+        // one lane per distinct minimum in the warp, then the CTA's cache,
+        // then an L2 read: an atomic on a bit already set costs far more
+        // than the read
+        const unsigned grp = __match_any_sync(kFull, mark);
+        if (mark != kNoMark && lane == __ffs(grp) - 1) {
+            const uint32_t c = (mark * 2654435761u) >> 22;
+            if (s_mark[c] != mark) {
+                s_mark[c] = mark;
+                const uint32_t bit = 1u << (mark & 31);
+                if (!(__ldcg(p.shared + (mark >> 5)) & bit)) atomicOr(&p.shared[mark >> 5], bit);
+            }
+        }
+        if (moved) {
+            const unsigned w = __ballot_sync(kFull, mv);
+            if (p.perm) {
+                if (mv) atomicOr(&moved[p.perm[v] >> 5], 1u << (p.perm[v] & 31));
+            } else if (lane == 0) {
+                moved[base >> 5] = w;
+            }
+        }
+    }
+}
+
+// Vertices of bitmap word w that are neither alone in their block nor
+// edgeless (and exist).
+__device__ __forceinline__ uint32_t candidate_word(const uint32_t* bitmap, const uint32_t* shared,
+                                                   const uint32_t* edgeless, int64_t w, int64_t n) {
+    uint32_t c = ~(bitmap[w] & ~shared[w]);
+    if (edgeless) c &= ~edgeless[w];
+    const int64_t first = w * 32;
+    if (first + 32 > n) c &= n > first ? ((1u << (uint32_t)(n - first)) - 1u) : 0u;
+    return c;
+}
+
+// A warp takes 32 consecutive bitmap words (1024 vertices) and deals their
+// candidate vertices (candidate_word) to its lanes, 32 at a time: *v receives
+// the vertex of rank r among them, or -1.  excl / c are this lane's word's
+// exclusive candidate prefix and candidate bits.
+__device__ __forceinline__ int64_t dealt_vertex(int64_t w0, uint32_t excl, uint32_t c, int r, int total) {
+    int src = 0;
+#pragma unroll
+    for (int j = 1; j < 32; ++j)
+        if ((int)__shfl_sync(kFull, excl, j) <= r) src = j;
+    const uint32_t cs = __shfl_sync(kFull, c, src);
+    const uint32_t es = __shfl_sync(kFull, excl, src);
+    if (r >= total) return -1;
+    return (w0 + src) * 32 + (int64_t)__fns(cs, 0, r - (int)es + 1);
+}
+
+// A level-i block X can split in the next round only if one of its members
+// has an edge to a vertex whose smallest block member changed this round.
+// For X to split, two members u, v with equal signatures over level i-1 must
+// differ over level i: u has an edge (label l) into a level-i part C of some
+// level-(i-1) block B, and v has its label-l edges into B only outside C, in
+// another part C'.  So B split, and C or C' lacks B's smallest member: the
+// members of that part changed smallest member, and u or v has an edge to
+// one of them.  Mark (bit = level-i id) the blocks that hold such a member; a
+// vertex with more than max_scan edges marks its block unread.  When more
+// than an eighth of the vertices moved, nothing is scanned: the freeze pass
+// then takes every block as marked.
+__device__ __forceinline__ bool few_moved(const RoundParams& p) { return p.ctr->moved * 8 <= p.n; }
+
+__global__ void __launch_bounds__(256) dirty_blocks_kernel(const RoundParams p, const uint32_t* edgeless,
+                                                            const uint32_t* moved, const int32_t* level,
+                                                            int32_t max_scan, uint32_t* mark) {
+    if (!few_moved(p)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (p.n >> 5) + 1;
+    const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    if (w0 >= nw) return;  // uniform over the warp
+    const uint32_t c = w0 + lane < nw ? candidate_word(p.bitmap, p.shared, edgeless, w0 + lane, p.n) : 0u;
+    uint32_t incl = __popc(c);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = (int)__shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - __popc(c);
+    for (int t = 0; t < total; t += 32) {
+        const int64_t v = dealt_vertex(w0, excl, c, t + lane, total);
+        if (v < 0) continue;
+        const int64_t a = p.row[v], e_end = p.row[v + 1];
+        bool dirty = e_end - a > max_scan;
+        for (int64_t e0 = a; e0 < e_end && !dirty; e0 += 4) {
+            int32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = e0 + u < e_end ? (__ldg(p.col + e0 + u) & 0x7fffffff) : -1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (w[u] >= 0 && ((moved[w[u] >> 5] >> (w[u] & 31)) & 1u)) dirty = true;
+        }
+        if (dirty) {
+            const uint32_t b = (uint32_t)level[v];
+            const uint32_t mb = 1u << (b & 31);
+            if (!(__ldcg(mark + (b >> 5)) & mb)) atomicOr(&mark[b >> 5], mb);
+        }
+    }
+}
+
+// The frozen blocks of the next round: a vertex is frozen when it is alone in
+// its block (a minimum that no other vertex marked shared), edgeless
+// (edgeless != null), or in a level-i block without a mark bit (mark != null
+// and no more than an eighth of the vertices moved).  frozen_min holds the
+// minima of frozen blocks, and the shared marks of exactly those minima are
+// kept for the next round (their blocks keep their members; the others are
+// marked afresh).  A warp takes 32 bitmap words and deals the candidates
+// whose block it must look up to its lanes, as dirty_blocks_kernel does.
+__global__ void __launch_bounds__(256) freeze_clean_kernel(int64_t n, const uint32_t* bitmap, uint32_t* shared,
+                                                            const uint32_t* edgeless, const int32_t* level,
+                                                            const uint32_t* mark, uint32_t* frozen,
+                                                            uint32_t* frozen_min, Counters* ctr) {
+    __shared__ uint32_t s_clean[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nw = (n >> 5) + 1;
+    const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+    if (w0 >= nw) return;  // uniform over the warp
+    if (mark && ctr->moved * 8 > n) mark = nullptr;  // the dirty pass scanned nothing
+    const int64_t w = w0 + lane;
+    uint32_t b = 0, sh = 0, e = 0, c = 0;
+    if (w < nw) {
+        b = bitmap[w];
+        sh = shared[w];
+        e = edgeless ? edgeless[w] : 0u;
+        c = mark ? candidate_word(bitmap, shared, edgeless, w, n) : 0u;
+    }
+    s_clean[warp][lane] = 0u;
+    __syncwarp();
+    uint32_t incl = __popc(c);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = (int)__shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - __popc(c);
+    for (int t = 0; t < total; t += 32) {
+        const int64_t v = dealt_vertex(w0, excl, c, t + lane, total);
+        if (v < 0) continue;
+        const uint32_t l = (uint32_t)level[v];
+        if (!((mark[l >> 5] >> (l & 31)) & 1u)) atomicOr(&s_clean[warp][(v >> 5) - w0], 1u << (v & 31));
+    }
+    __syncwarp();
+    if (w < nw) {
+        const uint32_t single = b & ~sh;
+        const uint32_t cl = s_clean[warp][lane];
+        const uint32_t fz = single | e | cl;
+        const uint32_t fm = single | (b & (e | cl));
+        frozen[w] = fz;
+        frozen_min[w] = fm;
+        shared[w] = sh & fm;
+    }
+}
+
+// The vertices a round re-keys (those not in frozen; all when frozen is null)
+// and their processed edges, per kernel family: small (at most small_max
+// edges), medium, hub (more than thr edges).
+__global__ void __launch_bounds__(256) round_work_kernel(int64_t n, const int64_t* row, const uint32_t* frozen,
+                                                          int32_t small_max, int32_t thr, Counters* ctr) {
+    __shared__ unsigned long long s_sum[6][8];
+    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        if (frozen && ((frozen[v >> 5] >> (v & 31)) & 1u)) continue;
+        const int64_t d = row[v + 1] - row[v];
+        const int f = d <= small_max ? 0 : (d > thr ? 2 : 1);
+        c[f] += 1;
+        c[3 + f] += (unsigned long long)d;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->frozen), cnt);
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(kFull, c[k], o);
+        if ((threadIdx.x & 31) == 0) s_sum[k][threadIdx.x >> 5] = c[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 8; ++w) t += s_sum[threadIdx.x][w];
+        int64_t* dst = threadIdx.x < 3 ? &ctr->keyed_v[threadIdx.x] : &ctr->keyed_e[threadIdx.x - 3];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long*>(dst), t);
+    }
+}
+
+// *out += set bits of words[0..nw): a few hundred atomics in all
+__global__ void __launch_bounds__(256) count_bits_kernel(const uint32_t* words, int64_t nw, int64_t* out) {
+    __shared__ unsigned long long s_sum[8];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nw; i += stride) c += __popc(words[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 8; ++w) t += s_sum[w];
+        if (t) atomicAdd(reinterpret_cast<unsigned long long*>(out), t);
+    }
 }
 
 __global__ void count_refining_kernel(const int32_t* med_v, int64_t n_med, const int32_t* hub_v, int64_t n_hubs,
@@ -630,10 +862,28 @@ void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream
     clear_hub_sets_kernel<<<(unsigned)((total_slots + kClearTile - 1) / kClearTile), 256, 0, s>>>(p);
 }
 
-void launch_freeze(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless, uint32_t* frozen,
-                   uint32_t* frozen_min, Counters* ctr, cudaStream_t s) {
+void launch_dirty_blocks(const RoundParams& p, const uint32_t* edgeless, const uint32_t* moved, const int32_t* level,
+                         int32_t max_scan, uint32_t* mark, cudaStream_t s) {
+    if (p.n <= 0) return;
+    const int64_t warps = ((p.n >> 5) + 1 + 31) / 32;  // 32 bitmap words each
+    dirty_blocks_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(p, edgeless, moved, level, max_scan, mark);
+}
+
+void launch_freeze_clean(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
+                         const int32_t* level, const uint32_t* mark, uint32_t* frozen, uint32_t* frozen_min,
+                         Counters* ctr, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t warps = ((n >> 5) + 1 + 31) / 32;  // 32 bitmap words each
+    freeze_clean_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(n, bitmap, shared, edgeless, level, mark, frozen,
+                                                                     frozen_min, ctr);
     const int64_t nw = (n >> 5) + 1;
-    if (n > 0) freeze_kernel<<<grid_for(nw, 256), 256, 0, s>>>(nw, bitmap, shared, edgeless, frozen, frozen_min, ctr);
+    count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(frozen, nw, &ctr->frozen);
+}
+
+void launch_round_work(const RoundParams& p, cudaStream_t s) {
+    if (p.n <= 0) return;
+    const int g = grid_for(p.n, 256) < 1216 ? grid_for(p.n, 256) : 1216;
+    round_work_kernel<<<g, 256, 0, s>>>(p.n, p.row, p.frozen, p.small_max, p.hub_threshold, p.ctr);
 }
 
 void launch_count_refining(const RoundParams& p, const uint32_t* frozen, Counters* ctr, cudaStream_t s) {
@@ -669,6 +919,13 @@ void launch_bitmap_rank(const uint32_t* bitmap, int64_t nw, uint32_t* scan_tmp, 
 void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
     const int64_t nw = (p.n >> 5) + 1;
     launch_bitmap_rank(p.bitmap, nw, scan_tmp, prefix, p.ctr, s);
+    if (p.minof) {
+        if (p.moved && p.perm) cudaMemsetAsync(p.moved, 0, sizeof(uint32_t) * (size_t)nw, s);
+        if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out, p.moved);
+        if (p.moved) count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(
+            p.moved, nw, &p.ctr->moved);
+        return;
+    }
     if (batched(p)) {
         // prefix[nw] (one past the last word) is not written by the scan: the
         // total sits in the counters; graph_base_kernel reads prefix only for

@@ -423,3 +423,58 @@ def test_invalid_inputs_rejected(ctx):
         gpu_levels(ctx, g, 0, True, True, 3, reorder=3)
     # the context stays usable after errors
     assert_same(ctx, g, 0, True, True, 3)
+
+
+def _late_split_graphs():
+    # graphs whose blocks keep splitting for many rounds while others stay put
+    n = 500
+    spine = np.arange(n - 1)
+    leaves = np.arange(n, 3 * n)
+    comb = graphgen.from_edges(3 * n, np.concatenate([spine, (leaves - n) // 2]),
+                               np.concatenate([spine + 1, leaves]), None, None)
+    paths, _ = graphgen.disjoint_union([graphgen.path_graph(L) for L in range(1, 80)])
+    return [graphgen.path_graph(2000), graphgen.binary_tree(11), comb, paths, _path_and_cycles()]
+
+
+def _path_and_cycles():
+    # a labelled path next to 300 directed 10-cycles of another label: the
+    # path's block splits every round, the cycles' blocks never do
+    parts = [graphgen.path_graph(500)] + [graphgen.cycle_graph(10) for _ in range(300)]
+    g, off = graphgen.disjoint_union(parts)
+    g.vlabel = np.ones(g.n, dtype=np.int32)
+    g.vlabel[:500] = 0
+    return g
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_clean_blocks(ctx, power_law, d):
+    # rounds skip the blocks none of whose members has an edge into a block
+    # that the last round split; skipping and re-keying everything give the
+    # same levels, and both equal the oracle (locality order on and off,
+    # resumed runs included)
+    for g in _late_split_graphs() + [power_law]:
+        for rekey in (False, True):
+            assert_same(ctx, g, d, True, True, 12, early_stop=False, rekey_all=rekey)
+        assert_same(ctx, g, d, False, True, 9, reorder=2)
+    g = _path_and_cycles()
+    L, C, _ = oracle.refine_graph(g, d, True, True, k=12, early_stop=False)
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    res = ctx.refine_from(dg, torch.from_numpy(L[3]).to("cuda:0"), 3, 12, kb.Options(direction=d, early_stop=False))
+    assert np.array_equal(res.levels.cpu().numpy()[3:], L[3:])
+
+
+def test_clean_blocks_are_skipped(ctx):
+    # the cycles' blocks are clean from the second round on: only the path's
+    # vertices (and its edges) are re-keyed after that
+    g = _path_and_cycles()
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    ctx.set_timing(2)
+    res = ctx.refine(dg, 12, kb.Options(direction=kb.DIR_OUT, early_stop=False))
+    ctx.set_timing(0)
+    L, _, _ = oracle.refine_graph(g, 0, True, True, k=12, early_stop=False)
+    assert np.array_equal(res.levels.cpu().numpy(), L)
+    work = ctx.round_work()
+    assert len(work) == 12
+    keyed = [sum(v for v, _ in w.values()) for w in work]
+    assert keyed[0] == g.n
+    assert all(v <= 500 for v in keyed[2:]), keyed

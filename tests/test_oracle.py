@@ -265,6 +265,66 @@ def test_frozen_blocks_never_change(d):
     assert checked > 0
 
 
+def _smallest_member(level):
+    first = np.full(level.max() + 1, level.shape[0], dtype=np.int64)
+    np.minimum.at(first, level, np.arange(level.shape[0]))
+    return first[level]
+
+
+def _clean_blocks_keep_members(g, d, L, k):
+    """For levels i = 1..k-1: a level-i block none of whose members has an edge
+    (in direction d) to a vertex whose smallest block member changed between
+    levels i-1 and i must be one block of level i+1.  Returns how many such
+    blocks were checked."""
+    src, dst, _ = g.edges()
+    pairs = []
+    if d in (0, 2):
+        pairs.append((src, dst))
+    if d in (1, 2):
+        pairs.append((dst, src))
+    checked = 0
+    for i in range(1, k):
+        prev, cur, nxt = L[i - 1], L[i], L[i + 1]
+        moved = _smallest_member(cur) != _smallest_member(prev)
+        dirty = np.zeros(g.n, dtype=bool)
+        for a, b in pairs:
+            dirty[a[moved[b]]] = True
+        dirty_block = np.zeros(cur.max() + 1, dtype=bool)
+        dirty_block[cur[dirty]] = True
+        for blk in np.unique(cur[~dirty_block[cur]]):
+            members = np.nonzero(cur == blk)[0]
+            assert np.unique(nxt[members]).size == 1, (d, i, blk)
+            checked += members.size > 1
+    return checked
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_clean_blocks_never_split(d):
+    # What the GPU rounds also skip.  For a level-i block to split at level
+    # i+1, two members with equal signatures over level i-1 must differ over
+    # level i, which takes a level-(i-1) block B split into parts C, C' with
+    # one member's edge into C and the other's into C' only; one of the parts
+    # lacks B's smallest member, so its vertices changed smallest member.
+    # Hence a block none of whose members has an edge to such a vertex stays
+    # whole.  Checked on the oracle's levels of paths, trees, combs, power-law
+    # and random graphs.
+    rng = np.random.Generator(np.random.PCG64(90 + d))
+    graphs = [graphgen.path_graph(40), graphgen.binary_tree(6),
+              graphgen.make(graphgen.scaled(graphgen.CONFIG_RDF, 0.0005, seed=29))]
+    n = 60
+    spine = np.arange(n - 1)
+    leaves = np.arange(n, 3 * n)
+    graphs.append(graphgen.from_edges(3 * n, np.concatenate([spine, (leaves - n) // 2]),
+                                      np.concatenate([spine + 1, leaves]), None, None))
+    graphs += [graphgen.tiny_random(rng, n_max=50, m_max=70, n_labels=2) for _ in range(40)]
+    checked = 0
+    for g in graphs:
+        for vl in (True, False):
+            L, _, _ = oracle.refine_graph(g, d, vl, True, k=8, early_stop=False)
+            checked += _clean_blocks_keep_members(g, d, L, 8)
+    assert checked > 100
+
+
 def test_early_stop_matches_full_run():
     for d in (0, 1, 2):
         g = graphgen.erdos_renyi(300, 400, 2, 2, seed=d)
