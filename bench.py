@@ -305,10 +305,13 @@ def run_ours(args, rank, world, local):
     del r
 
     # roofline of the dominant kernel family (algorithmic bytes per launch).
-    # A round skips the blocks that cannot change (a vertex alone in its
-    # previous block; from the second round on, the edgeless vertices, whose
-    # blocks were formed by a round), so a launch's units are the edges and
-    # vertices of the others: averaged over the rounds of the last step.
+    # A round skips the blocks that cannot change (frozen blocks), so a
+    # launch's units are the vertices and edges the round re-keyed, which the
+    # library counts when asked to (one more call, outside the timed region).
+    ctx.set_timing(2)
+    ctx.refine(dg, k, opts, out=levels)
+    work = ctx.round_work()
+    ctx.set_timing(0)
     hub_thr, small_max = (args.hub_threshold or 1024), 32
     deg = (wl["row_offsets"][1:] - wl["row_offsets"][:-1])
     cls_small = deg <= small_max
@@ -317,21 +320,12 @@ def run_ours(args, rank, world, local):
     vertex_classes = {"small_le32": [int(cls_small.sum().item()), int(deg[cls_small].sum().item())],
                       "medium": [int(cls_med.sum().item()), int(deg[cls_med].sum().item())],
                       "hub_gt%d" % hub_thr: [int(cls_hub.sum().item()), int(deg[cls_hub].sum().item())]}
-    lc = max(1, rounds // max(1, args.steps))
-    units = {"small_edges": 0, "med_edges": 0, "hub_edges": 0, "n_small": 0, "n_med": 0, "n_hubs": 0}
-    keyed = []  # per round: [vertices, edges] re-keyed (the others sit in frozen blocks)
-    for i in range(1, lc + 1):
-        prev = levels[i - 1].long()
-        active = torch.bincount(prev, minlength=n)[prev] > 1
-        if i >= 2:
-            active &= deg > 0
-        for name, cls in (("small", cls_small), ("med", cls_med), ("hub", cls_hub)):
-            sel = active & cls
-            units[name + "_edges"] += int(deg[sel].sum().item())
-            units["n_" + ("hubs" if name == "hub" else name)] += int(sel.sum().item())
-        keyed.append([int(active.sum().item()), int(deg[active].sum().item())])
-        del prev, active, sel
     del deg, cls_small, cls_hub, cls_med
+    lc = max(1, len(work))
+    units = {"small_edges": sum(w["small"][1] for w in work), "med_edges": sum(w["medium"][1] for w in work),
+             "hub_edges": sum(w["hub"][1] for w in work), "n_small": sum(w["small"][0] for w in work),
+             "n_med": sum(w["medium"][0] for w in work), "n_hubs": sum(w["hub"][0] for w in work)}
+    keyed = [[sum(f[0] for f in w.values()), sum(f[1] for f in w.values())] for w in work]
     # per step, then per launch of each family (the medium and hub kernels are
     # launched only in rounds where some of their vertices refine)
     step_bytes = {
@@ -358,12 +352,13 @@ def run_ours(args, rank, world, local):
                 "per_launch_ms": {kname: fam_ms[kname] / max(1, fam_n[kname]) for kname in fam_ms}}
     # our kernels per family event: the medium family is a warp kernel and a
     # CTA kernel, the hub-chunk family clears the refining hubs' sets first,
-    # renumbering is 4 kernels plus the freeze and refining-count passes,
+    # renumbering is the 3-kernel rank scan, the assignment, the moved count,
+    # the dirty, freeze and frozen-count passes and the refining count;
     # "other" is memsets only; per call add the setup kernels (validation,
-    # classification, hub search, chunk extents, edgeless bits) and level 0
-    # (small kernel, renumbering, freeze, count)
-    per_event = {"small": 1, "medium": 2, "hub_chunk": 2, "hub_final": 1, "renumber": 6, "other": 0}
-    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 12 * args.steps
+    # hub search, chunk extents, classification, edgeless bits) and level 0
+    # (small kernel, rank scan, assignment, freeze, frozen count, refining count)
+    per_event = {"small": 1, "medium": 2, "hub_chunk": 2, "hub_final": 1, "renumber": 9, "other": 0}
+    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 13 * args.steps
     # Round 1 is the one round that keys every vertex and every edge (nothing
     # is frozen before it): the full-work figure, with the whole round's
     # algorithmic bytes taken as 12 B per edge (neighbour id, edge label,
@@ -536,11 +531,22 @@ def bench_batch(ctx, device, steps=3):
             "plain_graphs_per_s": G / tp, "plain_ms": 1000 * tp, "speedup_vs_plain": tp / tb}
 
 
-def bench_serve(device, duration_s=8.0, rate=200.0, seed=4, plain_requests=120):
-    """A Poisson stream of summarisation requests through kb_server_*.
-    Graphs come from a pre-drawn pool spanning the size distribution (each
-    request takes the pool graph closest to its drawn size), since drawing
-    hundreds of million-edge graphs per second on the host is not possible."""
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(np.ceil(q * len(xs))) - 1))] if xs else None
+
+
+def bench_serve(device, duration_s=8.0, rate=200.0, seed=4, sat_requests=600):
+    """A Poisson stream of summarisation requests through kb_server_*, and the
+    same requests through the plain path (one kb_refine_host per request, in
+    arrival order): at the nominal rate (p50 / p99 latency from arrival to
+    completion, both arms) and at saturation (every request queued at once:
+    requests per second, both arms).  Graphs come from a pre-drawn pool
+    spanning the size distribution (each request takes the pool graph closest
+    to its drawn size), since drawing hundreds of million-edge graphs per
+    second on the host is not possible."""
+    import threading as th
+
     import torch
 
     import paper_2204_05821_gb300 as kb
@@ -557,64 +563,102 @@ def bench_serve(device, duration_s=8.0, rate=200.0, seed=4, plain_requests=120):
         pool.append(tuple(d[kx].cpu().numpy() for kx in ("row_offsets", "col", "elabel", "vlabel")))
         del d
     torch.cuda.synchronize()
-    pick = [int(np.argmin(np.abs(qs - mm))) for mm in sizes]
+    reqs = [(ta, pool[int(np.argmin(np.abs(qs - mm)))], k) for (ta, mm, k, _) in stream]
     opts = kb.Options()
-    import threading as th
+    # Every request gets its own output array, allocated and touched before
+    # any timing, for both arms: the measurement is of the refinement and the
+    # copies, not of the host allocator faulting in fresh pages.
+    outs = [np.zeros((k + 1, g[0].shape[0] - 1), dtype=np.int32) for _, g, k in reqs]
+    for o in outs:
+        o.fill(0)
+    dev = int(str(device).split(":")[-1]) if ":" in str(device) else 0
 
-    done = {}
-    with kb.Server(int(str(device).split(":")[-1]) if ":" in str(device) else 0, max_vertices=1 << 26,
-                   max_edges=1 << 28, max_requests=256) as sv:
-        lock = th.Lock()
-        tickets = []
+    def serve(batch, arrivals):
+        """Run requests through a server; arrivals: submit at their times
+        (else all at once).  Returns (seconds, stats, latencies_ms)."""
+        with kb.Server(dev, max_vertices=1 << 26, max_edges=1 << 28, max_requests=256) as sv:
+            for _, (r, c, e, v), k in batch[:4]:  # warm
+                sv.submit(r, c, e, v, k, opts)
+            while sv.step() != (0, 0):
+                pass
+            for t in list(sv._meta):
+                sv.fetch(t)
+            lock = th.Lock()
+            tickets, done_at, sub_at = [], {}, {}
+            t_start = time.perf_counter()
+
+            def producer():
+                for i, (ta, (r, c, e, v), k) in enumerate(batch):
+                    if arrivals:
+                        dt = t_start + ta - time.perf_counter()
+                        if dt > 0:
+                            time.sleep(dt)
+                    t = sv.submit(r, c, e, v, k, opts, out=outs[i])
+                    with lock:
+                        tickets.append(t)
+                        sub_at[t] = (t_start + ta) if arrivals else t_start
+
+            prod = th.Thread(target=producer)
+            prod.start()
+            while True:
+                running, waiting = sv.step()
+                now = time.perf_counter()
+                with lock:
+                    pending = list(tickets)
+                for t in pending:
+                    if sv.poll(t) == kb.Server.DONE:
+                        sv.fetch(t)
+                        done_at[t] = now
+                        with lock:
+                            tickets.remove(t)
+                if not prod.is_alive() and running == 0 and waiting == 0:
+                    with lock:
+                        if not tickets:
+                            break
+                if running == 0 and waiting == 0:
+                    time.sleep(0.0002)
+            prod.join()
+            elapsed = time.perf_counter() - t_start
+            st = sv.stats()
+        lat = [1000 * (done_at[t] - sub_at[t]) for t in done_at]
+        return elapsed, st, lat
+
+    def plain(batch, arrivals):
+        """One kb_refine_host per request, in arrival order (a FIFO queue)."""
+        ctx = kb.Context(dev)
+        for _, (r, c, e, v), k in batch[:4]:
+            ctx.refine_host(r, c, e, v, k, opts)
+        lat = []
         t_start = time.perf_counter()
-
-        def producer():
-            for (ta, mm, k, _), pi in zip(stream, pick):
+        for i, (ta, (r, c, e, v), k) in enumerate(batch):
+            if arrivals:
                 dt = t_start + ta - time.perf_counter()
                 if dt > 0:
                     time.sleep(dt)
-                r, c, e, v = pool[pi]
-                t = sv.submit(r, c, e, v, k, opts)
-                with lock:
-                    tickets.append(t)
+            ctx.refine_host(r, c, e, v, k, opts, out=outs[i])
+            lat.append(1000 * (time.perf_counter() - (t_start + (ta if arrivals else 0.0))))
+        elapsed = time.perf_counter() - t_start
+        ctx.close()
+        return elapsed, lat
 
-        prod = th.Thread(target=producer)
-        prod.start()
-        while True:
-            running, waiting = sv.step()
-            with lock:
-                pending = list(tickets)
-            for t in pending:
-                if sv.poll(t) == kb.Server.DONE:
-                    sv.fetch(t)
-                    with lock:
-                        tickets.remove(t)
-                    done[t] = 1
-            if not prod.is_alive() and running == 0 and waiting == 0:
-                with lock:
-                    if not tickets:
-                        break
-            if running == 0 and waiting == 0:
-                time.sleep(0.0005)
-        prod.join()
-        st = sv.stats()
-    # plain path: the same requests one after another through kb_refine_host
-    ctx = kb.Context(int(str(device).split(":")[-1]) if ":" in str(device) else 0)
-    t0 = time.perf_counter()
-    for (ta, mm, k, _), pi in list(zip(stream, pick))[:plain_requests]:
-        r, c, e, v = pool[pi]
-        ctx.refine_host(r, c, e, v, k, opts)
-    tp = time.perf_counter() - t0
-    ctx.close()
+    sv_t, sv_st, sv_lat = serve(reqs, True)
+    pl_t, pl_lat = plain(reqs, True)
+    sat = reqs[:sat_requests]
+    sat_sv_t, _, _ = serve(sat, False)
+    sat_pl_t, _ = plain(sat, False)
     return {"workload": "Poisson arrivals %.0f/s for %.0f s; edges lognormal(median 7e5, sigma 1.4) in [1e4, 5e7], "
                         "Chung-Lu exponent 2.1, 64 vertex / 32 edge labels Zipf, k uniform 1..10, seed %d; graphs "
                         "from a pool of %d pre-drawn graphs at the size quantiles" % (rate, duration_s, seed, len(qs)),
-            "requests": len(stream), "completed": int(st["completed"]), "p50_ms": st["p50_ms"],
-            "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "requests_per_s": st["requests_per_s"],
-            "edge_rounds_per_s": st["edge_rounds_per_s"], "steps": int(st["steps"]),
-            "compactions": int(st["compactions"]), "plain_requests_per_s": min(plain_requests, len(stream)) / tp,
-            "plain_sample": "first %d requests, one kb_refine_host each, back to back" % min(plain_requests,
-                                                                                         len(stream))}
+            "requests": len(reqs), "completed": int(sv_st["completed"]),
+            "nominal_rate": {"server_p50_ms": _pct(sv_lat, 0.5), "server_p99_ms": _pct(sv_lat, 0.99),
+                             "plain_p50_ms": _pct(pl_lat, 0.5), "plain_p99_ms": _pct(pl_lat, 0.99),
+                             "server_requests_per_s": len(reqs) / sv_t, "plain_requests_per_s": len(reqs) / pl_t,
+                             "server_steps": int(sv_st["steps"]), "server_compactions": int(sv_st["compactions"]),
+                             "plain": "one kb_refine_host per request, FIFO in arrival order"},
+            "saturation": {"requests": len(sat), "server_requests_per_s": len(sat) / sat_sv_t,
+                           "plain_requests_per_s": len(sat) / sat_pl_t,
+                           "server_vs_plain": sat_pl_t / sat_sv_t,
+                           "how": "every request queued at once; plain: back to back"}}
 
 
 def main():

@@ -374,6 +374,7 @@ typedef struct {
     double p50_ms, p99_ms, mean_ms;   /* submit-to-completion latency of completed requests */
     double requests_per_s;            /* completed requests / time since the first submit */
     double edge_rounds_per_s;         /* processed edges x rounds of completed requests / same time */
+    int64_t failed;                   /* requests rejected at admission (malformed CSR) */
 } kb_server_stats;
 
 typedef struct kb_server kb_server;
@@ -382,17 +383,29 @@ kb_server_config kb_server_config_default(void);
 kb_status kb_server_create(kb_server** server, int device, void* stream, const kb_server_config* cfg);
 kb_status kb_server_destroy(kb_server* server);
 const char* kb_server_last_error(const kb_server* server);
-/* Queue a request.  g holds HOST arrays, copied before the call returns;
- * ticket receives its id.  Thread-safe with respect to kb_server_step. */
-kb_status kb_server_submit(kb_server* server, const kb_graph* g, const kb_options* opt, int k, int64_t* ticket);
+/* Queue a request.  g holds HOST arrays that the caller keeps alive and
+ * unchanged until the request has been admitted (kb_server_poll reports 1, 2
+ * or 3): they are copied to the device at admission, not at submission.
+ * levels_out is HOST int32[(k+1)*n] or NULL: when given, the levels are
+ * written there when the request finishes (no host copy inside the library;
+ * keep it alive until kb_server_fetch).  Checked here: sizes, the ends of
+ * row_offsets and the arena's capacity; every offset and neighbour id is
+ * checked on the device at admission, where a malformed graph fails alone
+ * (state 3) without reaching the shared arena.  ticket receives the request's
+ * id.  Thread-safe with respect to kb_server_step. */
+kb_status kb_server_submit(kb_server* server, const kb_graph* g, const kb_options* opt, int k, int32_t* levels_out,
+                           int64_t* ticket);
 /* Admit what fits, then run one round for every in-flight request and retire
  * finished ones (their levels are copied to host memory).  running / waiting
  * (may be NULL) receive the request counts after the step. */
 kb_status kb_server_step(kb_server* server, int32_t* running, int32_t* waiting);
-/* state: 0 waiting, 1 running, 2 done (fetchable); KB_ERR_NOT_FOUND if unknown. */
+/* state: 0 waiting, 1 running, 2 done (fetchable), 3 rejected at admission
+ * (kb_server_fetch returns KB_ERR_INVALID_ARG and forgets it); KB_ERR_NOT_FOUND
+ * if unknown. */
 kb_status kb_server_poll(kb_server* server, int64_t ticket, int32_t* state);
 /* Copy a finished request's results to HOST buffers (levels int32[(k+1)*n],
- * counts int64[k+1]) and forget it. */
+ * may be NULL or the levels_out given at submission; counts int64[k+1]) and
+ * forget it. */
 kb_status kb_server_fetch(kb_server* server, int64_t ticket, int32_t* levels, int64_t* counts,
                           int32_t* levels_computed);
 kb_status kb_server_get_stats(kb_server* server, kb_server_stats* stats);

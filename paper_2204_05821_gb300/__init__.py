@@ -382,12 +382,15 @@ class Context:
 class Server:
     """Continuous-batching summarisation server (``kb_server_*`` in the C ABI).
 
-    ``submit`` copies a host graph (numpy CSR) and queues it; every ``step``
-    admits what fits (arena space, request slots, device memory), runs one
-    refinement round for all in-flight requests at once and retires finished
-    ones.  ``fetch`` returns (levels [k+1, n], counts, levels_computed)."""
+    ``submit`` queues a host graph (numpy CSR; the arrays are kept referenced
+    until the request is fetched, since the library reads them at admission)
+    with a host array for its levels; every ``step`` admits what fits (arena
+    space, request slots, device memory), runs one refinement round for all
+    in-flight requests at once and retires finished ones.  ``fetch`` returns
+    (levels [k+1, n], counts, levels_computed), or raises KbError for a
+    request rejected at admission (state FAILED)."""
 
-    WAITING, RUNNING, DONE = 0, 1, 2
+    WAITING, RUNNING, DONE, FAILED = 0, 1, 2, 3
 
     def __init__(self, device: int = 0, stream=None, max_vertices: int = 1 << 26, max_edges: int = 1 << 28,
                  max_requests: int = 256, memory_budget: int = 0, load_factor: float = 0.0,
@@ -429,17 +432,24 @@ class Server:
     def __exit__(self, *a):
         self.close()
 
-    def submit(self, row_offsets, col, elabel, vlabel, k: int, options: Options = None) -> int:
+    def submit(self, row_offsets, col, elabel, vlabel, k: int, options: Options = None, out=None) -> int:
+        """Queue a request; ``out`` (int32 [k+1, n], C-contiguous) receives
+        its levels when it finishes (a new array when None)."""
         options = options or Options()
         row = np.ascontiguousarray(row_offsets, dtype=np.int64)
         col = np.ascontiguousarray(col, dtype=np.int32)
         el = None if elabel is None else np.ascontiguousarray(elabel, dtype=np.int32)
         vl = None if vlabel is None else np.ascontiguousarray(vlabel, dtype=np.int32)
-        g = _capi.KbGraph(row.shape[0] - 1, col.shape[0], _np_ptr(row), _np_ptr(col), _np_ptr(el), _np_ptr(vl))
+        n = row.shape[0] - 1
+        g = _capi.KbGraph(n, col.shape[0], _np_ptr(row), _np_ptr(col), _np_ptr(el), _np_ptr(vl))
         o = options.to_c()
         t = ctypes.c_int64(0)
-        self._check(self._lib.kb_server_submit(self._h, ctypes.byref(g), ctypes.byref(o), int(k), ctypes.byref(t)))
-        self._meta[t.value] = (row.shape[0] - 1, int(k))
+        levels = out if out is not None else np.empty((int(k) + 1, n), dtype=np.int32)
+        if levels.dtype != np.int32 or levels.shape != (int(k) + 1, n) or not levels.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous int32 array of shape (k+1, n)")
+        self._check(self._lib.kb_server_submit(self._h, ctypes.byref(g), ctypes.byref(o), int(k), _np_ptr(levels),
+                                               ctypes.byref(t)))
+        self._meta[t.value] = (levels, (row, col, el, vl))
         return int(t.value)
 
     def submit_graph(self, g, k: int, options: Options = None) -> int:
@@ -457,9 +467,8 @@ class Server:
         return int(st.value)
 
     def fetch(self, ticket: int):
-        n, k = self._meta.pop(ticket)
-        levels = np.empty((k + 1, n), dtype=np.int32)
-        counts = np.zeros(k + 1, dtype=np.int64)
+        levels, _graph = self._meta.pop(ticket)
+        counts = np.zeros(levels.shape[0], dtype=np.int64)
         lc = ctypes.c_int32(0)
         self._check(self._lib.kb_server_fetch(self._h, int(ticket), _np_ptr(levels), _np_ptr(counts), ctypes.byref(lc)))
         return levels, counts, int(lc.value)

@@ -81,6 +81,7 @@ class KbServerStats(ctypes.Structure):
         ("mean_ms", ctypes.c_double),
         ("requests_per_s", ctypes.c_double),
         ("edge_rounds_per_s", ctypes.c_double),
+        ("failed", ctypes.c_int64),
     ]
 
 
@@ -116,8 +117,8 @@ SIGNATURES = [
     ("kb_server_create", _I, [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(KbServerConfig)]),
     ("kb_server_destroy", _I, [_P]),
     ("kb_server_last_error", ctypes.c_char_p, [_P]),
-    ("kb_server_submit", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I,
-                              ctypes.POINTER(ctypes.c_int64)]),
+    ("kb_server_submit", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P,
+                          ctypes.POINTER(_I64)]),
     ("kb_server_step", _I, [_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]),
     ("kb_server_poll", _I, [_P, _I64, ctypes.POINTER(_I32)]),
     ("kb_server_fetch", _I, [_P, _I64, _P, _P, ctypes.POINTER(_I32)]),

@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <cstdio>
 #include <cstring>
@@ -122,6 +123,8 @@ struct Plan {
     bool reorder = false;  // locality order of the gather (RoundParams::perm)
     int subject = 0;       // kb_options::subject (generic CSE rounds when > 0)
     bool freeze = false;   // frozen blocks skip the rounds (RoundParams::frozen)
+    bool ext_table = false;  // block table and empty-signature minima live outside the workspace
+    bool ext_freeze = false;  // frozen-block state lives outside the workspace
     // hubs (host copies, ascending vertex id)
     std::vector<int32_t> hub_v;
     std::vector<int64_t> chunk_off, set_off;
@@ -157,9 +160,9 @@ void layout_round(Plan& P) {
     const int64_t nw = (P.n >> 5) + 1;
     const size_t H = P.hub_v.size();
     P.o_med = take(sizeof(int32_t) * (size_t)(std::min<int64_t>(P.n, P.m_proc / 2 + 1) + 1));
-    P.o_emin = take(sizeof(uint64_t) * (size_t)std::max<int64_t>(P.n, 1));
+    P.o_emin = take(P.ext_table ? 0 : sizeof(uint64_t) * (size_t)std::max<int64_t>(P.n, 1));
     P.o_slot = take(sizeof(int32_t) * (size_t)std::max<int64_t>(P.n, 1));
-    P.o_table = take(sizeof(uint64_t) * (size_t)P.cap);
+    P.o_table = take(P.ext_table ? 0 : sizeof(uint64_t) * (size_t)P.cap);
     P.o_bitmap = take(sizeof(uint32_t) * (size_t)nw);
     P.o_prefix = take(sizeof(uint32_t) * (size_t)(nw + 1));
     P.o_scan = take(sizeof(uint32_t) * kb::scan_tmp_words(nw));
@@ -178,14 +181,15 @@ void layout_round(Plan& P) {
     P.o_colr = take(P.reorder && !needs_in_csr(P.dir) ? sizeof(int32_t) * (size_t)P.m_proc : 0);
     P.o_hist = take(P.reorder ? sizeof(unsigned long long) * 512 : 0);
     P.o_ownkey = take(P.subject ? sizeof(int32_t) * (size_t)P.n : 0);
-    P.o_frozen = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
-    P.o_fmin = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    const bool own_freeze = P.freeze && !P.ext_freeze;
+    P.o_frozen = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_fmin = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_edgeless = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
-    P.o_shared = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
-    P.o_minof = take(P.freeze ? sizeof(uint32_t) * (size_t)P.n : 0);
+    P.o_shared = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_minof = take(own_freeze ? sizeof(uint32_t) * (size_t)P.n : 0);
     P.o_bm2 = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
-    P.o_moved = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
-    P.o_mark = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_moved = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_mark = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.total = off;
 }
 
@@ -306,7 +310,7 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
 // `rounds`: refinement rounds the call runs (decides the automatic locality
 // order); negative for batched and served refinement, which never reorder.
 kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, Plan& P, char** csr_base_out,
-                    bool for_query, int rounds) {
+                    bool for_query, int rounds, bool multi = false) {
     P.n = g->n;
     P.m = g->m;
     P.dir = opt->direction;
@@ -314,10 +318,10 @@ kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, P
     P.subject = opt->subject;
     P.reorder = rounds >= 0 && P.n > 0 && P.m_proc > 0 &&
                 (opt->reorder == 2 || (opt->reorder == 0 && rounds >= 24 && P.m_proc >= ((int64_t)1 << 22)));
-    // single-graph stratified rounds only: batched, served and incremental
-    // refinement plan with rounds < 0, and generic CSE keys need not hold the
-    // own previous block
-    P.freeze = rounds >= 0 && P.subject == KB_SUBJECT_PREVIOUS && opt->rekey_all == 0;
+    // stratified rounds of one graph or (multi) of batched and served graphs;
+    // incremental refinement plans without, and generic CSE keys need not
+    // hold the own previous block
+    P.freeze = (rounds >= 0 || multi) && P.subject == KB_SUBJECT_PREVIOUS && opt->rekey_all == 0;
     P.labels = opt->use_edge_labels && g->edge_labels != nullptr;
     int thr = opt->hub_threshold ? opt->hub_threshold : ctx->tuned_hub_threshold;
     P.thr = thr > 0 ? thr : kb::kDefaultHubThreshold;
@@ -419,6 +423,23 @@ struct Prepared {
     uint32_t* moved = nullptr;
     uint32_t* mark = nullptr;
     bool compact = false;  // small-kernel windows skip frozen vertices (many frozen)
+    // A caller-held block table (ext_cap slots) and empty-signature minima
+    // (at least n entries) that outlive one prepare: they are neither carved
+    // from the workspace nor cleared, and the table epoch carries on (the
+    // server re-plans its arena at every admission).
+    uint64_t* ext_table = nullptr;
+    uint64_t ext_cap = 0;
+    uint64_t* ext_emin = nullptr;
+    // Likewise the frozen-block state (frozen, frozen_min, shared, minof,
+    // moved, mark; bitmaps of at least n bits, minof of n entries): kept as it
+    // is by prepare, so that blocks stay frozen across a re-plan that moves
+    // no vertex (the server's admissions, which append at the arena's tail).
+    uint32_t* ext_frozen = nullptr;
+    uint32_t* ext_frozen_min = nullptr;
+    uint32_t* ext_shared = nullptr;
+    uint32_t* ext_minof = nullptr;
+    uint32_t* ext_moved = nullptr;
+    uint32_t* ext_mark = nullptr;
     bool med_on = true;    // some medium vertex refines this round
     bool hub_on = true;    // some hub refines this round
 };
@@ -426,7 +447,8 @@ struct Prepared {
 // Validate, plan, acquire the workspace, bind the round parameters, list the
 // medium vertices and reset the per-call state (block table, empty-signature
 // minima).  Synchronises.
-kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Prepared& R, int rounds) {
+kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Prepared& R, int rounds,
+                  bool multi = false) {
     cudaStream_t s = ctx->stream;
     const int64_t n = g->n;
     KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
@@ -457,7 +479,9 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
             base = reinterpret_cast<char*>(ctx->plan_tmp);
         }
     }
-    KB_TRY(make_plan(ctx, g, opt, P, &base, false, rounds));
+    P.ext_table = R.ext_table != nullptr;
+    P.ext_freeze = R.ext_frozen != nullptr;
+    KB_TRY(make_plan(ctx, g, opt, P, &base, false, rounds, multi));
     char* ws = nullptr;
     if (ctx->user_ws) {
         KB_TRY(acquire_workspace(ctx, P.total, &ws));
@@ -488,11 +512,15 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
     p.small_max = std::min(kb::kSmallDegree, P.thr);
     p.warp_verts = opt->small_task_vertices ? opt->small_task_vertices : ctx->tuned_warp_verts;
     p.hash_mode = opt->hash_mode;
-    p.table = reinterpret_cast<uint64_t*>(ws + P.o_table);
-    p.mask = P.cap - 1;
+    p.table = R.ext_table ? R.ext_table : reinterpret_cast<uint64_t*>(ws + P.o_table);
+    p.mask = (R.ext_table ? R.ext_cap : P.cap) - 1;
     p.slot_of = reinterpret_cast<int32_t*>(ws + P.o_slot);
-    p.emin = reinterpret_cast<uint64_t*>(ws + P.o_emin);
-    KB_CUDA(ctx, cudaMemsetAsync(p.emin, 0xff, sizeof(uint64_t) * (size_t)n, s));
+    if (R.ext_table) {
+        p.emin = R.ext_emin;  // entries of earlier rounds carry a larger round word and lose
+    } else {
+        p.emin = reinterpret_cast<uint64_t*>(ws + P.o_emin);
+        KB_CUDA(ctx, cudaMemsetAsync(p.emin, 0xff, sizeof(uint64_t) * (size_t)n, s));
+    }
     p.bitmap = reinterpret_cast<uint32_t*>(ws + P.o_bitmap);
     p.ctr = ctx->d_ctr;
     const size_t H = P.hub_v.size();
@@ -547,24 +575,36 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
     }
     R.total_chunks = H ? P.chunk_off[H] : 0;
     R.set_bytes = sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0);
-    KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
-    R.epoch = 0;
+    if (!R.ext_table) {
+        KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
+        R.epoch = 0;
+    }
     if (P.freeze) {
-        // nothing frozen before the starting level; shared starts empty
-        const size_t bw = sizeof(uint32_t) * (size_t)((n >> 5) + 1);
-        R.frozen = reinterpret_cast<uint32_t*>(ws + P.o_frozen);
-        R.frozen_min = reinterpret_cast<uint32_t*>(ws + P.o_fmin);
         R.edgeless = reinterpret_cast<uint32_t*>(ws + P.o_edgeless);
-        p.shared = reinterpret_cast<uint32_t*>(ws + P.o_shared);
-        p.minof = reinterpret_cast<uint32_t*>(ws + P.o_minof);
         R.bm[0] = p.bitmap;
         R.bm[1] = reinterpret_cast<uint32_t*>(ws + P.o_bm2);
         R.bm_cur = 0;
-        R.moved = reinterpret_cast<uint32_t*>(ws + P.o_moved);
-        R.mark = reinterpret_cast<uint32_t*>(ws + P.o_mark);
-        KB_CUDA(ctx, cudaMemsetAsync(R.frozen, 0, bw, s));
-        KB_CUDA(ctx, cudaMemsetAsync(R.frozen_min, 0, bw, s));
-        KB_CUDA(ctx, cudaMemsetAsync(p.shared, 0, bw, s));
+        if (R.ext_frozen) {
+            // the caller's state, kept as it is
+            R.frozen = R.ext_frozen;
+            R.frozen_min = R.ext_frozen_min;
+            p.shared = R.ext_shared;
+            p.minof = R.ext_minof;
+            R.moved = R.ext_moved;
+            R.mark = R.ext_mark;
+        } else {
+            // nothing frozen before the starting level; shared starts empty
+            const size_t bw = sizeof(uint32_t) * (size_t)((n >> 5) + 1);
+            R.frozen = reinterpret_cast<uint32_t*>(ws + P.o_frozen);
+            R.frozen_min = reinterpret_cast<uint32_t*>(ws + P.o_fmin);
+            p.shared = reinterpret_cast<uint32_t*>(ws + P.o_shared);
+            p.minof = reinterpret_cast<uint32_t*>(ws + P.o_minof);
+            R.moved = reinterpret_cast<uint32_t*>(ws + P.o_moved);
+            R.mark = reinterpret_cast<uint32_t*>(ws + P.o_mark);
+            KB_CUDA(ctx, cudaMemsetAsync(R.frozen, 0, bw, s));
+            KB_CUDA(ctx, cudaMemsetAsync(R.frozen_min, 0, bw, s));
+            KB_CUDA(ctx, cudaMemsetAsync(p.shared, 0, bw, s));
+        }
         kb::launch_edgeless_bits(n, p.row, R.edgeless, s);
         KB_CUDA(ctx, cudaGetLastError());
     }
@@ -575,7 +615,7 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
 // is cleared once every 255 rounds.
 kb_status next_epoch(kb_context* ctx, Prepared& R, cudaStream_t s) {
     if (R.epoch == 255) {
-        KB_CUDA(ctx, cudaMemsetAsync(R.p.table, 0, sizeof(uint64_t) * (size_t)R.P.cap, s));
+        KB_CUDA(ctx, cudaMemsetAsync(R.p.table, 0, sizeof(uint64_t) * (size_t)(R.p.mask + 1), s));
         R.epoch = 0;
     }
     R.p.epoch = ++R.epoch;
@@ -1073,7 +1113,7 @@ kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, 
     reset_timing(ctx);
     cudaStream_t s = ctx->stream;
     Prepared R;
-    KB_TRY(prepare(ctx, g, opt, R, -1));
+    KB_TRY(prepare(ctx, g, opt, R, -1, true));
     kb::RoundParams& p = R.p;
 
     // batch scratch
@@ -1137,10 +1177,27 @@ kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, 
             p.bitmap_prev = (i & 1) ? bm_a : bm_b;
             p.gbase_prev = bases + (size_t)(i - 1) * (size_t)(G + 1);
             p.gbase_cur = bases + (size_t)i * (size_t)(G + 1);
+            // frozen blocks as in a single-graph call (blocks never span
+            // graphs); the small kernel keeps consecutive windows and the
+            // medium and hub kernels always launch (no host reads inside the
+            // captured rounds)
+            p.frozen = R.frozen;
+            p.frozen_min = R.frozen_min;
+            p.moved = R.moved;
+            int32_t* out = levels + (size_t)i * (size_t)n;
             st = launch_round_body(ctx, R, cs, nullptr);
             if (st != KB_OK) break;
             kb::launch_carry_minima(p, cs);
-            kb::launch_renumber(p, R.prefix, R.scan_tmp, levels + (size_t)i * (size_t)n, cs);
+            kb::launch_renumber(p, R.prefix, R.scan_tmp, out, cs);
+            if (p.shared) {
+                if (cudaMemsetAsync(R.mark, 0, sizeof(uint32_t) * (size_t)nw, cs) != cudaSuccess) {
+                    st = fail(ctx, KB_ERR_CUDA, "memset failed");
+                    break;
+                }
+                kb::launch_dirty_blocks(p, R.edgeless, R.moved, out, kb::kMaxHubThreshold, R.mark, cs);
+                kb::launch_freeze_clean(n, p.bitmap, p.shared, R.edgeless, out, R.mark, R.frozen, R.frozen_min,
+                                        ctx->d_ctr, cs);
+            }
             kb::launch_graph_stop(p, i, kd, early, gact, glast, sticky, cs);
         }
         cudaGraph_t graph = nullptr;
@@ -1208,20 +1265,25 @@ struct Arena {
 
 struct ServeRequest {
     int64_t ticket = 0;
-    int state = 0;  // 0 waiting, 1 running, 2 done
+    int state = 0;  // 0 waiting, 1 running, 2 done, 3 failed (rejected at admission)
     int64_t n = 0, m = 0, m_proc = 0;
-    std::vector<int64_t> row;
-    std::vector<int32_t> col, lab, vlab;
+    // the caller's host arrays, read at admission (lab / vlab null when unused)
+    const int64_t* row = nullptr;
+    const int32_t* col = nullptr;
+    const int32_t* lab = nullptr;
+    const int32_t* vlab = nullptr;
     kb_options opt;
     int k = 0;
     int slot = -1;
     int round = 0;  // next level to compute (0 = level 0)
     int32_t* d_levels = nullptr;
     size_t level_bytes = 0;
-    std::vector<int32_t> levels;  // host copy after completion
+    int32_t* out = nullptr;               // caller's host levels, or null: kept in `levels`
+    std::unique_ptr<int32_t[]> levels;    // host copy after completion (when out is null)
     std::vector<int64_t> counts;
     int32_t levels_computed = 0;
     double t_submit = 0, t_done = 0;
+    std::string error;
 };
 
 struct Slot {
@@ -1249,6 +1311,26 @@ struct kb_server {
     std::map<int64_t, ServeRequest> reqs;
     int64_t next_ticket = 1;
     size_t level_bytes_in_use = 0;
+    // level stores are reused: freed ones wait in a list per power-of-two size
+    std::map<size_t, std::vector<int32_t*>> level_pool;
+    // block table and empty-signature minima of the arena, kept across re-plans
+    uint64_t* table = nullptr;
+    uint64_t table_cap = 0;
+    uint64_t* emin = nullptr;
+    uint64_t round_counter = 0;  // rounds run; decreasing round words of the minima
+    // Frozen-block state of the arena, sized for a full arena and kept across
+    // re-plans: frozen vertices, minima of frozen blocks, shared marks,
+    // smallest members, moved vertices, dirty blocks, and the two bitmaps of
+    // block minima used in turn.
+    uint32_t* frz[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t* minof = nullptr;
+    uint32_t* bitmap1 = nullptr;
+    int64_t planned_n = 0;        // arena vertices at the last re-plan
+    bool vertices_moved = false;  // a compaction since the last re-plan
+    // The last step's minima and smallest members are valid for this step's
+    // moved vertices (false after a compaction, which moves vertices and
+    // clears the frozen blocks)
+    bool history = false;
     // per-slot device arrays (capacity max_requests + dead slots: sized by max_slots)
     int32_t max_slots = 0;
     int32_t* vgraph = nullptr;
@@ -1267,12 +1349,12 @@ struct kb_server {
     // round state
     Prepared R;
     bool dirty = true;
-    uint32_t rounds_since_prepare = 0;
+
     int bmsel = 0;
     uint32_t* bm_ws = nullptr;
     // stats
     double t_first = -1;
-    int64_t submitted = 0, completed = 0, steps = 0, compactions = 0;
+    int64_t submitted = 0, completed = 0, failed = 0, steps = 0, compactions = 0;
     double edge_rounds = 0;
     std::vector<double> latencies_ms;
 };
@@ -1305,7 +1387,8 @@ kb_status sfail(kb_server* sv, kb_status st, const char* fmt, ...) {
     } while (0)
 
 // Copy request r's graph into the arena at the tail as slot `slot`.
-kb_status place_request(kb_server* sv, ServeRequest& r, int slot) {
+kb_status place_request(kb_server* sv, ServeRequest& r, int slot, bool* rejected) {
+    *rejected = false;
     kb_context* ctx = sv->ctx;
     cudaStream_t s = ctx->stream;
     Arena& A = sv->arena[sv->cur];
@@ -1322,7 +1405,7 @@ kb_status place_request(kb_server* sv, ServeRequest& r, int slot) {
     P.m = m;
     P.dir = r.opt.direction;
     P.m_proc = mp;
-    P.labels = !r.lab.empty();
+    P.labels = r.lab != nullptr;
     layout_csr(P);
     const size_t o_csr = take(P.csr_bytes);
     if (off > sv->stage_bytes) {
@@ -1336,12 +1419,24 @@ kb_status place_request(kb_server* sv, ServeRequest& r, int slot) {
         sv->stage_bytes = off;
     }
     char* b = reinterpret_cast<char*>(sv->stage);
-    SV_CUDA(sv, cudaMemcpyAsync(b + o_row, r.row.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
-    if (m) SV_CUDA(sv, cudaMemcpyAsync(b + o_col, r.col.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+    SV_CUDA(sv, cudaMemcpyAsync(b + o_row, r.row, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
+    if (m) SV_CUDA(sv, cudaMemcpyAsync(b + o_col, r.col, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
     if (m && P.labels)
-        SV_CUDA(sv, cudaMemcpyAsync(b + o_lab, r.lab.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
-    if (!r.vlab.empty())
-        SV_CUDA(sv, cudaMemcpyAsync(b + o_vlab, r.vlab.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+        SV_CUDA(sv, cudaMemcpyAsync(b + o_lab, r.lab, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+    if (r.vlab) SV_CUDA(sv, cudaMemcpyAsync(b + o_vlab, r.vlab, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    // the arena is shared: a malformed CSR is checked on the device before it
+    // is placed, and the request fails alone
+    SV_CUDA(sv, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    kb::launch_validate(n, m, reinterpret_cast<const int64_t*>(b + o_row), reinterpret_cast<const int32_t*>(b + o_col),
+                        ctx->d_ctr, s);
+    SV_CUDA(sv, cudaGetLastError());
+    SV_CUDA(sv, cudaMemcpyAsync(ctx->h_ctr, ctx->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    SV_CUDA(sv, cudaStreamSynchronize(s));
+    if (ctx->h_ctr->err & kb::kErrInvalid) {
+        *rejected = true;
+        r.error = "row_offsets not monotone from 0 to m, or a neighbour id out of [0, n)";
+        return KB_OK;
+    }
     kb::PlaceArgs a{};
     a.srow = reinterpret_cast<const int64_t*>(b + o_row);
     a.scol = reinterpret_cast<const int32_t*>(b + o_col);
@@ -1354,7 +1449,7 @@ kb_status place_request(kb_server* sv, ServeRequest& r, int slot) {
         a.scol = reinterpret_cast<const int32_t*>(csr + P.o_colp);
         a.slab = P.labels ? reinterpret_cast<const int32_t*>(csr + P.o_labp) : nullptr;
     }
-    a.svlab = r.vlab.empty() ? nullptr : reinterpret_cast<const int32_t*>(b + o_vlab);
+    a.svlab = r.vlab ? reinterpret_cast<const int32_t*>(b + o_vlab) : nullptr;
     a.drow = A.row;
     a.dcol = A.col;
     a.dlab = A.lab;
@@ -1429,6 +1524,7 @@ kb_status compact(kb_server* sv) {
     sv->bsel = 0;
     sv->gbase_host.clear();
     sv->dirty = true;
+    sv->vertices_moved = true;
     ++sv->compactions;
     return KB_OK;
 }
@@ -1440,6 +1536,13 @@ size_t free_device_bytes() {
         return 0;
     }
     return fr;
+}
+
+// Size class of a level store: the next power of two of at least 256 bytes.
+size_t level_store_bytes(size_t bytes) {
+    size_t b = 256;
+    while (b < bytes) b <<= 1;
+    return b;
 }
 
 // Admit waiting requests in arrival order while they fit.
@@ -1456,11 +1559,12 @@ kb_status admit(kb_server* sv, bool* changed) {
         int live = 0;
         for (const Slot& sl : sv->slots) live += sl.ticket >= 0;
         if (live >= sv->cfg.max_requests) break;
-        const size_t lb = sizeof(int32_t) * (size_t)r.n * (size_t)(r.k + 1);
+        const size_t lb = level_store_bytes(sizeof(int32_t) * (size_t)r.n * (size_t)(r.k + 1));
+        std::vector<int32_t*>& pooled = sv->level_pool[lb];
         const size_t budget = sv->cfg.memory_budget;
         if (budget) {
             if (sv->level_bytes_in_use + lb > budget) break;
-        } else {
+        } else if (pooled.empty()) {
             const size_t fr = free_device_bytes();
             if (fr < lb + ((size_t)1 << 30)) break;
         }
@@ -1476,41 +1580,65 @@ kb_status admit(kb_server* sv, bool* changed) {
             if (ln + r.n > sv->cfg.max_vertices || lm + r.m_proc > sv->cfg.max_edges) break;
             SV_TRY(sv, compact(sv));
         }
-        if (cudaMalloc(&r.d_levels, std::max<size_t>(lb, 4)) != cudaSuccess) {
+        if (!pooled.empty()) {
+            r.d_levels = pooled.back();
+            pooled.pop_back();
+        } else if (cudaMalloc(&r.d_levels, lb) != cudaSuccess) {
             cudaGetLastError();
             r.d_levels = nullptr;
             break;
         }
         r.level_bytes = lb;
         sv->level_bytes_in_use += lb;
-        SV_TRY(sv, place_request(sv, r, (int)sv->slots.size()));
+        bool rejected = false;
+        SV_TRY(sv, place_request(sv, r, (int)sv->slots.size(), &rejected));
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->waiting.pop_front();
+        if (rejected) {
+            sv->level_pool[lb].push_back(r.d_levels);
+            sv->level_bytes_in_use -= lb;
+            r.d_levels = nullptr;
+            r.state = 3;
+            r.row = nullptr;
+            ++sv->failed;
+            continue;
+        }
         r.state = 1;
         r.round = 0;
         r.counts.assign((size_t)r.k + 1, 0);
-        {
-            std::lock_guard<std::mutex> lk(sv->mu);
-            sv->waiting.pop_front();
-        }
+        r.row = nullptr;  // the caller's graph arrays are no longer read
+        r.col = r.lab = r.vlab = nullptr;
         *changed = true;
     }
     return KB_OK;
 }
 
-// Finish request r after its last round: copy its levels to the host.
-kb_status retire(kb_server* sv, ServeRequest& r, int last) {
+// Finish request r after its last round, in two parts so that every request
+// retiring in a step shares one synchronisation: retire_copy queues the copy
+// of its levels to the host (the caller's buffer given at submission, else a
+// buffer of its own; rows after the last refined level repeat it), and
+// retire_finish, after the stream has drained, releases its level store.
+kb_status retire_copy(kb_server* sv, ServeRequest& r, int last) {
     cudaStream_t s = sv->ctx->stream;
-    r.levels.assign((size_t)r.n * (size_t)(r.k + 1), 0);
-    if (r.n)
-        SV_CUDA(sv, cudaMemcpyAsync(r.levels.data(), r.d_levels, sizeof(int32_t) * (size_t)r.n * (size_t)(last + 1),
-                                    cudaMemcpyDeviceToHost, s));
-    SV_CUDA(sv, cudaStreamSynchronize(s));
-    for (int j = last + 1; j <= r.k; ++j) {
-        std::copy(r.levels.begin() + (size_t)last * (size_t)r.n, r.levels.begin() + (size_t)(last + 1) * (size_t)r.n,
-                  r.levels.begin() + (size_t)j * (size_t)r.n);
-        r.counts[(size_t)j] = r.counts[(size_t)last];
+    const size_t n = (size_t)r.n;
+    if (!r.out) {
+        r.levels.reset(new (std::nothrow) int32_t[std::max<size_t>(n * (size_t)(r.k + 1), 1)]);
+        if (!r.levels) return sfail(sv, KB_ERR_OOM, "cannot allocate host memory for the levels");
     }
+    int32_t* dst = r.out ? r.out : r.levels.get();
+    if (n) {
+        SV_CUDA(sv, cudaMemcpyAsync(dst, r.d_levels, sizeof(int32_t) * n * (size_t)(last + 1), cudaMemcpyDeviceToHost, s));
+        for (int j = last + 1; j <= r.k; ++j)
+            SV_CUDA(sv, cudaMemcpyAsync(dst + (size_t)j * n, r.d_levels + (size_t)last * n, sizeof(int32_t) * n,
+                                        cudaMemcpyDeviceToHost, s));
+    }
+    return KB_OK;
+}
+
+void retire_finish(kb_server* sv, ServeRequest& r, int last) {
+    for (int j = last + 1; j <= r.k; ++j) r.counts[(size_t)j] = r.counts[(size_t)last];
     r.levels_computed = last;
-    cudaFree(r.d_levels);
+    sv->level_pool[r.level_bytes].push_back(r.d_levels);
     r.d_levels = nullptr;
     sv->level_bytes_in_use -= r.level_bytes;
     sv->slots[(size_t)r.slot].ticket = -1;
@@ -1521,7 +1649,6 @@ kb_status retire(kb_server* sv, ServeRequest& r, int last) {
     ++sv->completed;
     sv->latencies_ms.push_back(1000.0 * (r.t_done - r.t_submit));
     sv->edge_rounds += (double)r.m_proc * (double)last;
-    return KB_OK;
 }
 
 kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
@@ -1532,7 +1659,16 @@ kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
     SV_TRY(sv, admit(sv, &changed));
     if (changed) sv->dirty = true;
     int live = 0;
-    for (const Slot& sl : sv->slots) live += sl.ticket >= 0;
+    int64_t live_n = 0;
+    for (const Slot& sl : sv->slots)
+        if (sl.ticket >= 0) {
+            ++live;
+            live_n += sl.n;
+        }
+    // every round's kernels span the whole arena, retired ranges included:
+    // pack the live requests once the dead ones dominate (cheap under light
+    // load, when little is live)
+    if (live > 0 && sv->n_used - live_n > 4 * live_n + ((int64_t)1 << 22)) SV_TRY(sv, compact(sv));
     if (live > 0) {
         const int G = (int)sv->slots.size();
         Arena& A = sv->arena[sv->cur];
@@ -1545,14 +1681,36 @@ kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
             o.load_factor = sv->cfg.load_factor;
             o.hub_threshold = sv->cfg.hub_threshold;
             o.hash_mode = sv->cfg.hash_mode;
-            SV_TRY(sv, prepare(ctx, &view, &o, sv->R, -1));
-            sv->bm_ws = sv->R.p.bitmap;
+            sv->R.ext_table = sv->table;
+            sv->R.ext_cap = sv->table_cap;
+            sv->R.ext_emin = sv->emin;
+            sv->R.ext_frozen = sv->frz[0];
+            sv->R.ext_frozen_min = sv->frz[1];
+            sv->R.ext_shared = sv->frz[2];
+            sv->R.ext_moved = sv->frz[3];
+            sv->R.ext_mark = sv->frz[4];
+            sv->R.ext_minof = sv->minof;
+            const size_t bw = sizeof(uint32_t) * (size_t)((sv->n_used >> 5) + 1);
+            if (sv->vertices_moved) {
+                // compacted: vertex ids moved, nothing carries over
+                for (int f = 0; f < 3; ++f) SV_CUDA(sv, cudaMemsetAsync(sv->frz[f], 0, bw, s));
+                sv->history = false;
+                sv->vertices_moved = false;
+            } else {
+                // admitted at the tail: the new vertices start unfrozen, the
+                // others keep their blocks' state; the bits past the last
+                // vertex are cleared too (rank scans count whole words)
+                const int64_t word_end = ((sv->n_used >> 5) + 1) * 32;
+                for (int f = 0; f < 3; ++f) kb::launch_clear_bits(sv->frz[f], sv->planned_n, word_end, s);
+            }
+            SV_TRY(sv, prepare(ctx, &view, &o, sv->R, -1, true));
+            sv->bm_ws = sv->bitmap1;
+            sv->planned_n = sv->n_used;
             std::vector<int64_t> voff((size_t)G + 1);
             for (int j = 0; j < G; ++j) voff[(size_t)j] = sv->slots[(size_t)j].vbase;
             voff[(size_t)G] = sv->n_used;
             SV_CUDA(sv, cudaMemcpyAsync(sv->voff, voff.data(), sizeof(int64_t) * (size_t)(G + 1), cudaMemcpyHostToDevice, s));
             kb::launch_vertex_graph(sv->voff, G, sv->n_used, sv->vgraph, s);
-            sv->rounds_since_prepare = 0;
             sv->dirty = false;
         }
         // per-slot flags for this step
@@ -1577,7 +1735,7 @@ kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
         SV_CUDA(sv, cudaMemcpyAsync(sv->slot_n, sn.data(), sizeof(int64_t) * (size_t)G, cudaMemcpyHostToDevice, s));
         // one round for everything in flight
         SV_TRY(sv, next_epoch(ctx, sv->R, s));
-        p.ehigh = 0xffffffffu - (++sv->rounds_since_prepare);
+        p.ehigh = 0xffffffffu - (uint32_t)(++sv->round_counter);
         p.vgraph = sv->vgraph;
         p.voff = sv->voff;
         p.n_graphs = G;
@@ -1591,10 +1749,25 @@ kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
         p.gbase_prev = sv->bases[1 - (sv->steps & 1)];
         p.gbase_cur = sv->bases[sv->steps & 1];
         int32_t* out = A.B[1 - sv->bsel];
+        // frozen blocks, as in a single-graph call (blocks never span graphs)
+        p.frozen = sv->R.frozen;
+        p.frozen_min = sv->R.frozen_min;
+        p.moved = sv->history ? sv->R.moved : nullptr;
         SV_TRY(sv, launch_round_body(ctx, sv->R, s, nullptr));
         kb::launch_carry_minima(p, s);
         kb::launch_renumber(p, sv->R.prefix, sv->R.scan_tmp, out, s);
         kb::launch_emit(sv->n_used, sv->vgraph, out, p.gbase_cur, sv->slot_levels, sv->slot_row, sv->slot_n, sv->voff, s);
+        if (p.shared) {
+            const uint32_t* mark = nullptr;
+            if (p.moved) {
+                SV_CUDA(sv, cudaMemsetAsync(sv->R.mark, 0, sizeof(uint32_t) * (size_t)((sv->n_used >> 5) + 1), s));
+                kb::launch_dirty_blocks(p, sv->R.edgeless, sv->R.moved, out, kb::kMaxHubThreshold, sv->R.mark, s);
+                mark = sv->R.mark;
+            }
+            kb::launch_freeze_clean(sv->n_used, p.bitmap, p.shared, sv->R.edgeless, out, mark, sv->R.frozen,
+                                    sv->R.frozen_min, ctx->d_ctr, s, sv->vgraph, sv->gmode);
+        }
+        sv->history = true;
         SV_CUDA(sv, cudaGetLastError());
         sv->gbase_host.assign((size_t)G + 1, 0);
         SV_CUDA(sv, cudaMemcpyAsync(sv->gbase_host.data(), p.gbase_cur, sizeof(uint32_t) * (size_t)(G + 1),
@@ -1606,7 +1779,8 @@ kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
         }
         sv->bsel = 1 - sv->bsel;
         sv->bmsel = 1 - sv->bmsel;
-        // bookkeeping and retirement
+        // bookkeeping and retirement (one synchronisation for all copies)
+        std::vector<std::pair<ServeRequest*, int>> finished;
         for (int j = 0; j < G; ++j) {
             const Slot sl = sv->slots[(size_t)j];
             if (sl.ticket < 0) continue;
@@ -1617,7 +1791,14 @@ kb_status server_step(kb_server* sv, int32_t* running, int32_t* waiting_out) {
             bool done = done_round >= r.k;
             if (done_round > 0 && r.opt.early_stop && cnt == r.counts[(size_t)done_round - 1]) done = true;
             ++r.round;
-            if (done) SV_TRY(sv, retire(sv, r, done_round));
+            if (done) {
+                SV_TRY(sv, retire_copy(sv, r, done_round));
+                finished.push_back({&r, done_round});
+            }
+        }
+        if (!finished.empty()) {
+            SV_CUDA(sv, cudaStreamSynchronize(s));
+            for (auto& f : finished) retire_finish(sv, *f.first, f.second);
         }
         ++sv->steps;
     }
@@ -1972,10 +2153,24 @@ kb_status kb_server_create(kb_server** out, int device, void* stream, const kb_s
     alloc((void**)&sv->slot_levels, sizeof(int32_t*) * (size_t)S);
     alloc((void**)&sv->slot_row, sizeof(int32_t) * (size_t)S);
     alloc((void**)&sv->slot_n, sizeof(int64_t) * (size_t)S);
+    // the arena's block table and empty-signature minima, sized for a full arena
+    const float lf = cfg->load_factor > 0.f ? cfg->load_factor : 0.5f;
+    sv->table_cap = next_pow2((uint64_t)((double)N / (double)lf) + 1);
+    if (sv->table_cap < 1024) sv->table_cap = 1024;
+    alloc((void**)&sv->table, sizeof(uint64_t) * (size_t)sv->table_cap);
+    alloc((void**)&sv->emin, sizeof(uint64_t) * (size_t)N);
+    const size_t bwN = sizeof(uint32_t) * (size_t)((N >> 5) + 1);
+    for (int f = 0; f < 5; ++f) alloc((void**)&sv->frz[f], bwN);
+    alloc((void**)&sv->minof, sizeof(uint32_t) * (size_t)N);
+    alloc((void**)&sv->bitmap1, bwN);
     if (ok) {
         ok = cudaMemset(sv->arena[0].row, 0, sizeof(int64_t)) == cudaSuccess &&
              cudaMemset(sv->arena[1].row, 0, sizeof(int64_t)) == cudaSuccess &&
-             cudaMemset(sv->bitmap2, 0, sizeof(uint32_t) * (size_t)((N >> 5) + 1)) == cudaSuccess;
+             cudaMemset(sv->bitmap2, 0, sizeof(uint32_t) * (size_t)((N >> 5) + 1)) == cudaSuccess &&
+             cudaMemset(sv->table, 0, sizeof(uint64_t) * (size_t)sv->table_cap) == cudaSuccess &&
+             cudaMemset(sv->emin, 0xff, sizeof(uint64_t) * (size_t)N) == cudaSuccess &&
+             cudaMemset(sv->frz[0], 0, bwN) == cudaSuccess && cudaMemset(sv->frz[1], 0, bwN) == cudaSuccess &&
+             cudaMemset(sv->frz[2], 0, bwN) == cudaSuccess && cudaMemset(sv->bitmap1, 0, bwN) == cudaSuccess;
     }
     if (!ok) {
         kb_server_destroy(sv);
@@ -1993,6 +2188,13 @@ kb_status kb_server_destroy(kb_server* sv) {
     }
     for (auto& kv : sv->reqs)
         if (kv.second.d_levels) cudaFree(kv.second.d_levels);
+    for (auto& kv : sv->level_pool)
+        for (int32_t* b : kv.second) cudaFree(b);
+    cudaFree(sv->table);
+    cudaFree(sv->emin);
+    for (int f = 0; f < 5; ++f) cudaFree(sv->frz[f]);
+    cudaFree(sv->minof);
+    cudaFree(sv->bitmap1);
     for (int a = 0; a < 2; ++a) {
         Arena& A = sv->arena[a];
         cudaFree(A.row);
@@ -2020,7 +2222,9 @@ kb_status kb_server_destroy(kb_server* sv) {
 
 const char* kb_server_last_error(const kb_server* sv) { return sv ? sv->last_error.c_str() : "no server"; }
 
-kb_status kb_server_submit(kb_server* sv, const kb_graph* g, const kb_options* opt, int k, int64_t* ticket) {
+kb_status kb_server_submit(kb_server* sv, const kb_graph* g, const kb_options* opt, int k, int32_t* levels_out,
+                           int64_t* ticket) {
+    static const int64_t kEmptyRow[1] = {0};
     if (!sv || !ticket) return KB_ERR_INVALID_ARG;
     if (!g || !opt) return sfail(sv, KB_ERR_INVALID_ARG, "graph and options must not be NULL");
     if (opt->subject != KB_SUBJECT_PREVIOUS)
@@ -2029,28 +2233,25 @@ kb_status kb_server_submit(kb_server* sv, const kb_graph* g, const kb_options* o
         return sfail(sv, KB_ERR_INVALID_ARG, "bad request");
     if (g->n > 0 && !g->row_offsets) return sfail(sv, KB_ERR_INVALID_ARG, "row_offsets is NULL");
     if (g->m > 0 && !g->col_indices) return sfail(sv, KB_ERR_INVALID_ARG, "col_indices is NULL");
+    if (g->n == 0 && g->m != 0) return sfail(sv, KB_ERR_INVALID_ARG, "edges without vertices");
     const int64_t mp = opt->direction == KB_DIR_BOTH ? 2 * g->m : g->m;
     if (g->n > sv->cfg.max_vertices || mp > sv->cfg.max_edges)
         return sfail(sv, KB_ERR_INVALID_ARG, "request larger than the arena");
-    // host-side validation of the CSR (the arena is shared: a bad request must not reach it)
+    // the ends of the offsets here; every offset and neighbour id is checked
+    // on the device at admission, before the graph reaches the shared arena
     if (g->n > 0 && (g->row_offsets[0] != 0 || g->row_offsets[g->n] != g->m))
         return sfail(sv, KB_ERR_INVALID_ARG, "row_offsets must run from 0 to m");
-    for (int64_t v = 0; v < g->n; ++v)
-        if (g->row_offsets[v + 1] < g->row_offsets[v]) return sfail(sv, KB_ERR_INVALID_ARG, "row_offsets not monotone");
-    for (int64_t e = 0; e < g->m; ++e)
-        if (g->col_indices[e] < 0 || g->col_indices[e] >= g->n)
-            return sfail(sv, KB_ERR_INVALID_ARG, "neighbour id out of range");
     ServeRequest r;
     r.n = g->n;
     r.m = g->m;
     r.m_proc = mp;
     r.opt = *opt;
     r.k = k;
-    if (g->n > 0) r.row.assign(g->row_offsets, g->row_offsets + g->n + 1);
-    else r.row.assign(1, 0);
-    if (g->m) r.col.assign(g->col_indices, g->col_indices + g->m);
-    if (g->m && g->edge_labels && opt->use_edge_labels) r.lab.assign(g->edge_labels, g->edge_labels + g->m);
-    if (g->n && g->vertex_labels && opt->use_vertex_labels) r.vlab.assign(g->vertex_labels, g->vertex_labels + g->n);
+    r.row = g->n > 0 ? g->row_offsets : kEmptyRow;
+    r.col = g->col_indices;
+    r.lab = (g->m && g->edge_labels && opt->use_edge_labels) ? g->edge_labels : nullptr;
+    r.vlab = (g->n && g->vertex_labels && opt->use_vertex_labels) ? g->vertex_labels : nullptr;
+    r.out = levels_out;
     r.t_submit = now_s();
     std::lock_guard<std::mutex> lk(sv->mu);
     r.ticket = sv->next_ticket++;
@@ -2084,8 +2285,21 @@ kb_status kb_server_fetch(kb_server* sv, int64_t ticket, int32_t* levels, int64_
     auto it = sv->reqs.find(ticket);
     if (it == sv->reqs.end()) return KB_ERR_NOT_FOUND;
     ServeRequest& r = it->second;
+    if (r.state == 3) {
+        const std::string why = r.error;
+        sv->reqs.erase(it);
+        return sfail(sv, KB_ERR_INVALID_ARG, "request %lld was rejected at admission: %s", (long long)ticket,
+                     why.c_str());
+    }
     if (r.state != 2) return sfail(sv, KB_ERR_INVALID_ARG, "request %lld has not finished", (long long)ticket);
-    if (levels && !r.levels.empty()) std::memcpy(levels, r.levels.data(), sizeof(int32_t) * r.levels.size());
+    if (levels && r.n) {
+        const size_t bytes = sizeof(int32_t) * (size_t)r.n * (size_t)(r.k + 1);
+        if (r.out) {
+            if (levels != r.out) std::memcpy(levels, r.out, bytes);
+        } else {
+            std::memcpy(levels, r.levels.get(), bytes);
+        }
+    }
     if (counts) std::memcpy(counts, r.counts.data(), sizeof(int64_t) * r.counts.size());
     if (levels_computed) *levels_computed = r.levels_computed;
     sv->reqs.erase(it);
@@ -2098,6 +2312,7 @@ kb_status kb_server_get_stats(kb_server* sv, kb_server_stats* st) {
     std::memset(st, 0, sizeof(*st));
     st->submitted = sv->submitted;
     st->completed = sv->completed;
+    st->failed = sv->failed;
     int run = 0;
     for (const Slot& sl : sv->slots) run += sl.ticket >= 0;
     st->running = run;

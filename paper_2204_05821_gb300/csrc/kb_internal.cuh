@@ -224,9 +224,14 @@ void launch_dirty_blocks(const RoundParams& p, const uint32_t* edgeless, const u
 // eighth of the vertices moved).  frozen_min receives the minima of frozen
 // blocks; shared keeps exactly their marks; ctr->frozen counts the frozen
 // vertices.
+// Serving (vgraph, gmode given): the vertices of graphs that computed their
+// level 0 in this step are not frozen by the edgeless rule.
 void launch_freeze_clean(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
                          const int32_t* level, const uint32_t* mark, uint32_t* frozen, uint32_t* frozen_min,
-                         Counters* ctr, cudaStream_t s);
+                         Counters* ctr, cudaStream_t s, const int32_t* vgraph = nullptr,
+                         const uint8_t* gmode = nullptr);
+// Clear bits a..b-1 of a bitmap.
+void launch_clear_bits(uint32_t* words, int64_t a, int64_t b, cudaStream_t s);
 // The vertices this round re-keys (not in p.frozen) and their edges, per
 // kernel family, into ctr->keyed_v / keyed_e (work accounting only).
 void launch_round_work(const RoundParams& p, cudaStream_t s);

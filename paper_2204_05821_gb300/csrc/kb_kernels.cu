@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
     }
 }
 
-// Canonical ids of a single-graph stratified round with frozen blocks
-// (RoundParams::minof): assign_kernel's work with every lane of a warp on one
+// Canonical ids of a stratified round with frozen blocks (RoundParams::minof;
+// one graph, or several at once): assign_kernel's work with every lane of a warp on one
 // bitmap word (a warp-uniform loop), so that the moved vertices (re-keyed
 // vertices whose smallest block member changed: v itself or minof[v] at the
 // previous level, read before minof[v] is rewritten) leave as one word per
@@ -463,7 +463,11 @@ __global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p,
         const int64_t v = base + lane;
         bool mv = false;
         uint32_t mark = kNoMark;
-        if (v < p.n) {
+        if (v < p.n && !vertex_active(p, v)) {
+            // a batched graph that stopped: its ids shift with the graphs before it
+            const int32_t g = p.vgraph[v];
+            out[v] = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
+        } else if (v < p.n) {
             const bool fz = vertex_frozen(p, v);
             uint32_t mn = (uint32_t)v;
             if (!((p.bitmap[v >> 5] >> (v & 31)) & 1u)) {
@@ -487,7 +491,8 @@ __global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p,
             out[v] = b;
             if (p.perm) p.gat[p.perm[v]] = b;
             if (!fz) {
-                if (moved) {
+                // a graph that computed its level 0 here has no previous level
+                if (moved && !vertex_level0(p, v)) {
                     const uint32_t pm = ((p.bitmap_prev[v >> 5] >> (v & 31)) & 1u) ? (uint32_t)v : p.minof[v];
                     mv = pm != mn;
                 }
@@ -575,9 +580,10 @@ __global__ void __launch_bounds__(256) dirty_blocks_kernel(const RoundParams p, 
     const uint32_t excl = incl - __popc(c);
     for (int t = 0; t < total; t += 32) {
         const int64_t v = dealt_vertex(w0, excl, c, t + lane, total);
-        if (v < 0) continue;
+        if (v < 0 || !vertex_active(p, v)) continue;
         const int64_t a = p.row[v], e_end = p.row[v + 1];
-        bool dirty = e_end - a > max_scan;
+        // a graph that computed its level 0 here has no history: all dirty
+        bool dirty = e_end - a > max_scan || vertex_level0(p, v);
         for (int64_t e0 = a; e0 < e_end && !dirty; e0 += 4) {
             int32_t w[4];
 #pragma unroll
@@ -605,7 +611,8 @@ __global__ void __launch_bounds__(256) dirty_blocks_kernel(const RoundParams p, 
 __global__ void __launch_bounds__(256) freeze_clean_kernel(int64_t n, const uint32_t* bitmap, uint32_t* shared,
                                                             const uint32_t* edgeless, const int32_t* level,
                                                             const uint32_t* mark, uint32_t* frozen,
-                                                            uint32_t* frozen_min, Counters* ctr) {
+                                                            uint32_t* frozen_min, Counters* ctr, const int32_t* vgraph,
+                                                            const uint8_t* gmode) {
     __shared__ uint32_t s_clean[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nw = (n >> 5) + 1;
@@ -619,6 +626,22 @@ __global__ void __launch_bounds__(256) freeze_clean_kernel(int64_t n, const uint
         sh = shared[w];
         e = edgeless ? edgeless[w] : 0u;
         c = mark ? candidate_word(bitmap, shared, edgeless, w, n) : 0u;
+    }
+    if (gmode && edgeless) {
+        // serving: a graph that computed its level 0 in this step has not had
+        // its edgeless blocks formed by a round yet
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t ej = __shfl_sync(kFull, e, j);
+            const int64_t vj = (w0 + j) * 32 + lane;
+            const bool lvl0 = vj < n && ((ej >> lane) & 1u) && gmode[vgraph[vj]] == 1;
+            const uint32_t drop = __ballot_sync(kFull, lvl0);
+            if (lane == j) {
+                e &= ~drop;
+                // their blocks are looked up (and marked dirty) instead; without
+                // marks nothing but singletons is frozen
+                if (mark) c |= drop & ~(b & ~sh);
+            }
+        }
     }
     s_clean[warp][lane] = 0u;
     __syncwarp();
@@ -638,10 +661,12 @@ __global__ void __launch_bounds__(256) freeze_clean_kernel(int64_t n, const uint
     }
     __syncwarp();
     if (w < nw) {
-        const uint32_t single = b & ~sh;
+        // no bit past the last vertex survives (rank scans count whole words)
+        const uint32_t valid = w * 32 + 32 <= n ? 0xffffffffu : (n > w * 32 ? (1u << (uint32_t)(n - w * 32)) - 1u : 0u);
+        const uint32_t single = b & ~sh & valid;
         const uint32_t cl = s_clean[warp][lane];
-        const uint32_t fz = single | e | cl;
-        const uint32_t fm = single | (b & (e | cl));
+        const uint32_t fz = single | (e & valid) | cl;
+        const uint32_t fm = single | (b & (e | cl) & valid);
         frozen[w] = fz;
         frozen_min[w] = fm;
         shared[w] = sh & fm;
@@ -675,6 +700,18 @@ __global__ void __launch_bounds__(256) round_work_kernel(int64_t n, const int64_
         for (int w = 0; w < 8; ++w) t += s_sum[threadIdx.x][w];
         int64_t* dst = threadIdx.x < 3 ? &ctr->keyed_v[threadIdx.x] : &ctr->keyed_e[threadIdx.x - 3];
         if (t) atomicAdd(reinterpret_cast<unsigned long long*>(dst), t);
+    }
+}
+
+// Clear bits a..b-1 of a bitmap (partial words at the ends keep their other bits).
+__global__ void clear_bits_kernel(uint32_t* words, int64_t a, int64_t b) {
+    const int64_t w0 = a >> 5, w1 = (b - 1) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = w0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w <= w1; w += stride) {
+        uint32_t keep = 0u;
+        if (w == w0 && (a & 31)) keep |= (1u << (a & 31)) - 1u;
+        if (w == w1 && (b & 31)) keep |= ~((1u << (b & 31)) - 1u);
+        words[w] &= keep;
     }
 }
 
@@ -871,11 +908,11 @@ void launch_dirty_blocks(const RoundParams& p, const uint32_t* edgeless, const u
 
 void launch_freeze_clean(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
                          const int32_t* level, const uint32_t* mark, uint32_t* frozen, uint32_t* frozen_min,
-                         Counters* ctr, cudaStream_t s) {
+                         Counters* ctr, cudaStream_t s, const int32_t* vgraph, const uint8_t* gmode) {
     if (n <= 0) return;
     const int64_t warps = ((n >> 5) + 1 + 31) / 32;  // 32 bitmap words each
     freeze_clean_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(n, bitmap, shared, edgeless, level, mark, frozen,
-                                                                     frozen_min, ctr);
+                                                                     frozen_min, ctr, vgraph, gmode);
     const int64_t nw = (n >> 5) + 1;
     count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(frozen, nw, &ctr->frozen);
 }
@@ -884,6 +921,12 @@ void launch_round_work(const RoundParams& p, cudaStream_t s) {
     if (p.n <= 0) return;
     const int g = grid_for(p.n, 256) < 1216 ? grid_for(p.n, 256) : 1216;
     round_work_kernel<<<g, 256, 0, s>>>(p.n, p.row, p.frozen, p.small_max, p.hub_threshold, p.ctr);
+}
+
+void launch_clear_bits(uint32_t* words, int64_t a, int64_t b, cudaStream_t s) {
+    if (b <= a) return;
+    const int64_t w0 = a >> 5, w1 = (b - 1) >> 5;
+    clear_bits_kernel<<<grid_for(w1 - w0 + 1, 256), 256, 0, s>>>(words, a, b);
 }
 
 void launch_count_refining(const RoundParams& p, const uint32_t* frozen, Counters* ctr, cudaStream_t s) {
@@ -919,19 +962,19 @@ void launch_bitmap_rank(const uint32_t* bitmap, int64_t nw, uint32_t* scan_tmp, 
 void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
     const int64_t nw = (p.n >> 5) + 1;
     launch_bitmap_rank(p.bitmap, nw, scan_tmp, prefix, p.ctr, s);
-    if (p.minof) {
-        if (p.moved && p.perm) cudaMemsetAsync(p.moved, 0, sizeof(uint32_t) * (size_t)nw, s);
-        if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out, p.moved);
-        if (p.moved) count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(
-            p.moved, nw, &p.ctr->moved);
-        return;
-    }
     if (batched(p)) {
         // prefix[nw] (one past the last word) is not written by the scan: the
         // total sits in the counters; graph_base_kernel reads prefix only for
         // x < n, and takes the total from gbase of the last graph otherwise.
         write_total_kernel<<<1, 1, 0, s>>>(prefix, nw, p.ctr);
         graph_base_kernel<<<(p.n_graphs + 1 + 255) / 256, 256, 0, s>>>(p, prefix);
+    }
+    if (p.minof) {
+        if (p.moved && p.perm) cudaMemsetAsync(p.moved, 0, sizeof(uint32_t) * (size_t)nw, s);
+        if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out, p.moved);
+        if (p.moved) count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(
+            p.moved, nw, &p.ctr->moved);
+        return;
     }
     if (p.n > 0) assign_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out);
 }

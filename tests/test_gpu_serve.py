@@ -39,8 +39,14 @@ def drain(server, tickets, results):
     for _ in range(10000):
         running, waiting = server.step()
         for t in list(tickets):
-            if server.poll(t) == kb.Server.DONE:
+            state = server.poll(t)
+            if state == kb.Server.DONE:
                 results[t] = server.fetch(t)
+                tickets.remove(t)
+            elif state == kb.Server.FAILED:
+                with pytest.raises(kb.KbError) as e:
+                    server.fetch(t)
+                results[t] = e.value.status
                 tickets.remove(t)
         if not tickets and running == 0 and waiting == 0:
             return
@@ -111,14 +117,23 @@ def test_serve_rejects_bad_requests():
         g = graphgen.erdos_renyi(200, 50, 2, 2, 1)
         with pytest.raises(kb.KbError):
             sv.submit_graph(g, 3)
+        g1 = graphgen.erdos_renyi(20, 30, 2, 2, 1)
+        g1.row_offsets = g1.row_offsets.copy()
+        g1.row_offsets[-1] += 1  # the offsets must end at m: checked at submission
+        with pytest.raises(kb.KbError):
+            sv.submit_graph(g1, 3)
+        # a neighbour id out of range is found on the device at admission: that
+        # request fails alone, the one queued behind it completes
         g2 = graphgen.erdos_renyi(20, 30, 2, 2, 1)
         g2.col = g2.col.copy()
         g2.col[3] = 99
-        with pytest.raises(kb.KbError):
-            sv.submit_graph(g2, 3)
+        bad = sv.submit_graph(g2, 3)
         g3 = graphgen.erdos_renyi(20, 30, 2, 2, 1)
         t = sv.submit_graph(g3, 2)
         results = {}
-        drain(sv, [t], results)
+        drain(sv, [bad, t], results)
+        assert results[bad] == 1  # KB_ERR_INVALID_ARG
         L, C, lc = expected(g3, 2, kb.Options())
         assert np.array_equal(results[t][0], L)
+        st = sv.stats()
+        assert st["failed"] == 1 and st["completed"] == 1
