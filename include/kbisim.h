@@ -266,6 +266,11 @@ kb_status kb_summary(kb_context* ctx, const kb_graph* g, int direction, int use_
  *              the change (same n, same options); out: the levels of g
  *   counts, levels_computed  as for kb_refine
  *   work       HOST int64[k+1] or NULL: vertices re-keyed per level (level 0: n)
+ * When the first round's work set would exceed a quarter of the vertices (the
+ * old level-0 blocks holding changed vertices are that large, as label
+ * classes often are), the call runs as kb_refine on g instead, whose frozen
+ * blocks then cost less than re-keying whole blocks; work reports n for every
+ * computed level.  The result is the same either way.
  * KB_ERR_INVALID_ARG when an old level or a changed id lies outside [0, n).
  * Scratch: about 29 B x n of library-owned device memory.  Synchronises. */
 kb_status kb_refine_update(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k,

@@ -828,6 +828,9 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     return KB_OK;
 }
 
+kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
+                      int k, int32_t* levels, int64_t* counts, int* levels_computed);
+
 // Incremental refinement (kb_refine_update): levels holds the levels of the
 // graph before the change (same options); each round re-keys only the work set
 // and keeps the old grouping elsewhere (see kb_update.cu), then renumbers.
@@ -850,10 +853,6 @@ kb_status update_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         return KB_OK;
     }
     cudaStream_t s = ctx->stream;
-    Prepared R;
-    // no locality order: the dirty pass reads neighbour ids, not ranks
-    KB_TRY(prepare(ctx, g, opt, R, -1));
-    kb::RoundParams& p = R.p;
     auto row = [&](int i) { return levels + (size_t)i * (size_t)n; };
 
     // scratch: changed, dirty, moved and work-set bitmaps, block flags, kept
@@ -866,6 +865,42 @@ kb_status update_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         return fail(ctx, KB_ERR_OOM, "cannot allocate a counter");
     }
     char* b = reinterpret_cast<char*>(ctx->upd_buf);
+
+    // The first round re-keys at least every vertex of an old level-0 block
+    // that holds a changed vertex.  When that is over a quarter of the
+    // vertices (level-0 blocks are label classes, often huge), recomputing
+    // with the frozen blocks of a full refinement costs less than re-keying
+    // whole blocks round after round.
+    {
+        KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+        kb::launch_check_ids(n, row(0), ctx->d_ctr, s);
+        uint32_t* scratch = reinterpret_cast<uint32_t*>(b);
+        KB_CUDA(ctx, cudaMemsetAsync(scratch, 0, szb, s));
+        kb::launch_set_bits(n, n_changed, changed, scratch, ctx->d_ctr, s);
+        KB_TRY(read_counters(ctx));
+        if (ctx->h_ctr->err & kb::kErrInvalid)
+            return fail(ctx, KB_ERR_INVALID_ARG, "old levels or changed vertices hold ids outside [0, n)");
+        KB_CUDA(ctx, cudaMemsetAsync(scratch, 0, szb, s));
+        KB_CUDA(ctx, cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), s));
+        kb::launch_touched_size(n, n_changed, changed, row(0), scratch, ctx->d_work, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        unsigned long long w1 = 0;
+        KB_CUDA(ctx, cudaMemcpyAsync(&w1, ctx->d_work, sizeof(w1), cudaMemcpyDeviceToHost, s));
+        KB_CUDA(ctx, cudaStreamSynchronize(s));
+        if ((int64_t)w1 * 4 > n) {
+            KB_TRY(refine_impl(ctx, g, opt, nullptr, 0, k, levels, counts, levels_computed));
+            if (work) {
+                const int lc = levels_computed ? *levels_computed : k;
+                for (int i = 0; i <= k; ++i) work[i] = i <= lc ? n : 0;
+            }
+            return KB_OK;
+        }
+    }
+
+    Prepared R;
+    // no locality order: the dirty pass reads neighbour ids, not ranks
+    KB_TRY(prepare(ctx, g, opt, R, -1));
+    kb::RoundParams& p = R.p;
     uint32_t* changed_bits = reinterpret_cast<uint32_t*>(b);
     uint32_t* dirty = reinterpret_cast<uint32_t*>(b + szb);
     uint32_t* moved = reinterpret_cast<uint32_t*>(b + 2 * szb);
@@ -902,13 +937,18 @@ kb_status update_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     KB_CUDA(ctx, cudaMemsetAsync(wmask, 0xff, szb, s));
     kb::launch_moved(n, wmask, row(0), level0, ranges, moved, s);
     KB_CUDA(ctx, cudaMemcpyAsync(row(0), level0, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    kb::launch_count_bits(moved, nw, &ctx->d_ctr->moved, s);
+    KB_TRY(read_counters(ctx));
     if (work) work[0] = n;
 
     for (int i = 1; i <= k; ++i) {
         Timer T(ctx);
         // dirty = changed | moved | predecessors of moved; W = their previous-level blocks
+        // (the pass over every edge only when some vertex moved)
+        const bool any_moved = ctx->h_ctr->moved > 0;
         kb::launch_or_words(nw, changed_bits, moved, dirty, s);
-        kb::launch_dirty_from_moved(n, R.P.m_proc, p.row, p.col, moved, dirty, s);
+        if (any_moved) kb::launch_dirty_from_moved(n, R.P.m_proc, p.row, p.col, moved, dirty, s);
         KB_CUDA(ctx, cudaMemsetAsync(ctx->d_work, 0, sizeof(unsigned long long), s));
         kb::launch_work_set(n, row(i - 1), dirty, flag, wmask, ctx->d_work, s);
         KB_CUDA(ctx, cudaMemcpyAsync(keep, row(i), sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
@@ -925,6 +965,7 @@ kb_status update_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         kb::launch_renumber(p, R.prefix, R.scan_tmp, row(i), s);
         T.end();
         kb::launch_moved(n, wmask, keep, row(i), ranges, moved, s);
+        kb::launch_count_bits(moved, nw, &ctx->d_ctr->moved, s);
         KB_CUDA(ctx, cudaGetLastError());
         KB_TRY(read_counters(ctx));
         ctx->round_ms.push_back(T.collect());

@@ -328,6 +328,12 @@ void launch_keep_bits(int64_t n, const uint32_t* wmask, const int32_t* old, cons
 void launch_moved(int64_t n, const uint32_t* wmask, const int32_t* old, const int32_t* cur, int32_t* ranges,
                   uint32_t* moved, cudaStream_t s);
 void launch_check_ids(int64_t n, const int32_t* a, Counters* ctr, cudaStream_t s);
+// *out += vertices in the blocks of `level` that hold a vertex of ids
+// (touched: a zeroed bitmap of n bits; ids and level values in [0, n)).
+void launch_touched_size(int64_t n, int64_t count, const int32_t* ids, const int32_t* level, uint32_t* touched,
+                         unsigned long long* out, cudaStream_t s);
+// *out += set bits of words[0..nw) (kb_kernels.cu)
+void launch_count_bits(const uint32_t* words, int64_t nw, int64_t* out, cudaStream_t s);
 void launch_set_bits(int64_t n, int64_t count, const int32_t* ids, uint32_t* bits, Counters* ctr, cudaStream_t s);
 void launch_classify(int64_t n, const int64_t* row, int32_t lo, int32_t hi, int32_t* out, int64_t* n_out,
                      cudaStream_t s);

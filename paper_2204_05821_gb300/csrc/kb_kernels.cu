@@ -923,6 +923,11 @@ void launch_round_work(const RoundParams& p, cudaStream_t s) {
     round_work_kernel<<<g, 256, 0, s>>>(p.n, p.row, p.frozen, p.small_max, p.hub_threshold, p.ctr);
 }
 
+void launch_count_bits(const uint32_t* words, int64_t nw, int64_t* out, cudaStream_t s) {
+    if (nw <= 0) return;
+    count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(words, nw, out);
+}
+
 void launch_clear_bits(uint32_t* words, int64_t a, int64_t b, cudaStream_t s) {
     if (b <= a) return;
     const int64_t w0 = a >> 5, w1 = (b - 1) >> 5;

@@ -160,6 +160,37 @@ __global__ void set_bits_kernel(int64_t n, int64_t count, const int32_t* ids, ui
     }
 }
 
+// Blocks of `level` holding a vertex of ids[0..count) into touched (ids and
+// level values already checked to lie in [0, n)).
+__global__ void touch_blocks_kernel(int64_t count, const int32_t* ids, const int32_t* level, uint32_t* touched) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const int32_t b = level[ids[i]];
+        atomicOr(&touched[b >> 5], 1u << (b & 31));
+    }
+}
+
+// *out += vertices whose block of `level` is touched.
+__global__ void __launch_bounds__(256) touched_size_kernel(int64_t n, const int32_t* level, const uint32_t* touched,
+                                                            unsigned long long* out) {
+    __shared__ unsigned long long s_sum[8];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long c = 0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int32_t b = level[v];
+        c += (touched[b >> 5] >> (b & 31)) & 1u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < 8; ++w) t += s_sum[w];
+        if (t) atomicAdd(out, t);
+    }
+}
+
 }  // namespace
 
 void launch_dirty_from_moved(int64_t n, int64_t m, const int64_t* row, const int32_t* col, const uint32_t* moved,
@@ -213,6 +244,13 @@ void launch_check_ids(int64_t n, const int32_t* a, Counters* ctr, cudaStream_t s
 
 void launch_set_bits(int64_t n, int64_t count, const int32_t* ids, uint32_t* bits, Counters* ctr, cudaStream_t s) {
     if (count > 0) set_bits_kernel<<<grid_of(count, 256), 256, 0, s>>>(n, count, ids, bits, ctr);
+}
+
+void launch_touched_size(int64_t n, int64_t count, const int32_t* ids, const int32_t* level, uint32_t* touched,
+                         unsigned long long* out, cudaStream_t s) {
+    if (count > 0) touch_blocks_kernel<<<grid_of(count, 256), 256, 0, s>>>(count, ids, level, touched);
+    const int g = grid_of(n, 256) < 1216 ? grid_of(n, 256) : 1216;
+    if (n > 0) touched_size_kernel<<<g, 256, 0, s>>>(n, level, touched, out);
 }
 
 }  // namespace kb

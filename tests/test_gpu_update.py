@@ -77,16 +77,36 @@ def power_law():
     return graphgen.make(graphgen.scaled(graphgen.CONFIG_RDF, 0.002, seed=21))
 
 
+def _ran_full(work, n):
+    # the call ran as a full refinement: every computed level reports n
+    return work[0] == n and all(w in (0, n) for w in work[1:])
+
+
 @pytest.mark.parametrize("d", [0, 1, 2])
 def test_small_changes(ctx, er_tiny, power_law, d):
     rng = np.random.Generator(np.random.PCG64(40 + d))
     for g in (er_tiny, power_law):
         g2, ts, td = mutate(g, rng, n_ins=5, n_del=5, n_relabel=3)
         work = check(ctx, g, g2, changed_for(d, ts, td), d, True, True, 8, early_stop=False)
-        # level 1 may re-key whole label classes; later levels only part of the graph
-        assert work[2:].max() < g.n
-        check(ctx, g, g2, changed_for(d, ts, td), d, False, True, 6, early_stop=False)
+        # level 1 re-keys whole label classes: either later levels re-key only
+        # part of the graph, or the first round's work set was so large that
+        # the call ran as a full refinement
+        assert work[2:].max() < g.n or _ran_full(work, g.n)
+        # without vertex labels level 0 is one block: always the full refinement
+        work = check(ctx, g, g2, changed_for(d, ts, td), d, False, True, 6, early_stop=False)
+        assert _ran_full(work, g.n) or len(ts) + len(td) == 0
         check(ctx, g, g2, changed_for(d, ts, td), d, True, False, 6)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_incremental_path_on_fine_level0(ctx, d):
+    # thousands of vertex labels make level-0 blocks small: a few changed
+    # edges touch few of them, so the rounds re-key only work sets
+    g = graphgen.erdos_renyi(20_000, 60_000, 4000, 3, seed=70 + d)
+    rng = np.random.Generator(np.random.PCG64(71 + d))
+    g2, ts, td = mutate(g, rng, n_ins=4, n_del=4, n_relabel=2)
+    work = check(ctx, g, g2, changed_for(d, ts, td), d, True, True, 6, early_stop=False)
+    assert not _ran_full(work, g.n) and 0 < work[1] < g.n // 4
 
 
 def test_no_change_rekeys_nothing(ctx, power_law):
