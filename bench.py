@@ -489,8 +489,11 @@ def run_ours(args, rank, world, local):
 
 
 def bench_batch(ctx, device, steps=3):
-    """The batching workload (4,096 uneven graphs) through kb_refine_batch,
-    against one kb_refine launch per graph on the same GPU."""
+    """The batching workload (4,096 uneven graphs) through kb_refine_batch with
+    the library defaults, then with the autotuner's choice for this batch (the
+    tuning is cached in the context under the batch's size class, and
+    kb_refine_batch picks it up), against one kb_refine launch per graph on
+    the same GPU."""
     import torch
 
     import paper_2204_05821_gb300 as kb
@@ -499,14 +502,24 @@ def bench_batch(ctx, device, steps=3):
     dg = kb.DeviceGraph(union["row_offsets"], union["col"], union["elabel"], union["vlabel"])
     opts = kb.Options()
     G = len(ks)
-    ctx.refine_batch(dg, voff, ks, opts)  # warm
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        _, counts, lc = ctx.refine_batch(dg, voff, ks, opts)
-    torch.cuda.synchronize()
-    tb = (time.perf_counter() - t0) / steps
-    # plain path: one kb_refine per graph
+
+    def time_batch():
+        ctx.refine_batch(dg, voff, ks, opts)  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            _, counts, lc = ctx.refine_batch(dg, voff, ks, opts)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / steps, lc
+
+    ctx.clear_tuning()
+    td, lc = time_batch()
+    t_tune = time.perf_counter()
+    tuning = ctx.autotune(dg, opts, vertex_offsets=voff, ks=ks)
+    t_tune = time.perf_counter() - t_tune
+    tb, lc = time_batch()
+    # plain path: one kb_refine per graph (single-graph calls keep the defaults:
+    # the batch's tuning is cached under a batch size class)
     row, col, el, vl = union["row_offsets"], union["col"], union["elabel"], union["vlabel"]
     singles = []
     for j in range(G):
@@ -524,10 +537,15 @@ def bench_batch(ctx, device, steps=3):
     tp = time.perf_counter() - t0
     edge_rounds = float(np.sum(lc.astype(np.float64) * np.diff([int(row[int(x)].item()) for x in voff])))
     del singles
+    ctx.clear_tuning()
     return {"workload": "4096 ER graphs, edges lognormal(median 5e4, sigma 1.25) in [1e3, 2e6], n=m/5, "
                         "16 vertex / 8 edge labels uniform, k uniform 1..10, seed 3",
             "graphs": G, "edges": int(union["m"]), "vertices": int(union["n"]),
             "graphs_per_s": G / tb, "ms_per_batch": 1000 * tb, "edge_rounds_per_s": edge_rounds / tb,
+            "default_graphs_per_s": G / td, "default_ms_per_batch": 1000 * td,
+            "tuned": {k: tuning[k] for k in ("load_factor", "hub_threshold", "small_task_vertices",
+                                             "hub_chunk_edges", "medium_split", "small_max_degree")},
+            "autotune_s": t_tune, "autotune_ms_tuned": tuning["ms"], "autotune_ms_default": tuning["default_ms"],
             "plain_graphs_per_s": G / tp, "plain_ms": 1000 * tp, "speedup_vs_plain": tp / tb}
 
 

@@ -92,6 +92,18 @@ typedef struct {
  *   validate           1: check offsets and ids on the device before refining
  *   small_task_vertices vertices each warp of the small-vertex kernel takes per task
  *                      (tile size); 0 -> default 128, else 32..65536
+ *   hub_chunk_edges    edges of one hub that one CTA dedups in shared memory before
+ *                      merging into the hub's global set (tile size of the hub
+ *                      path); 0 -> default 512, else 256, 512 or 1024
+ *   medium_split       medium vertices (above small_max_degree edges, at most
+ *                      hub_threshold) with at most this many edges take a warp each,
+ *                      larger ones a CTA each; 0 -> default 256, else 1..256
+ *   small_max_degree   vertices with at most this many edges take the small-vertex
+ *                      (warp-per-task) kernel; 0 -> default 32, else 1..32 (and at
+ *                      most hub_threshold)
+ *                      The five tuning fields above, load_factor and hub_threshold,
+ *                      when 0, take the values kb_autotune cached for the call's size
+ *                      class, else the defaults.  None of them changes any result.
  *   reorder            internal locality order for the per-edge gather of neighbour
  *                      blocks: vertices are ranked by how often they are gathered
  *                      (sampled in-degree of the processed direction) and the
@@ -145,7 +157,10 @@ typedef struct {
     int32_t reorder;
     int32_t subject;
     int32_t rekey_all;
-    int32_t reserved[4];
+    int32_t hub_chunk_edges;
+    int32_t medium_split;
+    int32_t small_max_degree;
+    int32_t reserved[1];
 } kb_options;
 
 enum { KB_SUBJECT_PREVIOUS = 0, KB_SUBJECT_ALL = 1, KB_SUBJECT_LABEL = 2, KB_SUBJECT_ID = 3 };
@@ -340,11 +355,42 @@ kb_status kb_refine_batch(kb_context* ctx, const kb_graph* union_graph,
                           const int32_t* k_per_graph, const kb_options* opt, int32_t* levels,
                           int64_t* counts, int32_t* levels_computed);
 
-/* Autotuner: time refinement rounds of `g` for a grid of load factors and hub
- * thresholds, keep the fastest in the context (used when the options leave
- * those fields 0) and report it.  Synchronises. */
-kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt, int rounds,
-                      float* best_load_factor, int32_t* best_hub_threshold, float* best_ms);
+/* Autotuner.  Chooses the block-table load factor, the degree-class bounds
+ * (hub_threshold, small_max_degree, medium_split) and the tile sizes
+ * (small_task_vertices, hub_chunk_edges) by timing the call it is given:
+ *   graph_vertex_offsets == NULL: kb_refine of g with `rounds` rounds;
+ *   else (HOST int64[G+1], as kb_refine_batch): kb_refine_batch of the union g,
+ *        every graph with k = rounds (k_per_graph NULL) or k_per_graph[j].
+ * Early stop is off while timing.  A coordinate search starts from the
+ * options' values (defaults where 0), tries every value of one field at a time
+ * and keeps a value only when it is faster by more than 2%:
+ *   load_factor {0.35, 0.5, 0.7}, hub_threshold {256, 512, 1024},
+ *   small_max_degree {16, 24, 32}, medium_split {64, 128, 256},
+ *   small_task_vertices {64, 128, 256, 512}, hub_chunk_edges {256, 512, 1024};
+ * each setting is timed (CUDA events, one warm-up run) as the best of two
+ * runs.  The choice is cached in the context under the call's size class
+ * (single graph or batch, and log2 of the processed edges per graph); later
+ * kb_refine, kb_refine_batch and kb_workspace_size calls whose options leave a
+ * field 0 take it from the cached entry of their own class, or of the nearest
+ * class of the same kind within a factor of 8.  `out` (HOST, may be NULL)
+ * receives the choice, its time and the time with library defaults.
+ * Results never depend on these fields.  Synchronises. */
+typedef struct {
+    float load_factor;
+    int32_t hub_threshold;
+    int32_t small_task_vertices;
+    int32_t hub_chunk_edges;
+    int32_t medium_split;
+    int32_t small_max_degree;
+    float ms;           /* time of the timed call with the chosen values */
+    float default_ms;   /* the same with every tuning field at its default */
+    int32_t size_class; /* key of the cached entry */
+    int32_t reserved[3];
+} kb_tuning;
+kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const int64_t* graph_vertex_offsets, int64_t G,
+                      const int32_t* k_per_graph, const kb_options* opt, int rounds, kb_tuning* out);
+/* Forget every cached tuning of the context. */
+kb_status kb_clear_tuning(kb_context* ctx);
 
 /* ---- Serving: continuous batching of summarisation requests ----------------
  * A server keeps every admitted request's graph and partitions on the device
@@ -428,8 +474,9 @@ kb_status kb_server_get_stats(kb_server* server, kb_server_stats* stats);
  *   g        DEVICE CSR as for kb_refine, with n <= KB_NOALLOC_MAX_VERTICES and
  *            no vertex with more than hub_threshold (default 1024) edges
  *   opt      direction must be KB_DIR_OUT; use_edge_labels, hash_mode,
- *            hub_threshold, small_task_vertices (0 or 32..65536) and validate
- *            are honoured
+ *            hub_threshold, small_task_vertices (0 or 32..65536),
+ *            medium_split (0..256), small_max_degree (0..32) and validate are
+ *            honoured (0 = library default; cached tunings are not consulted)
  *   prev     DEVICE int32[n], canonical ids of level i-1, each in [0, n)
  *   out      DEVICE int32[n], receives the canonical ids of level i
  *   count    HOST, receives the number of blocks of level i
@@ -443,7 +490,7 @@ kb_status kb_server_get_stats(kb_server* server, kb_server_stats* stats);
  * several streams or threads -- race; the caller must serialise them.
  * Errors: KB_ERR_INVALID_ARG for n above the limit, another direction, a
  * vertex whose degree lies outside [0, hub threshold], an id of prev outside
- * [0, n), small_task_vertices out of range or (with validate) malformed CSR;
+ * [0, n), a tuning field out of range or (with validate) malformed CSR;
  * `out` is then left untouched.  KB_ERR_CUDA when a runtime call fails. */
 #define KB_NOALLOC_MAX_VERTICES 1048576
 kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, const kb_options* opt,

@@ -52,6 +52,9 @@ class Options:
     reorder: int = 0  # 0 automatic, 1 off, 2 on
     subject: int = 0  # SUBJECT_PREVIOUS, SUBJECT_ALL, SUBJECT_LABEL or SUBJECT_ID (generic CSE rounds)
     rekey_all: bool = False  # True: re-key every vertex every round (no skipping of frozen blocks)
+    hub_chunk_edges: int = 0  # 0 or 256, 512, 1024
+    medium_split: int = 0  # 0 or 1..256
+    small_max_degree: int = 0  # 0 or 1..32
 
     @classmethod
     def schaetzle(cls, **kw) -> "Options":
@@ -77,6 +80,9 @@ class Options:
         o.reorder = int(self.reorder)
         o.subject = int(self.subject)
         o.rekey_all = int(bool(self.rekey_all))
+        o.hub_chunk_edges = int(self.hub_chunk_edges)
+        o.medium_split = int(self.medium_split)
+        o.small_max_degree = int(self.small_max_degree)
         return o
 
 
@@ -341,15 +347,34 @@ class Context:
                                               _np_ptr(lc)))
         return levels, counts, lc
 
-    def autotune(self, graph: DeviceGraph, options: Options = None, rounds: int = 2):
+    def autotune(self, graph: DeviceGraph, options: Options = None, rounds: int = 2, vertex_offsets=None,
+                 ks=None) -> dict:
+        """``kb_autotune``: time ``rounds`` rounds of ``graph`` (or, with
+        ``vertex_offsets``, kb_refine_batch of the union with k = ``rounds`` or
+        ``ks`` per graph) over the tuning fields, cache the choice in this
+        context for the call's size class and return it as a dict (the
+        kb_tuning fields: the chosen values, ``ms`` and ``default_ms``)."""
         options = options or Options()
-        lf = ctypes.c_float(0)
-        thr = ctypes.c_int32(0)
-        ms = ctypes.c_float(0)
         g, o = graph.to_c(), options.to_c()
-        self._check(self._lib.kb_autotune(self._h, ctypes.byref(g), ctypes.byref(o), int(rounds), ctypes.byref(lf),
-                                          ctypes.byref(thr), ctypes.byref(ms)))
-        return float(lf.value), int(thr.value), float(ms.value)
+        t = _capi.KbTuning()
+        voff_p, G, ks_p = None, 0, None
+        if vertex_offsets is not None:
+            voff = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+            G = voff.shape[0] - 1
+            voff_p = _np_ptr(voff)
+            if ks is not None:
+                ks = np.ascontiguousarray(ks, dtype=np.int32)
+                if ks.shape[0] != G:
+                    raise ValueError("ks needs one entry per graph")
+                ks_p = _np_ptr(ks)
+        self._check(self._lib.kb_autotune(self._h, ctypes.byref(g), voff_p, G, ks_p, ctypes.byref(o), int(rounds),
+                                          ctypes.byref(t)))
+        return {name: (float(getattr(t, name)) if name in ("load_factor", "ms", "default_ms") else
+                       int(getattr(t, name))) for name, _ in _capi.KbTuning._fields_ if name != "reserved"}
+
+    def clear_tuning(self):
+        """Forget every tuning ``autotune`` cached in this context."""
+        self._check(self._lib.kb_clear_tuning(self._h))
 
     # -- timing
     def set_timing(self, enable=True):

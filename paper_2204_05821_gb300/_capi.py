@@ -51,7 +51,25 @@ class KbOptions(ctypes.Structure):
         ("reorder", ctypes.c_int32),
         ("subject", ctypes.c_int32),
         ("rekey_all", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("hub_chunk_edges", ctypes.c_int32),
+        ("medium_split", ctypes.c_int32),
+        ("small_max_degree", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
+    ]
+
+
+class KbTuning(ctypes.Structure):
+    _fields_ = [
+        ("load_factor", ctypes.c_float),
+        ("hub_threshold", ctypes.c_int32),
+        ("small_task_vertices", ctypes.c_int32),
+        ("hub_chunk_edges", ctypes.c_int32),
+        ("medium_split", ctypes.c_int32),
+        ("small_max_degree", ctypes.c_int32),
+        ("ms", ctypes.c_float),
+        ("default_ms", ctypes.c_float),
+        ("size_class", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -112,7 +130,9 @@ SIGNATURES = [
     ("kb_get_timing", _I, [_P, _P, _I, _P, _P, _P]),
     ("kb_get_round_work", _I, [_P, _P, _P, _I, _P]),
     ("kb_refine_batch", _I, [_P, ctypes.POINTER(KbGraph), _P, _I64, _P, ctypes.POINTER(KbOptions), _P, _P, _P]),
-    ("kb_autotune", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
+    ("kb_autotune", _I, [_P, ctypes.POINTER(KbGraph), _P, _I64, _P, ctypes.POINTER(KbOptions), _I,
+                         ctypes.POINTER(KbTuning)]),
+    ("kb_clear_tuning", _I, [_P]),
     ("kb_server_config_default", KbServerConfig, []),
     ("kb_server_create", _I, [ctypes.POINTER(_P), _I, _P, ctypes.POINTER(KbServerConfig)]),
     ("kb_server_destroy", _I, [_P]),

@@ -42,10 +42,10 @@ struct kb_context {
     // host-buffer refinement staging (library-owned)
     void* stage = nullptr;
     size_t stage_bytes = 0;
-    // autotuned defaults
-    float tuned_load_factor = 0.f;
-    int32_t tuned_hub_threshold = 0;
-    int32_t tuned_warp_verts = 0;
+    // autotuned values per size class (kb_autotune); plan_graphs is the graph
+    // count of the batched call being planned
+    std::map<int32_t, kb_tuning> tuned;
+    int64_t plan_graphs = 1;
     // batched refinement
     void* batch_ws = nullptr;
     size_t batch_ws_bytes = 0;
@@ -119,6 +119,11 @@ struct Plan {
     int dir = 0;
     bool labels = false;
     int thr = kb::kDefaultHubThreshold;
+    int hub_chunk = kb::kDefaultHubChunk;
+    int med_split = kb::kDefaultMedSplit;
+    int small_max = kb::kSmallDegree;
+    int warp_verts = kb::kDefaultWarpVerts;
+    int32_t size_class = 0;  // key of the tuning cache
     uint64_t cap = 0;
     bool reorder = false;  // locality order of the gather (RoundParams::perm)
     int subject = 0;       // kb_options::subject (generic CSE rounds when > 0)
@@ -212,6 +217,13 @@ kb_status check_graph(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     if (opt->subject < 0 || opt->subject > 3) return fail(ctx, KB_ERR_INVALID_ARG, "subject must be 0..3");
     if (opt->small_task_vertices != 0 && (opt->small_task_vertices < 32 || opt->small_task_vertices > 65536))
         return fail(ctx, KB_ERR_INVALID_ARG, "small_task_vertices must be 0 or in [32, 65536]");
+    if (opt->hub_chunk_edges != 0 && opt->hub_chunk_edges != 256 && opt->hub_chunk_edges != 512 &&
+        opt->hub_chunk_edges != 1024)
+        return fail(ctx, KB_ERR_INVALID_ARG, "hub_chunk_edges must be 0, 256, 512 or 1024");
+    if (opt->medium_split < 0 || opt->medium_split > kb::kMaxMedSplit)
+        return fail(ctx, KB_ERR_INVALID_ARG, "medium_split must be in [0, %d]", kb::kMaxMedSplit);
+    if (opt->small_max_degree < 0 || opt->small_max_degree > kb::kSmallDegree)
+        return fail(ctx, KB_ERR_INVALID_ARG, "small_max_degree must be in [0, %d]", kb::kSmallDegree);
     if (opt->direction == KB_DIR_BOTH && g->m > (int64_t)1 << 62)
         return fail(ctx, KB_ERR_INVALID_ARG, "too many edges");
     return KB_OK;
@@ -298,13 +310,39 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
     P.set_off.resize((size_t)H + 1);
     for (int32_t i = 0; i < H; ++i) {
         const int64_t d = deg[(size_t)i];
-        P.chunk_off[(size_t)i + 1] = P.chunk_off[(size_t)i] + (d + kb::kHubChunk - 1) / kb::kHubChunk;
+        P.chunk_off[(size_t)i + 1] = P.chunk_off[(size_t)i] + (d + P.hub_chunk - 1) / P.hub_chunk;
         P.set_off[(size_t)i + 1] = P.set_off[(size_t)i] + kb::hub_set_capacity(d);
     }
     P.chunk_hub.resize((size_t)P.chunk_off[(size_t)H]);
     for (int32_t i = 0; i < H; ++i)
         for (int64_t c = P.chunk_off[(size_t)i]; c < P.chunk_off[(size_t)i + 1]; ++c) P.chunk_hub[(size_t)c] = i;
     return KB_OK;
+}
+
+// Size class of a call, the key of the tuning cache: single graphs by
+// floor(log2) of their processed edges, batches (64 + ...) by floor(log2) of
+// the processed edges per graph.
+int32_t size_class(int64_t m_proc, int64_t graphs, bool batch) {
+    const int64_t per = std::max<int64_t>(1, m_proc / std::max<int64_t>(graphs, 1));
+    int32_t c = 0;
+    while ((per >> (c + 1)) > 0) ++c;
+    return batch ? 64 + c : c;
+}
+
+// The cached tuning of class c, else of the nearest class of the same kind
+// at most 3 classes (a factor of 8 in edges) away, else nullptr.
+const kb_tuning* tuned_for(const kb_context* ctx, int32_t c) {
+    const kb_tuning* best = nullptr;
+    int32_t dist = 4;
+    for (const auto& kv : ctx->tuned) {
+        if ((kv.first >= 64) != (c >= 64)) continue;
+        const int32_t d = std::abs(kv.first - c);
+        if (d < dist) {
+            dist = d;
+            best = &kv.second;
+        }
+    }
+    return best;
 }
 
 // `rounds`: refinement rounds the call runs (decides the automatic locality
@@ -323,9 +361,17 @@ kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, P
     // hold the own previous block
     P.freeze = (rounds >= 0 || multi) && P.subject == KB_SUBJECT_PREVIOUS && opt->rekey_all == 0;
     P.labels = opt->use_edge_labels && g->edge_labels != nullptr;
-    int thr = opt->hub_threshold ? opt->hub_threshold : ctx->tuned_hub_threshold;
-    P.thr = thr > 0 ? thr : kb::kDefaultHubThreshold;
-    float lf = opt->load_factor > 0.f ? opt->load_factor : ctx->tuned_load_factor;
+    // tuning fields: the options' value, else the cached tuning of the call's
+    // size class, else the library default
+    P.size_class = size_class(P.m_proc, multi ? ctx->plan_graphs : 1, multi);
+    const kb_tuning* T = tuned_for(ctx, P.size_class);
+    auto pick = [](int32_t given, int32_t cached, int32_t dflt) { return given ? given : (cached ? cached : dflt); };
+    P.thr = pick(opt->hub_threshold, T ? T->hub_threshold : 0, kb::kDefaultHubThreshold);
+    P.hub_chunk = pick(opt->hub_chunk_edges, T ? T->hub_chunk_edges : 0, kb::kDefaultHubChunk);
+    P.med_split = pick(opt->medium_split, T ? T->medium_split : 0, kb::kDefaultMedSplit);
+    P.small_max = std::min(pick(opt->small_max_degree, T ? T->small_max_degree : 0, kb::kSmallDegree), P.thr);
+    P.warp_verts = pick(opt->small_task_vertices, T ? T->small_task_vertices : 0, kb::kDefaultWarpVerts);
+    float lf = opt->load_factor > 0.f ? opt->load_factor : (T ? T->load_factor : 0.f);
     if (!(lf > 0.f)) lf = 0.5f;
     P.cap = next_pow2((uint64_t)((double)std::max<int64_t>(P.n, 1) / (double)lf) + 1);
     if (P.cap < 1024) P.cap = 1024;
@@ -509,8 +555,10 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
         p.lab = P.labels ? g->edge_labels : nullptr;
     }
     p.hub_threshold = P.thr;
-    p.small_max = std::min(kb::kSmallDegree, P.thr);
-    p.warp_verts = opt->small_task_vertices ? opt->small_task_vertices : ctx->tuned_warp_verts;
+    p.small_max = P.small_max;
+    p.warp_verts = P.warp_verts;
+    p.hub_chunk = P.hub_chunk;
+    p.med_split = P.med_split;
     p.hash_mode = opt->hash_mode;
     p.table = R.ext_table ? R.ext_table : reinterpret_cast<uint64_t*>(ws + P.o_table);
     p.mask = (R.ext_table ? R.ext_cap : P.cap) - 1;
@@ -543,7 +591,7 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
                                      cudaMemcpyHostToDevice, s));
         KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunkhub, P.chunk_hub.data(), sizeof(int32_t) * P.chunk_hub.size(),
                                      cudaMemcpyHostToDevice, s));
-        kb::launch_chunk_ext((int64_t)P.chunk_hub.size(), p.chunk_hub, p.hub_v, p.hub_chunk_off, p.row,
+        kb::launch_chunk_ext((int64_t)P.chunk_hub.size(), p.chunk_hub, p.hub_v, p.hub_chunk_off, p.row, P.hub_chunk,
                              reinterpret_cast<uint64_t*>(ws + P.o_chunkext), s);
         KB_CUDA(ctx, cudaGetLastError());
     }
@@ -1154,7 +1202,10 @@ kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, 
     reset_timing(ctx);
     cudaStream_t s = ctx->stream;
     Prepared R;
-    KB_TRY(prepare(ctx, g, opt, R, -1, true));
+    ctx->plan_graphs = G;
+    const kb_status pst = prepare(ctx, g, opt, R, -1, true);
+    ctx->plan_graphs = 1;
+    KB_TRY(pst);
     kb::RoundParams& p = R.p;
 
     // batch scratch
@@ -2085,58 +2136,127 @@ kb_status kb_refine_batch(kb_context* ctx, const kb_graph* union_graph, const in
     return batch_impl(ctx, union_graph, graph_vertex_offsets, G, k_per_graph, opt, levels, counts, levels_computed);
 }
 
-kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const kb_options* opt, int rounds, float* best_lf,
-                      int32_t* best_thr, float* best_ms) {
+kb_status kb_autotune(kb_context* ctx, const kb_graph* g, const int64_t* voff, int64_t G, const int32_t* k_per_graph,
+                      const kb_options* opt, int rounds, kb_tuning* out) {
     if (!ctx) return KB_ERR_INVALID_ARG;
-    if (rounds < 1) return fail(ctx, KB_ERR_INVALID_ARG, "rounds must be >= 1");
-    KB_TRY(check_graph(ctx, g, opt, rounds));
+    if (!g || !opt) return fail(ctx, KB_ERR_INVALID_ARG, "graph and options must not be NULL");
+    const bool batch = voff != nullptr;
+    if (batch && (G < 1 || G > (int64_t)1 << 30)) return fail(ctx, KB_ERR_INVALID_ARG, "bad graph count");
+    std::vector<int32_t> ks;
+    int kmax = rounds;
+    if (batch) {
+        ks.assign((size_t)G, rounds);
+        if (k_per_graph) {
+            kmax = 0;
+            for (int64_t j = 0; j < G; ++j) {
+                ks[(size_t)j] = k_per_graph[j];
+                kmax = std::max(kmax, (int)k_per_graph[j]);
+            }
+        }
+    }
+    if (kmax < 1) return fail(ctx, KB_ERR_INVALID_ARG, "the timed call must run at least one round");
+    KB_TRY(check_graph(ctx, g, opt, kmax));
     KB_CUDA(ctx, cudaSetDevice(ctx->device));
     const int64_t n = g->n;
     KB_TRY(ensure_buffer(ctx, &ctx->tune_buf, &ctx->tune_buf_bytes,
-                         std::max<size_t>(256, sizeof(int32_t) * (size_t)n * (size_t)(rounds + 1))));
+                         std::max<size_t>(256, sizeof(int32_t) * (size_t)n * (size_t)(kmax + 1))));
     int32_t* lev = reinterpret_cast<int32_t*>(ctx->tune_buf);
-    std::vector<int64_t> counts((size_t)rounds + 1);
+    std::vector<int64_t> counts((size_t)(batch ? G : 1) * (size_t)(kmax + 1));
+    const int64_t m_proc = opt->direction == KB_DIR_BOTH ? 2 * g->m : g->m;
+    const int32_t cls = size_class(m_proc, batch ? G : 1, batch);
+
+    // every tuning field explicit, so no cached tuning is consulted while timing
+    kb_options base = *opt;
+    base.early_stop = 0;
+    base.validate = 0;
+    kb_options dflt = base;
+    dflt.load_factor = 0.5f;
+    dflt.hub_threshold = kb::kDefaultHubThreshold;
+    dflt.small_task_vertices = kb::kDefaultWarpVerts;
+    dflt.hub_chunk_edges = kb::kDefaultHubChunk;
+    dflt.medium_split = kb::kDefaultMedSplit;
+    dflt.small_max_degree = kb::kSmallDegree;
+    kb_options start = dflt;
+    if (base.load_factor > 0.f) start.load_factor = base.load_factor;
+    if (base.hub_threshold) start.hub_threshold = base.hub_threshold;
+    if (base.small_task_vertices) start.small_task_vertices = base.small_task_vertices;
+    if (base.hub_chunk_edges) start.hub_chunk_edges = base.hub_chunk_edges;
+    if (base.medium_split) start.medium_split = base.medium_split;
+    if (base.small_max_degree) start.small_max_degree = base.small_max_degree;
+
+    // one warm-up run, then the best of two timed runs
+    auto timed = [&](const kb_options& t, float* best_ms) -> kb_status {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEvent_t e0 = ctx->ev[20], e1 = ctx->ev[21];
+            KB_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+            if (batch)
+                KB_TRY(batch_impl(ctx, g, voff, G, ks.data(), &t, lev, counts.data(), nullptr));
+            else
+                KB_TRY(refine_impl(ctx, g, &t, nullptr, 0, rounds, lev, counts.data(), nullptr));
+            KB_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+            KB_CUDA(ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            KB_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) best = std::min(best, ms);
+        }
+        *best_ms = best;
+        return KB_OK;
+    };
+    float default_ms = 0.f;
+    KB_TRY(timed(dflt, &default_ms));
+    float best = default_ms;
+    kb_options win = start;
+    if (std::memcmp(&start, &dflt, sizeof(kb_options)) != 0) KB_TRY(timed(start, &best));
+
+    // coordinate search, one field at a time
     const float lfs[] = {0.35f, 0.5f, 0.7f};
     const int32_t thrs[] = {256, 512, 1024};
-    const int32_t wvs[] = {64, 128, 256};
-    float best = 1e30f;
-    kb_options o = *opt;
-    o.early_stop = 0;
-    o.validate = 0;
-    if (!(o.load_factor > 0.f)) o.load_factor = 0.5f;
-    if (o.hub_threshold == 0) o.hub_threshold = kb::kDefaultHubThreshold;
-    if (o.small_task_vertices == 0) o.small_task_vertices = kb::kDefaultWarpVerts;
-    kb_options win = o;
-    // coordinate search: load factor, then hub threshold, then warp task size
-    for (int axis = 0; axis < 3; ++axis) {
-        for (int c = 0; c < 3; ++c) {
-            kb_options t = win;
-            if (axis == 0) t.load_factor = lfs[c];
-            if (axis == 1) t.hub_threshold = thrs[c];
-            if (axis == 2) t.small_task_vertices = wvs[c];
-            float total = 0.f;
-            for (int rep = 0; rep < 2; ++rep) {
-                cudaEvent_t e0 = ctx->ev[20], e1 = ctx->ev[21];
-                cudaEventRecord(e0, ctx->stream);
-                KB_TRY(refine_impl(ctx, g, &t, nullptr, 0, rounds, lev, counts.data(), nullptr));
-                cudaEventRecord(e1, ctx->stream);
-                KB_CUDA(ctx, cudaEventSynchronize(e1));
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep == 1) total = ms;  // the first run warms caches and scratch
+    const int32_t smaxs[] = {16, 24, 32};
+    const int32_t splits[] = {64, 128, 256};
+    const int32_t wvs[] = {64, 128, 256, 512};
+    const int32_t chunks[] = {256, 512, 1024};
+    const int n_values[6] = {3, 3, 3, 3, 4, 3};
+    for (int axis = 0; axis < 6; ++axis) {
+        kb_options center = win;
+        for (int c = 0; c < n_values[axis]; ++c) {
+            kb_options t = center;
+            switch (axis) {
+                case 0: t.load_factor = lfs[c]; break;
+                case 1: t.hub_threshold = thrs[c]; break;
+                case 2: t.small_max_degree = smaxs[c]; break;
+                case 3: t.medium_split = splits[c]; break;
+                case 4: t.small_task_vertices = wvs[c]; break;
+                default: t.hub_chunk_edges = chunks[c]; break;
             }
-            if (total < best) {
-                best = total;
+            if (std::memcmp(&t, &center, sizeof(kb_options)) == 0) continue;  // timed already
+            float ms = 0.f;
+            KB_TRY(timed(t, &ms));
+            if (ms < 0.98f * best) {
+                best = ms;
                 win = t;
             }
         }
     }
-    ctx->tuned_load_factor = win.load_factor;
-    ctx->tuned_hub_threshold = win.hub_threshold;
-    ctx->tuned_warp_verts = win.small_task_vertices;
-    if (best_lf) *best_lf = win.load_factor;
-    if (best_thr) *best_thr = win.hub_threshold;
-    if (best_ms) *best_ms = best;
+    kb_tuning T;
+    std::memset(&T, 0, sizeof(T));
+    T.load_factor = win.load_factor;
+    T.hub_threshold = win.hub_threshold;
+    T.small_task_vertices = win.small_task_vertices;
+    T.hub_chunk_edges = win.hub_chunk_edges;
+    T.medium_split = win.medium_split;
+    T.small_max_degree = win.small_max_degree;
+    T.ms = best;
+    T.default_ms = default_ms;
+    T.size_class = cls;
+    ctx->tuned[cls] = T;
+    if (out) *out = T;
+    return KB_OK;
+}
+
+kb_status kb_clear_tuning(kb_context* ctx) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    ctx->tuned.clear();
     return KB_OK;
 }
 

@@ -12,20 +12,19 @@ namespace kb {
 
 // ---------------------------------------------------------------- geometry
 // Vertices with more than hub_threshold edges (at most kMaxHubThreshold) are
-// hubs, split into chunks of kHubChunk edges; medium vertices keep their pairs
-// in one shared-memory set of 2 x kMaxHubThreshold entries.
+// hubs, split into chunks of RoundParams::hub_chunk edges (256, 512 or 1024);
+// medium vertices keep their pairs in one shared-memory set of 2 x
+// kMaxHubThreshold entries.
 constexpr int kMaxHubThreshold = 1024;
 constexpr int kDefaultHubThreshold = kMaxHubThreshold;
-#ifndef KB_HUB_CHUNK
-#define KB_HUB_CHUNK 512
-#endif
-#ifndef KB_HUB_THREADS
-#define KB_HUB_THREADS 128
-#endif
-constexpr int kHubChunk = KB_HUB_CHUNK;      // edges per hub-chunk CTA
-constexpr int kHubThreads = KB_HUB_THREADS;  // threads of a hub-chunk CTA
-constexpr int kHubSetCap = 2 * kHubChunk;    // its shared dedup set
-static_assert(kHubChunk < 65536, "a chunk's edge count is packed in 16 bits");
+constexpr int kDefaultHubChunk = 512;   // edges per hub-chunk CTA
+constexpr int kMaxHubChunk = 1024;
+constexpr int kHubThreads = 128;        // threads of a hub-chunk CTA
+static_assert(kMaxHubChunk < 65536, "a chunk's edge count is packed in 16 bits");
+// Medium vertices up to this degree take a warp each, larger ones a CTA
+// (RoundParams::med_split, at most kMaxMedSplit).
+constexpr int kMaxMedSplit = 256;
+constexpr int kDefaultMedSplit = kMaxMedSplit;
 constexpr int kHubFinalThreads = 256;
 constexpr int kProbeLimit = 1 << 22;  // bound on block-table probes per vertex
 constexpr int kSmallDegree = 32;      // vertices with at most this many edges take the warp kernel
@@ -98,8 +97,10 @@ struct RoundParams {
     uint32_t* minof;
     uint32_t* moved;
     int32_t hub_threshold;
-    int32_t small_max;    // min(kSmallDegree, hub_threshold)
+    int32_t small_max;    // largest degree of the small-vertex kernel (<= kSmallDegree, <= hub_threshold)
     int32_t warp_verts;   // vertices per warp task of the small-vertex kernel
+    int32_t hub_chunk;    // edges per hub-chunk CTA: 256, 512 or 1024
+    int32_t med_split;    // medium vertices up to this degree take a warp, larger a CTA (1..kMaxMedSplit)
     int32_t hash_mode;
     uint32_t epoch;       // 1..255, tags this round's table entries
     uint64_t* table;      // [mask+1] block table
@@ -285,7 +286,7 @@ void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v
 // Append the vertices with lo < degree <= hi to out (order within a warp
 // preserved); count in *n_out.
 void launch_chunk_ext(int64_t chunks, const int32_t* chunk_hub, const int32_t* hub_v, const int64_t* chunk_off,
-                      const int64_t* row, uint64_t* out, cudaStream_t s);
+                      const int64_t* row, int32_t chunk, uint64_t* out, cudaStream_t s);
 void launch_locality_order(int64_t n, int64_t m, const int32_t* col, uint32_t* cnt, unsigned long long* hist,
                            int32_t* perm, cudaStream_t s);
 void launch_remap_cols(int64_t m, const int32_t* col, const int32_t* perm, int32_t* out, cudaStream_t s);

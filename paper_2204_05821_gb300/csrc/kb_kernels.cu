@@ -24,13 +24,15 @@ namespace kb {
 namespace {
 
 // ----------------------------------------------------------------------------
-// Hub chunks: kHubChunk edges of one hub per CTA.  Chunk-local dedup in shared
+// Hub chunks: kChunk edges of one hub per CTA.  Chunk-local dedup in shared
 // memory, then the chunk's distinct pairs go into the hub's global set; pairs
 // new to the hub are appended to its list and summed into its hash.
 // ----------------------------------------------------------------------------
+template <int kChunk>
 __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParams p) {
-    __shared__ uint64_t s_pair[kHubChunk];
-    __shared__ uint64_t s_new[kHubChunk];
+    constexpr int kHubSetCap = 2 * kChunk;  // the chunk's shared dedup set
+    __shared__ uint64_t s_pair[kChunk];
+    __shared__ uint64_t s_new[kChunk];
     __shared__ uint32_t s_set[kHubSetCap];
     __shared__ int s_nuniq, s_nnew;
     __shared__ uint64_t s_accsum;
@@ -109,10 +111,10 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
     const uint64_t gcap = (uint64_t)(p.hub_set_off[h + 1] - p.hub_set_off[h]);
     uint64_t lacc = 0;
     uint32_t lnew = 0;
-    // Up to kHubChunk / kHubThreads pairs per thread: the first probe of every
+    // Up to kChunk / kHubThreads pairs per thread: the first probe of every
     // pair is a CAS issued before waiting on any, then the rare collisions are
     // finished one by one.
-    constexpr int kPer = kHubChunk / kHubThreads;
+    constexpr int kPer = kChunk / kHubThreads;
     uint64_t prs[kPer], slots[kPer], olds[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
@@ -946,7 +948,12 @@ void launch_edgeless_bits(int64_t n, const int64_t* row, uint32_t* bits, cudaStr
 
 void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s) {
     if (p.n_hubs <= 0 || total_chunks <= 0) return;
-    hub_chunk_kernel<<<(unsigned)total_chunks, kHubThreads, 0, s>>>(p);
+    if (p.hub_chunk == 256)
+        hub_chunk_kernel<256><<<(unsigned)total_chunks, kHubThreads, 0, s>>>(p);
+    else if (p.hub_chunk == 1024)
+        hub_chunk_kernel<1024><<<(unsigned)total_chunks, kHubThreads, 0, s>>>(p);
+    else
+        hub_chunk_kernel<kDefaultHubChunk><<<(unsigned)total_chunks, kHubThreads, 0, s>>>(p);
 }
 
 void launch_hub_final(const RoundParams& p, cudaStream_t s) {

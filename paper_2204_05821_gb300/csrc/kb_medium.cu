@@ -17,8 +17,9 @@
 //     the vertex's own count.
 //
 // Two kernels share the medium-vertex list, each skipping the other's
-// vertices: degrees up to 256 take a warp each (512-entry sets, 4 warps per
-// CTA); degrees up to 1024 take a CTA of 128 threads each (one 2048-entry set).
+// vertices: degrees up to RoundParams::med_split (at most 256) take a warp
+// each (512-entry sets, 4 warps per CTA); larger degrees, up to 1024, take a
+// CTA of 128 threads each (one 2048-entry set).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +30,7 @@
 namespace kb {
 namespace {
 
-constexpr int kMedSplit = 256;  // largest degree of the first class
+constexpr int kMedSplit = kMaxMedSplit;  // largest degree the warp kernel's set holds
 constexpr int kMedTask = 32;    // list entries per warp task (one per lane)
 constexpr int kMedCtaThreads = 128;  // threads per vertex of the second class
 static_assert(kMaxHubThreshold <= 1024, "the second class holds degrees up to 1024");
@@ -416,14 +417,15 @@ void launch_medium_round(const RoundParams& p, cudaStream_t s) {
     if (p.n_med <= 0) return;
     const int64_t tasks = (p.n_med + kMedTask - 1) / kMedTask;
     const int32_t thr = std::min(p.hub_threshold, (int32_t)kMaxHubThreshold);
-    if (p.small_max < kMedSplit) {
+    const int32_t split = std::min(std::max(p.med_split, 1), (int32_t)kMedSplit);
+    if (p.small_max < split) {
         constexpr int kW = 4;
         medium_round_kernel<2 * kMedSplit, kW>
-            <<<(unsigned)((tasks + kW - 1) / kW), kW * 32, 0, s>>>(p, p.small_max, std::min(thr, (int32_t)kMedSplit));
+            <<<(unsigned)((tasks + kW - 1) / kW), kW * 32, 0, s>>>(p, p.small_max, std::min(thr, split));
     }
-    if (thr > kMedSplit)
+    if (thr > split)
         medium_cta_kernel<2 * kMaxHubThreshold, kMedCtaThreads>
-            <<<(unsigned)tasks, kMedCtaThreads, 0, s>>>(p, std::max(p.small_max, (int32_t)kMedSplit), thr);
+            <<<(unsigned)tasks, kMedCtaThreads, 0, s>>>(p, std::max(p.small_max, split), thr);
 }
 
 }  // namespace kb

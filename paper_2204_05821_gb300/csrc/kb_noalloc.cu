@@ -105,6 +105,8 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     if (opt->hub_threshold < 0 || opt->hub_threshold > kb::kMaxHubThreshold) return KB_ERR_INVALID_ARG;
     if (opt->small_task_vertices != 0 && (opt->small_task_vertices < 32 || opt->small_task_vertices > 65536))
         return KB_ERR_INVALID_ARG;
+    if (opt->medium_split < 0 || opt->medium_split > kb::kMaxMedSplit) return KB_ERR_INVALID_ARG;
+    if (opt->small_max_degree < 0 || opt->small_max_degree > kb::kSmallDegree) return KB_ERR_INVALID_ARG;
     if (g->n == 0) {
         *count = 0;
         return KB_OK;
@@ -130,8 +132,10 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
     p.lab = opt->use_edge_labels ? g->edge_labels : nullptr;
     p.prev = prev;
     p.hub_threshold = thr;
-    p.small_max = std::min(kb::kSmallDegree, thr);
+    p.small_max = std::min(opt->small_max_degree > 0 ? opt->small_max_degree : kb::kSmallDegree, thr);
     p.warp_verts = opt->small_task_vertices;
+    p.hub_chunk = kb::kDefaultHubChunk;  // no hubs here
+    p.med_split = opt->medium_split > 0 ? opt->medium_split : kb::kDefaultMedSplit;
     p.hash_mode = opt->hash_mode;
     p.epoch = 1;
     p.table = reinterpret_cast<uint64_t*>(base + kOffTable);

@@ -93,13 +93,13 @@ __global__ void find_hubs_kernel(int64_t n, const int64_t* row, int32_t thr, int
 // Extent of every hub chunk, packed as (first edge << 16) | edge count, so a
 // chunk CTA reads one word instead of a chain of four dependent loads.
 __global__ void chunk_ext_kernel(int64_t chunks, const int32_t* chunk_hub, const int32_t* hub_v,
-                                 const int64_t* chunk_off, const int64_t* row, uint64_t* out) {
+                                 const int64_t* chunk_off, const int64_t* row, int32_t chunk, uint64_t* out) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += stride) {
         const int32_t h = chunk_hub[c];
         const int32_t v = hub_v[h];
-        const int64_t e0 = row[v] + (c - chunk_off[h]) * (int64_t)kHubChunk;
-        const int64_t len = min((int64_t)kHubChunk, row[(int64_t)v + 1] - e0);
+        const int64_t e0 = row[v] + (c - chunk_off[h]) * (int64_t)chunk;
+        const int64_t len = min((int64_t)chunk, row[(int64_t)v + 1] - e0);
         out[c] = ((uint64_t)e0 << 16) | (uint64_t)len;
     }
 }
@@ -320,9 +320,9 @@ void launch_find_hubs(int64_t n, const int64_t* row, int32_t thr, int32_t* out_v
 }
 
 void launch_chunk_ext(int64_t chunks, const int32_t* chunk_hub, const int32_t* hub_v, const int64_t* chunk_off,
-                      const int64_t* row, uint64_t* out, cudaStream_t s) {
+                      const int64_t* row, int32_t chunk, uint64_t* out, cudaStream_t s) {
     if (chunks <= 0) return;
-    chunk_ext_kernel<<<grid_for(chunks, 256), 256, 0, s>>>(chunks, chunk_hub, hub_v, chunk_off, row, out);
+    chunk_ext_kernel<<<grid_for(chunks, 256), 256, 0, s>>>(chunks, chunk_hub, hub_v, chunk_off, row, chunk, out);
 }
 
 void launch_locality_order(int64_t n, int64_t m, const int32_t* col, uint32_t* cnt, unsigned long long* hist,

@@ -84,14 +84,83 @@ def test_batch_single_and_degenerate(ctx):
     check_batch(ctx, [empty, g, empty], np.array([2, 2, 0], dtype=np.int32), 2, True, True)
 
 
+TUNING_FIELDS = ("load_factor", "hub_threshold", "small_task_vertices", "hub_chunk_edges", "medium_split",
+                 "small_max_degree")
+
+
+def _check_tuning(t):
+    assert min(abs(t["load_factor"] - x) for x in (0.35, 0.5, 0.7)) < 1e-6
+    assert t["hub_threshold"] in (256, 512, 1024)
+    assert t["small_task_vertices"] in (64, 128, 256, 512)
+    assert t["hub_chunk_edges"] in (256, 512, 1024)
+    assert t["medium_split"] in (64, 128, 256)
+    assert t["small_max_degree"] in (16, 24, 32)
+    assert 0 < t["ms"] <= t["default_ms"]
+
+
 def test_autotune_keeps_results(ctx):
+    # an RDF-like graph with hubs, so every tuning field has work to act on
+    g = graphgen.make(graphgen.scaled(graphgen.CONFIG_RDF, 0.002, seed=5))
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    ctx.clear_tuning()
+    t = ctx.autotune(dg, kb.Options(), rounds=2)
+    _check_tuning(t)
+    L, C, lc = oracle.refine_graph(g, 0, True, True, k=6)
+    res = ctx.refine(dg, 6, kb.Options())  # takes the cached tuning of this size class
+    assert np.array_equal(res.levels.cpu().numpy(), L) and np.array_equal(res.counts, C)
+    explicit = kb.Options(**{f: t[f] for f in TUNING_FIELDS})
+    res = ctx.refine(dg, 6, explicit)
+    assert np.array_equal(res.levels.cpu().numpy(), L)
+    ctx.clear_tuning()
+
+
+def test_autotune_batch_keeps_results(ctx):
+    gs, ks = mixed_graphs(40, 48)
+    union, voff = graphgen.disjoint_union(gs)
+    dg = kb.DeviceGraph.from_numpy(union, "cuda:0")
+    ctx.clear_tuning()
+    t = ctx.autotune(dg, kb.Options(), rounds=3, vertex_offsets=voff, ks=ks)
+    _check_tuning(t)
+    assert t["size_class"] >= 64
+    check_batch(ctx, gs, ks, 0, True, True)  # refine_batch now uses the cached choice
+    ctx.clear_tuning()
+
+
+@pytest.mark.parametrize("fields", [
+    dict(small_max_degree=1, medium_split=1),
+    dict(small_max_degree=16, medium_split=64, small_task_vertices=32),
+    dict(hub_chunk_edges=256, hub_threshold=64, medium_split=33),
+    dict(hub_chunk_edges=1024, hub_threshold=8, small_max_degree=4),
+    dict(small_max_degree=32, medium_split=256, hub_chunk_edges=512, small_task_vertices=65536),
+])
+def test_tuning_fields_keep_results(ctx, fields):
+    # extreme values of every tuning field against the oracle, one graph and a batch
+    g = graphgen.make(graphgen.scaled(graphgen.CONFIG_RDF, 0.001, seed=9))
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    for d in (kb.DIR_OUT, kb.DIR_BOTH):
+        L, C, _ = oracle.refine_graph(g, d, True, True, k=5, early_stop=False)
+        for rekey_all in (False, True):
+            res = ctx.refine(dg, 5, kb.Options(direction=d, early_stop=False, rekey_all=rekey_all, **fields))
+            assert np.array_equal(res.levels.cpu().numpy(), L), (d, rekey_all)
+            assert np.array_equal(res.counts, C)
+    gs, ks = mixed_graphs(41, 24)
+    union, voff = graphgen.disjoint_union(gs)
+    dgu = kb.DeviceGraph.from_numpy(union, "cuda:0")
+    levels, counts, lc = ctx.refine_batch(dgu, voff, ks, kb.Options(**fields))
+    for j, gj in enumerate(gs):
+        Lj, Cj, lcj = oracle.refine_graph(gj, 0, True, True, k=int(ks[j]), early_stop=True)
+        got = levels[:, int(voff[j]):int(voff[j + 1])].cpu().numpy()
+        for i in range(int(ks.max()) + 1):
+            assert np.array_equal(got[i], Lj[min(i, int(ks[j]))]), (j, i)
+
+
+def test_tuning_fields_are_range_checked(ctx):
     g = graphgen.make(graphgen.CONFIG_TINY)
     dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
-    lf, thr, ms = ctx.autotune(dg, kb.Options(), rounds=2)
-    assert 0 < lf <= 0.9 and thr in (256, 512, 1024) and ms > 0
-    L, C, lc = oracle.refine_graph(g, 0, True, True, k=10)
-    res = ctx.refine(dg, 10, kb.Options())
-    assert np.array_equal(res.levels.cpu().numpy(), L) and np.array_equal(res.counts, C)
+    for bad in (dict(hub_chunk_edges=300), dict(hub_chunk_edges=2048), dict(medium_split=257),
+                dict(medium_split=-1), dict(small_max_degree=33), dict(small_max_degree=-2)):
+        with pytest.raises(kb.KbError):
+            ctx.refine(dg, 2, kb.Options(**bad))
 
 
 def test_batch_rejects_cse_subjects(ctx):
