@@ -110,9 +110,10 @@ typedef struct {
  *                      library works on a copy of the neighbour ids in that order.
  *                      Costs one pass over the edges and 4 B x (m + 2n) of workspace
  *                      per call; results are identical either way.
- *                      0 -> automatic (on for single-graph calls with at least 2^22
- *                      processed edges and 24 rounds: on a 2e9-edge power-law graph
- *                      it saves ~7% per round and costs about 1.2 rounds once),
+ *                      0 -> automatic: on for prepared graphs (kb_graph_prepare)
+ *                      with at least 2^22 processed edges, where its cost is paid
+ *                      once; for kb_refine only with that many edges and at least
+ *                      24 rounds (its cost, about one round, is paid per call),
  *                      1 -> off, 2 -> on (single-graph calls; batched and served
  *                      refinement never reorder)
  *   subject            the subject part of every key, v ~s v' of Def. "cse" (complex
@@ -213,6 +214,56 @@ kb_status kb_refine(kb_context* ctx, const kb_graph* g, const kb_options* opt, i
 kb_status kb_refine_from(kb_context* ctx, const kb_graph* g, const kb_options* opt,
                          const int32_t* start, int i_start, int k, int32_t* levels,
                          int64_t* counts, int* levels_computed);
+
+/* ---- Prepared graphs ---------------------------------------------------------
+ * Every refinement call on a graph first derives per-graph structures from
+ * it: validation, the processed CSR (in-edges for KB_DIR_IN / KB_DIR_BOTH),
+ * the degree classes (list of medium vertices), the hub plan (chunks and the
+ * layout of the per-hub sets), the bits of edgeless vertices and, when on,
+ * the locality order (vertices ranked by how often they are gathered, with
+ * the neighbour ids rewritten to those ranks).  None of them depends on the
+ * levels, so Alg. 1's rounds (Sec. 4.1) can run on them any number of times.
+ * kb_graph_prepare builds them once, in device memory of the prepared graph's
+ * own; kb_refine_prepared is kb_refine without that per-call work.
+ *   g, opt    as for kb_refine.  The graph fields of opt are fixed here:
+ *             direction, use_edge_labels, hub_threshold, small_max_degree,
+ *             hub_chunk_edges, reorder and validate (checked once, here).
+ *             reorder 0 (automatic) turns the locality order on for at least
+ *             2^22 processed edges, since its cost is paid once (it costs about
+ *             as much as one round and saves part of every round's gather).
+ *   out       receives the prepared graph.  It refers to g's arrays, which must
+ *             stay alive and unchanged until kb_graph_release.  It can be used
+ *             by any context on the same device, by one call at a time.
+ * Errors as kb_refine (KB_ERR_INVALID_ARG for malformed CSR with validate,
+ * KB_ERR_OOM when its buffers do not fit).  Synchronises. */
+typedef struct kb_prepared kb_prepared;
+kb_status kb_graph_prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, kb_prepared** out);
+/* Free a prepared graph's device memory (NULL is accepted). */
+kb_status kb_graph_release(kb_prepared* pg);
+
+typedef struct {
+    size_t device_bytes;     /* device memory the prepared graph holds */
+    int64_t n_hubs;          /* vertices above the hub threshold */
+    int64_t n_hub_chunks;    /* hub-chunk CTAs of a round that keys every hub */
+    int64_t n_medium;        /* medium vertices */
+    int32_t reorder;         /* 1: locality order on */
+    int32_t hub_threshold;
+    int32_t small_max_degree;
+    int32_t hub_chunk_edges;
+    float build_ms;          /* host time of kb_graph_prepare */
+    int32_t reserved[3];
+} kb_prepared_info;
+kb_status kb_prepared_get_info(const kb_prepared* pg, kb_prepared_info* info);
+
+/* kb_refine on a prepared graph: levels, counts and levels_computed exactly as
+ * kb_refine of the same graph and options gives them.  opt->direction and
+ * opt->use_edge_labels must equal those of kb_graph_prepare
+ * (KB_ERR_INVALID_ARG otherwise); its other graph fields are ignored (the
+ * prepared values apply).  The per-call fields apply: use_vertex_labels,
+ * early_stop, load_factor, hash_mode, small_task_vertices, medium_split,
+ * subject, rekey_all. */
+kb_status kb_refine_prepared(kb_context* ctx, const kb_prepared* pg, const kb_options* opt, int k,
+                             int32_t* levels, int64_t* counts, int* levels_computed);
 
 /* Full (unstratified) bisimulation: refine until a round leaves the partition
  * unchanged, as Schaetzle et al. do (Sec. "Bisimulation Variants": they iterate

@@ -86,6 +86,44 @@ class Options:
         return o
 
 
+class PreparedGraph:
+    """A graph prepared by ``Context.prepare`` (``kb_graph_prepare``)."""
+
+    def __init__(self, lib, handle, graph, options):
+        self._lib = lib
+        self._h = handle
+        self.graph = graph  # keeps the tensors alive
+        self.options = options
+
+    @property
+    def handle(self):
+        if not self._h.value:
+            raise KbError(1, "prepared graph released")
+        return self._h
+
+    def info(self) -> dict:
+        i = _capi.KbPreparedInfo()
+        _capi.check(self._lib.kb_prepared_get_info(self.handle, ctypes.byref(i)))
+        return {name: getattr(i, name) for name, _ in _capi.KbPreparedInfo._fields_ if name != "reserved"}
+
+    def release(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.kb_graph_release(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.release()
+
+
 class DeviceGraph:
     """A CSR graph held in torch tensors on one CUDA device.
 
@@ -210,18 +248,45 @@ class Context:
         self._check(self._lib.kb_set_workspace(self._h, ctypes.c_void_p(self._ws.data_ptr()),
                                                self._ws.numel()))
 
+    # -- prepared graphs
+    def prepare(self, graph: DeviceGraph, options: Options = None) -> "PreparedGraph":
+        """``kb_graph_prepare``: the per-graph structures of every refinement
+        call (validation, processed CSR, degree classes, hub plan, edgeless
+        bits, locality order), built once.  Pass the result to ``refine`` in
+        place of the graph.  The graph's tensors must stay unchanged while it
+        lives (the prepared graph keeps a reference to them)."""
+        options = options or Options()
+        g, o = graph.to_c(), options.to_c()
+        h = ctypes.c_void_p()
+        self._check(self._lib.kb_graph_prepare(self._h, ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)))
+        return PreparedGraph(self._lib, h, graph, options)
+
     # -- refinement
-    def refine(self, graph: DeviceGraph, k: int, options: Options = None, out=None) -> Result:
+    def refine(self, graph, k: int, options: Options = None, out=None) -> Result:
+        """``kb_refine`` of a DeviceGraph, or ``kb_refine_prepared`` of a
+        PreparedGraph (``options`` then defaults to the preparation's)."""
         import torch
 
-        options = options or Options()
-        self._prepare_workspace(graph, k, options)
-        levels = out if out is not None else torch.empty((k + 1, graph.n), dtype=torch.int32, device=graph.device)
+        prepared = isinstance(graph, PreparedGraph)
+        if prepared:
+            options = options or graph.options
+            dg = graph.graph
+        else:
+            options = options or Options()
+            dg = graph
+            self._prepare_workspace(graph, k, options)
+        levels = out if out is not None else torch.empty((k + 1, dg.n), dtype=torch.int32, device=dg.device)
         counts = np.zeros(k + 1, dtype=np.int64)
         lc = ctypes.c_int(0)
-        g, o = graph.to_c(), options.to_c()
-        self._check(self._lib.kb_refine(self._h, ctypes.byref(g), ctypes.byref(o), int(k),
-                                        ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts), ctypes.byref(lc)))
+        o = options.to_c()
+        if prepared:
+            self._check(self._lib.kb_refine_prepared(self._h, graph.handle, ctypes.byref(o), int(k),
+                                                     ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts),
+                                                     ctypes.byref(lc)))
+        else:
+            g = dg.to_c()
+            self._check(self._lib.kb_refine(self._h, ctypes.byref(g), ctypes.byref(o), int(k),
+                                            ctypes.c_void_p(levels.data_ptr()), _np_ptr(counts), ctypes.byref(lc)))
         return Result(levels, counts, int(lc.value))
 
     def refine_from(self, graph: DeviceGraph, start, i_start: int, k: int, options: Options = None,

@@ -58,6 +58,21 @@ class KbOptions(ctypes.Structure):
     ]
 
 
+class KbPreparedInfo(ctypes.Structure):
+    _fields_ = [
+        ("device_bytes", ctypes.c_size_t),
+        ("n_hubs", ctypes.c_int64),
+        ("n_hub_chunks", ctypes.c_int64),
+        ("n_medium", ctypes.c_int64),
+        ("reorder", ctypes.c_int32),
+        ("hub_threshold", ctypes.c_int32),
+        ("small_max_degree", ctypes.c_int32),
+        ("hub_chunk_edges", ctypes.c_int32),
+        ("build_ms", ctypes.c_float),
+        ("reserved", ctypes.c_int32 * 3),
+    ]
+
+
 class KbTuning(ctypes.Structure):
     _fields_ = [
         ("load_factor", ctypes.c_float),
@@ -124,6 +139,10 @@ SIGNATURES = [
     ("kb_refine_host", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
     ("kb_refine_fixpoint", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _P, _I, _P, _P, _P, _P]),
     ("kb_summary", _I, [_P, ctypes.POINTER(KbGraph), _I, _I, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    ("kb_graph_prepare", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), ctypes.POINTER(_P)]),
+    ("kb_graph_release", _I, [_P]),
+    ("kb_prepared_get_info", _I, [_P, ctypes.POINTER(KbPreparedInfo)]),
+    ("kb_refine_prepared", _I, [_P, _P, ctypes.POINTER(KbOptions), _I, _P, _P, _P]),
     ("kb_refine_update", _I, [_P, ctypes.POINTER(KbGraph), ctypes.POINTER(KbOptions), _I, _P, ctypes.c_int64, _P, _P,
                               _P, _P]),
     ("kb_set_timing", _I, [_P, _I]),

@@ -130,10 +130,18 @@ struct Plan {
     bool freeze = false;   // frozen blocks skip the rounds (RoundParams::frozen)
     bool ext_table = false;  // block table and empty-signature minima live outside the workspace
     bool ext_freeze = false;  // frozen-block state lives outside the workspace
+    // the per-graph part (processed CSR, degree classes, hub plan, locality
+    // order, edgeless bits) lives in a prepared graph's own buffers: layout
+    // offsets of that part are relative to them (kb_graph_prepare)
+    bool graph_ext = false;
+    size_t graph_bytes = 0;
     // hubs (host copies, ascending vertex id)
     std::vector<int32_t> hub_v;
     std::vector<int64_t> chunk_off, set_off;
     std::vector<int32_t> chunk_hub;
+    // their sizes (the lists themselves are dropped once on the device)
+    size_t n_hubs = 0;
+    int64_t n_chunks = 0, set_slots = 0;
     // layout
     size_t o_rowp = 0, o_colp = 0, o_labp = 0, o_cursor = 0, o_inpref = 0, o_i64tmp = 0;
     size_t csr_bytes = 0;
@@ -144,6 +152,33 @@ struct Plan {
 };
 
 bool needs_in_csr(int dir) { return dir == KB_DIR_IN || dir == KB_DIR_BOTH; }
+
+}  // namespace
+
+// A prepared graph (kb_graph_prepare): the per-graph part of a plan built
+// once, in device buffers of its own.
+struct kb_prepared {
+    int device = 0;
+    kb_graph g{};       // the caller's arrays
+    int32_t dir = 0;
+    int32_t edge_labels = 0;
+    Plan P;             // graph_ext layout; host hub lists dropped after upload
+    char* csr = nullptr;   // processed CSR (IN / BOTH)
+    char* gbuf = nullptr;  // per-graph part
+    int64_t n_med = 0;
+    float build_ms = 0.f;
+    ~kb_prepared() {
+        if (!csr && !gbuf) return;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(device);
+        cudaFree(csr);
+        cudaFree(gbuf);
+        cudaSetDevice(cur);
+    }
+};
+
+namespace {
 
 void layout_csr(Plan& P) {
     size_t off = 0;
@@ -159,37 +194,43 @@ void layout_csr(Plan& P) {
     P.csr_bytes = off;
 }
 
+// Round buffers.  The per-graph part comes first, at offsets after the CSR
+// (or, with graph_ext, from 0 in a buffer of its own: graph_bytes); the
+// per-call part follows in the workspace (total).
 void layout_round(Plan& P) {
-    size_t off = P.csr_bytes;
-    auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
+    size_t goff = P.graph_ext ? 0 : P.csr_bytes;
+    auto takeg = [&](size_t bytes) { size_t o = goff; goff += align_up(bytes); return o; };
     const int64_t nw = (P.n >> 5) + 1;
-    const size_t H = P.hub_v.size();
-    P.o_med = take(sizeof(int32_t) * (size_t)(std::min<int64_t>(P.n, P.m_proc / 2 + 1) + 1));
+    const size_t H = P.n_hubs;
+    P.o_med = takeg(sizeof(int32_t) * (size_t)(std::min<int64_t>(P.n, P.m_proc / 2 + 1) + 1));
+    P.o_hubv = takeg(sizeof(int32_t) * H);
+    P.o_chunk = takeg(sizeof(int64_t) * (H + 1));
+    P.o_setoff = takeg(sizeof(int64_t) * (H + 1));
+    P.o_chunkhub = takeg(sizeof(int32_t) * (size_t)P.n_chunks);
+    P.o_chunkext = takeg(sizeof(uint64_t) * (size_t)P.n_chunks);
+    P.o_perm = takeg(P.reorder ? sizeof(int32_t) * (size_t)P.n : 0);
+    // a reordered copy of the caller's neighbour ids; the library's own in-edge
+    // CSR is reordered in place
+    P.o_colr = takeg(P.reorder && !needs_in_csr(P.dir) ? sizeof(int32_t) * (size_t)P.m_proc : 0);
+    P.o_hist = takeg(P.reorder ? sizeof(unsigned long long) * 512 : 0);
+    P.o_edgeless = takeg((P.freeze || P.graph_ext) ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.graph_bytes = P.graph_ext ? goff : 0;
+    size_t off = P.graph_ext ? 0 : goff;
+    auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes); return o; };
     P.o_emin = take(P.ext_table ? 0 : sizeof(uint64_t) * (size_t)std::max<int64_t>(P.n, 1));
     P.o_slot = take(sizeof(int32_t) * (size_t)std::max<int64_t>(P.n, 1));
     P.o_table = take(P.ext_table ? 0 : sizeof(uint64_t) * (size_t)P.cap);
     P.o_bitmap = take(sizeof(uint32_t) * (size_t)nw);
     P.o_prefix = take(sizeof(uint32_t) * (size_t)(nw + 1));
     P.o_scan = take(sizeof(uint32_t) * kb::scan_tmp_words(nw));
-    P.o_hubv = take(sizeof(int32_t) * H);
-    P.o_chunk = take(sizeof(int64_t) * (H + 1));
-    P.o_setoff = take(sizeof(int64_t) * (H + 1));
-    P.o_chunkhub = take(sizeof(int32_t) * P.chunk_hub.size());
-    P.o_chunkext = take(sizeof(uint64_t) * P.chunk_hub.size());
     P.o_acc = take(sizeof(uint64_t) * H);
     P.o_cnt = take(sizeof(uint32_t) * H);
-    P.o_sets = take(sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0));
-    P.o_perm = take(P.reorder ? sizeof(int32_t) * (size_t)P.n : 0);
+    P.o_sets = take(sizeof(uint64_t) * (size_t)P.set_slots);
     P.o_gat = take(P.reorder ? sizeof(int32_t) * (size_t)P.n : 0);
-    // a reordered copy of the caller's neighbour ids; the library's own in-edge
-    // CSR is reordered in place
-    P.o_colr = take(P.reorder && !needs_in_csr(P.dir) ? sizeof(int32_t) * (size_t)P.m_proc : 0);
-    P.o_hist = take(P.reorder ? sizeof(unsigned long long) * 512 : 0);
     P.o_ownkey = take(P.subject ? sizeof(int32_t) * (size_t)P.n : 0);
     const bool own_freeze = P.freeze && !P.ext_freeze;
     P.o_frozen = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_fmin = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
-    P.o_edgeless = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_shared = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_minof = take(own_freeze ? sizeof(uint32_t) * (size_t)P.n : 0);
     P.o_bm2 = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
@@ -279,6 +320,9 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
     P.hub_v.clear();
     P.chunk_off.assign(1, 0);
     P.set_off.assign(1, 0);
+    P.chunk_hub.clear();
+    P.n_hubs = 0;
+    P.n_chunks = P.set_slots = 0;
     if (P.n == 0 || P.m_proc == 0) return KB_OK;
     const int64_t hmax = std::min<int64_t>(P.n, P.m_proc / (P.thr + 1) + 1);
     const size_t deg_off = align_up(sizeof(int32_t) * (size_t)hmax);
@@ -316,6 +360,9 @@ kb_status plan_hubs(kb_context* ctx, Plan& P, const int64_t* row_p) {
     P.chunk_hub.resize((size_t)P.chunk_off[(size_t)H]);
     for (int32_t i = 0; i < H; ++i)
         for (int64_t c = P.chunk_off[(size_t)i]; c < P.chunk_off[(size_t)i + 1]; ++c) P.chunk_hub[(size_t)c] = i;
+    P.n_hubs = (size_t)H;
+    P.n_chunks = P.chunk_off[(size_t)H];
+    P.set_slots = P.set_off[(size_t)H];
     return KB_OK;
 }
 
@@ -345,37 +392,47 @@ const kb_tuning* tuned_for(const kb_context* ctx, int32_t c) {
     return best;
 }
 
+int32_t pick_field(int32_t given, int32_t cached, int32_t dflt) { return given ? given : (cached ? cached : dflt); }
+
+// The plan fields a call may choose on a prepared graph: key subject, frozen
+// blocks, table size, medium split and warp task size.
+void resolve_call_fields(Plan& P, const kb_options* opt, int rounds, bool multi, const kb_tuning* T) {
+    P.subject = opt->subject;
+    // stratified rounds of one graph or (multi) of batched and served graphs;
+    // incremental refinement plans without, and generic CSE keys need not
+    // hold the own previous block
+    P.freeze = (rounds >= 0 || multi) && P.subject == KB_SUBJECT_PREVIOUS && opt->rekey_all == 0;
+    P.med_split = pick_field(opt->medium_split, T ? T->medium_split : 0, kb::kDefaultMedSplit);
+    P.warp_verts = pick_field(opt->small_task_vertices, T ? T->small_task_vertices : 0, kb::kDefaultWarpVerts);
+    float lf = opt->load_factor > 0.f ? opt->load_factor : (T ? T->load_factor : 0.f);
+    if (!(lf > 0.f)) lf = 0.5f;
+    P.cap = next_pow2((uint64_t)((double)std::max<int64_t>(P.n, 1) / (double)lf) + 1);
+    if (P.cap < 1024) P.cap = 1024;
+    if (P.cap > ((uint64_t)1 << 32)) P.cap = (uint64_t)1 << 32;
+}
+
 // `rounds`: refinement rounds the call runs (decides the automatic locality
 // order); negative for batched and served refinement, which never reorder.
+// With P.graph_ext set (building a prepared graph) the automatic locality
+// order is on for at least 2^22 processed edges: its cost is paid once.
 kb_status make_plan(kb_context* ctx, const kb_graph* g, const kb_options* opt, Plan& P, char** csr_base_out,
                     bool for_query, int rounds, bool multi = false) {
     P.n = g->n;
     P.m = g->m;
     P.dir = opt->direction;
     P.m_proc = P.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
-    P.subject = opt->subject;
+    const bool auto_order = P.graph_ext || rounds >= 24;
     P.reorder = rounds >= 0 && P.n > 0 && P.m_proc > 0 &&
-                (opt->reorder == 2 || (opt->reorder == 0 && rounds >= 24 && P.m_proc >= ((int64_t)1 << 22)));
-    // stratified rounds of one graph or (multi) of batched and served graphs;
-    // incremental refinement plans without, and generic CSE keys need not
-    // hold the own previous block
-    P.freeze = (rounds >= 0 || multi) && P.subject == KB_SUBJECT_PREVIOUS && opt->rekey_all == 0;
+                (opt->reorder == 2 || (opt->reorder == 0 && auto_order && P.m_proc >= ((int64_t)1 << 22)));
     P.labels = opt->use_edge_labels && g->edge_labels != nullptr;
     // tuning fields: the options' value, else the cached tuning of the call's
     // size class, else the library default
     P.size_class = size_class(P.m_proc, multi ? ctx->plan_graphs : 1, multi);
     const kb_tuning* T = tuned_for(ctx, P.size_class);
-    auto pick = [](int32_t given, int32_t cached, int32_t dflt) { return given ? given : (cached ? cached : dflt); };
-    P.thr = pick(opt->hub_threshold, T ? T->hub_threshold : 0, kb::kDefaultHubThreshold);
-    P.hub_chunk = pick(opt->hub_chunk_edges, T ? T->hub_chunk_edges : 0, kb::kDefaultHubChunk);
-    P.med_split = pick(opt->medium_split, T ? T->medium_split : 0, kb::kDefaultMedSplit);
-    P.small_max = std::min(pick(opt->small_max_degree, T ? T->small_max_degree : 0, kb::kSmallDegree), P.thr);
-    P.warp_verts = pick(opt->small_task_vertices, T ? T->small_task_vertices : 0, kb::kDefaultWarpVerts);
-    float lf = opt->load_factor > 0.f ? opt->load_factor : (T ? T->load_factor : 0.f);
-    if (!(lf > 0.f)) lf = 0.5f;
-    P.cap = next_pow2((uint64_t)((double)std::max<int64_t>(P.n, 1) / (double)lf) + 1);
-    if (P.cap < 1024) P.cap = 1024;
-    if (P.cap > ((uint64_t)1 << 32)) P.cap = (uint64_t)1 << 32;
+    P.thr = pick_field(opt->hub_threshold, T ? T->hub_threshold : 0, kb::kDefaultHubThreshold);
+    P.hub_chunk = pick_field(opt->hub_chunk_edges, T ? T->hub_chunk_edges : 0, kb::kDefaultHubChunk);
+    P.small_max = std::min(pick_field(opt->small_max_degree, T ? T->small_max_degree : 0, kb::kSmallDegree), P.thr);
+    resolve_call_fields(P, opt, rounds, multi, T);
     layout_csr(P);
     const int64_t* row_p = g->row_offsets;
     char* csr_base = nullptr;
@@ -490,61 +547,15 @@ struct Prepared {
     bool hub_on = true;    // some hub refines this round
 };
 
-// Validate, plan, acquire the workspace, bind the round parameters, list the
-// medium vertices and reset the per-call state (block table, empty-signature
-// minima).  Synchronises.
-kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Prepared& R, int rounds,
-                  bool multi = false) {
-    cudaStream_t s = ctx->stream;
+// Bind the per-graph part of a plan into p: the processed CSR (csr: IN /
+// BOTH), the hub lists, the locality order and the medium list (gws: graph
+// part base).  build: also fill them (hub lists uploaded, chunk extents, the
+// locality order, using `count_tmp` (n words) as scratch, the medium list
+// and, with `edgeless`, the edgeless bits); else they hold a prepared graph's
+// contents.  Synchronises when building.
+kb_status bind_graph_part(kb_context* ctx, const kb_graph* g, const Plan& P, char* csr, char* gws, bool build,
+                          uint32_t* count_tmp, kb::RoundParams& p, cudaStream_t s) {
     const int64_t n = g->n;
-    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
-    if (opt->validate) {
-        kb::launch_validate(n, g->m, g->row_offsets, g->col_indices, ctx->d_ctr, s);
-        KB_CUDA(ctx, cudaGetLastError());
-        KB_TRY(read_counters(ctx));
-        KB_TRY(device_error(ctx));
-    }
-    // The processed CSR sits at the head of the workspace, so its size is known
-    // before the hub layout.
-    Plan& P = R.P;
-    Plan probe;
-    probe.n = n;
-    probe.m = g->m;
-    probe.dir = opt->direction;
-    probe.m_proc = probe.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
-    probe.labels = opt->use_edge_labels && g->edge_labels != nullptr;
-    layout_csr(probe);
-    char* base = nullptr;
-    if (probe.csr_bytes) {
-        // The hub layout is not known yet: reserve the CSR part first.  A
-        // library-owned workspace keeps its contents when it does not grow.
-        if (ctx->user_ws) {
-            KB_TRY(acquire_workspace(ctx, probe.csr_bytes, &base));
-        } else {
-            KB_TRY(ensure_buffer(ctx, &ctx->plan_tmp, &ctx->plan_tmp_bytes, probe.csr_bytes));
-            base = reinterpret_cast<char*>(ctx->plan_tmp);
-        }
-    }
-    P.ext_table = R.ext_table != nullptr;
-    P.ext_freeze = R.ext_frozen != nullptr;
-    KB_TRY(make_plan(ctx, g, opt, P, &base, false, rounds, multi));
-    char* ws = nullptr;
-    if (ctx->user_ws) {
-        KB_TRY(acquire_workspace(ctx, P.total, &ws));
-    } else {
-        // round buffers live in the owned workspace; the CSR stays in plan_tmp
-        const size_t csr_bytes = P.csr_bytes;
-        P.csr_bytes = 0;
-        layout_round(P);
-        P.csr_bytes = csr_bytes;
-        KB_TRY(ensure_buffer(ctx, &ctx->own_ws, &ctx->own_ws_bytes, std::max<size_t>(P.total, 256)));
-        ws = reinterpret_cast<char*>(ctx->own_ws);
-    }
-    char* csr = base;
-    R.ws = ws;
-    kb::RoundParams& p = R.p;
-    p = kb::RoundParams{};
-    p.n = n;
     if (needs_in_csr(P.dir)) {
         p.row = reinterpret_cast<const int64_t*>(csr + P.o_rowp);
         p.col = reinterpret_cast<const int32_t*>(csr + P.o_colp);
@@ -554,6 +565,135 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
         p.col = g->col_indices;
         p.lab = P.labels ? g->edge_labels : nullptr;
     }
+    const size_t H = P.n_hubs;
+    p.n_hubs = (int32_t)H;
+    p.hub_v = reinterpret_cast<const int32_t*>(gws + P.o_hubv);
+    p.hub_chunk_off = reinterpret_cast<const int64_t*>(gws + P.o_chunk);
+    p.hub_set_off = reinterpret_cast<const int64_t*>(gws + P.o_setoff);
+    p.chunk_hub = reinterpret_cast<const int32_t*>(gws + P.o_chunkhub);
+    p.chunk_ext = reinterpret_cast<const uint64_t*>(gws + P.o_chunkext);
+    if (build && H) {
+        KB_CUDA(ctx, cudaMemcpyAsync(gws + P.o_hubv, P.hub_v.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice, s));
+        KB_CUDA(ctx, cudaMemcpyAsync(gws + P.o_chunk, P.chunk_off.data(), sizeof(int64_t) * (H + 1),
+                                     cudaMemcpyHostToDevice, s));
+        KB_CUDA(ctx, cudaMemcpyAsync(gws + P.o_setoff, P.set_off.data(), sizeof(int64_t) * (H + 1),
+                                     cudaMemcpyHostToDevice, s));
+        KB_CUDA(ctx, cudaMemcpyAsync(gws + P.o_chunkhub, P.chunk_hub.data(), sizeof(int32_t) * P.chunk_hub.size(),
+                                     cudaMemcpyHostToDevice, s));
+        kb::launch_chunk_ext((int64_t)P.chunk_hub.size(), p.chunk_hub, p.hub_v, p.hub_chunk_off, p.row, P.hub_chunk,
+                             reinterpret_cast<uint64_t*>(gws + P.o_chunkext), s);
+        KB_CUDA(ctx, cudaGetLastError());
+    }
+    if (P.reorder) {
+        int32_t* perm = reinterpret_cast<int32_t*>(gws + P.o_perm);
+        int32_t* colr = needs_in_csr(P.dir) ? const_cast<int32_t*>(p.col) : reinterpret_cast<int32_t*>(gws + P.o_colr);
+        if (build) {
+            // rank vertices by how often they are gathered and move the
+            // neighbour ids to those ranks
+            kb::launch_locality_order(n, P.m_proc, p.col, count_tmp,
+                                      reinterpret_cast<unsigned long long*>(gws + P.o_hist), perm, s);
+            kb::launch_remap_cols(P.m_proc, p.col, perm, colr, s);
+            KB_CUDA(ctx, cudaGetLastError());
+        }
+        p.col = colr;
+        p.perm = perm;
+    }
+    p.med_v = reinterpret_cast<int32_t*>(gws + P.o_med);
+    if (build) {
+        p.n_med = 0;
+        if (g->m > 0) {
+            KB_CUDA(ctx, cudaMemsetAsync(ctx->d_med_n, 0, sizeof(int64_t), s));
+            kb::launch_classify(n, p.row, p.small_max, P.thr, const_cast<int32_t*>(p.med_v), ctx->d_med_n, s);
+            KB_CUDA(ctx, cudaGetLastError());
+            KB_CUDA(ctx, cudaMemcpyAsync(ctx->h_med_n, ctx->d_med_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            KB_CUDA(ctx, cudaStreamSynchronize(s));
+            p.n_med = *ctx->h_med_n;
+        }
+        if (P.freeze || P.graph_ext)  // laid out only then
+            kb::launch_edgeless_bits(n, p.row, reinterpret_cast<uint32_t*>(gws + P.o_edgeless), s);
+        KB_CUDA(ctx, cudaGetLastError());
+    }
+    return KB_OK;
+}
+
+// Validate, plan, acquire the workspace, bind the round parameters, list the
+// medium vertices and reset the per-call state (block table, empty-signature
+// minima).  With a prepared graph (pg) only the per-call part is planned and
+// reset.  Synchronises.
+kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Prepared& R, int rounds,
+                  bool multi = false, const kb_prepared* pg = nullptr) {
+    cudaStream_t s = ctx->stream;
+    const int64_t n = g->n;
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    Plan& P = R.P;
+    char* csr = nullptr;
+    char* gws = nullptr;
+    char* ws = nullptr;
+    kb::RoundParams& p = R.p;
+    p = kb::RoundParams{};
+    p.n = n;
+    p.ctr = ctx->d_ctr;
+    if (pg) {
+        P = pg->P;
+        P.ext_table = R.ext_table != nullptr;
+        P.ext_freeze = R.ext_frozen != nullptr;
+        resolve_call_fields(P, opt, rounds, multi, tuned_for(ctx, P.size_class));
+        layout_round(P);
+        KB_TRY(acquire_workspace(ctx, P.total, &ws));
+        p.small_max = P.small_max;
+        csr = pg->csr;
+        gws = pg->gbuf;
+        KB_TRY(bind_graph_part(ctx, g, P, csr, gws, false, nullptr, p, s));
+        p.n_med = pg->n_med;
+    } else {
+        if (opt->validate) {
+            kb::launch_validate(n, g->m, g->row_offsets, g->col_indices, ctx->d_ctr, s);
+            KB_CUDA(ctx, cudaGetLastError());
+            KB_TRY(read_counters(ctx));
+            KB_TRY(device_error(ctx));
+        }
+        // The processed CSR sits at the head of the workspace, so its size is known
+        // before the hub layout.
+        Plan probe;
+        probe.n = n;
+        probe.m = g->m;
+        probe.dir = opt->direction;
+        probe.m_proc = probe.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
+        probe.labels = opt->use_edge_labels && g->edge_labels != nullptr;
+        layout_csr(probe);
+        char* base = nullptr;
+        if (probe.csr_bytes) {
+            // The hub layout is not known yet: reserve the CSR part first.  A
+            // library-owned workspace keeps its contents when it does not grow.
+            if (ctx->user_ws) {
+                KB_TRY(acquire_workspace(ctx, probe.csr_bytes, &base));
+            } else {
+                KB_TRY(ensure_buffer(ctx, &ctx->plan_tmp, &ctx->plan_tmp_bytes, probe.csr_bytes));
+                base = reinterpret_cast<char*>(ctx->plan_tmp);
+            }
+        }
+        P.ext_table = R.ext_table != nullptr;
+        P.ext_freeze = R.ext_frozen != nullptr;
+        KB_TRY(make_plan(ctx, g, opt, P, &base, false, rounds, multi));
+        if (ctx->user_ws) {
+            KB_TRY(acquire_workspace(ctx, P.total, &ws));
+        } else {
+            // round buffers live in the owned workspace; the CSR stays in plan_tmp
+            const size_t csr_bytes = P.csr_bytes;
+            P.csr_bytes = 0;
+            layout_round(P);
+            P.csr_bytes = csr_bytes;
+            KB_TRY(ensure_buffer(ctx, &ctx->own_ws, &ctx->own_ws_bytes, std::max<size_t>(P.total, 256)));
+            ws = reinterpret_cast<char*>(ctx->own_ws);
+        }
+        csr = base;
+        gws = ws;
+        p.small_max = P.small_max;
+        // the slot array serves as the count buffer of the locality order:
+        // every round rewrites it
+        KB_TRY(bind_graph_part(ctx, g, P, csr, gws, true, reinterpret_cast<uint32_t*>(ws + P.o_slot), p, s));
+    }
+    R.ws = ws;
     p.hub_threshold = P.thr;
     p.small_max = P.small_max;
     p.warp_verts = P.warp_verts;
@@ -571,64 +711,20 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
     }
     p.bitmap = reinterpret_cast<uint32_t*>(ws + P.o_bitmap);
     p.ctr = ctx->d_ctr;
-    const size_t H = P.hub_v.size();
-    p.n_hubs = (int32_t)H;
-    p.hub_v = reinterpret_cast<const int32_t*>(ws + P.o_hubv);
-    p.hub_chunk_off = reinterpret_cast<const int64_t*>(ws + P.o_chunk);
-    p.hub_set_off = reinterpret_cast<const int64_t*>(ws + P.o_setoff);
-    p.chunk_hub = reinterpret_cast<const int32_t*>(ws + P.o_chunkhub);
-    p.chunk_ext = reinterpret_cast<const uint64_t*>(ws + P.o_chunkext);
     p.hub_sets = reinterpret_cast<uint64_t*>(ws + P.o_sets);
     p.hub_acc = reinterpret_cast<uint64_t*>(ws + P.o_acc);
     p.hub_cnt = reinterpret_cast<uint32_t*>(ws + P.o_cnt);
+    if (P.reorder) p.gat = reinterpret_cast<int32_t*>(ws + P.o_gat);
     R.prefix = reinterpret_cast<uint32_t*>(ws + P.o_prefix);
     R.scan_tmp = reinterpret_cast<uint32_t*>(ws + P.o_scan);
-    if (H) {
-        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_hubv, P.hub_v.data(), sizeof(int32_t) * H, cudaMemcpyHostToDevice, s));
-        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunk, P.chunk_off.data(), sizeof(int64_t) * (H + 1),
-                                     cudaMemcpyHostToDevice, s));
-        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_setoff, P.set_off.data(), sizeof(int64_t) * (H + 1),
-                                     cudaMemcpyHostToDevice, s));
-        KB_CUDA(ctx, cudaMemcpyAsync(ws + P.o_chunkhub, P.chunk_hub.data(), sizeof(int32_t) * P.chunk_hub.size(),
-                                     cudaMemcpyHostToDevice, s));
-        kb::launch_chunk_ext((int64_t)P.chunk_hub.size(), p.chunk_hub, p.hub_v, p.hub_chunk_off, p.row, P.hub_chunk,
-                             reinterpret_cast<uint64_t*>(ws + P.o_chunkext), s);
-        KB_CUDA(ctx, cudaGetLastError());
-    }
-    if (P.reorder) {
-        // rank vertices by how often they are gathered (the slot array serves as
-        // the count buffer: every round rewrites it) and move the neighbour ids
-        // to those ranks
-        int32_t* perm = reinterpret_cast<int32_t*>(ws + P.o_perm);
-        kb::launch_locality_order(n, P.m_proc, p.col, reinterpret_cast<uint32_t*>(p.slot_of),
-                                  reinterpret_cast<unsigned long long*>(ws + P.o_hist), perm, s);
-        int32_t* colr = needs_in_csr(P.dir) ? const_cast<int32_t*>(p.col) : reinterpret_cast<int32_t*>(ws + P.o_colr);
-        kb::launch_remap_cols(P.m_proc, p.col, perm, colr, s);
-        KB_CUDA(ctx, cudaGetLastError());
-        p.col = colr;
-        p.perm = perm;
-        p.gat = reinterpret_cast<int32_t*>(ws + P.o_gat);
-    }
-    // medium vertices, once per call
-    int32_t* med = reinterpret_cast<int32_t*>(ws + P.o_med);
-    p.med_v = med;
-    p.n_med = 0;
-    if (g->m > 0) {
-        KB_CUDA(ctx, cudaMemsetAsync(ctx->d_med_n, 0, sizeof(int64_t), s));
-        kb::launch_classify(n, p.row, p.small_max, P.thr, med, ctx->d_med_n, s);
-        KB_CUDA(ctx, cudaGetLastError());
-        KB_CUDA(ctx, cudaMemcpyAsync(ctx->h_med_n, ctx->d_med_n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        KB_CUDA(ctx, cudaStreamSynchronize(s));
-        p.n_med = *ctx->h_med_n;
-    }
-    R.total_chunks = H ? P.chunk_off[H] : 0;
-    R.set_bytes = sizeof(uint64_t) * (size_t)(H ? P.set_off[H] : 0);
+    R.total_chunks = P.n_chunks;
+    R.set_bytes = sizeof(uint64_t) * (size_t)P.set_slots;
     if (!R.ext_table) {
         KB_CUDA(ctx, cudaMemsetAsync(p.table, 0, sizeof(uint64_t) * (size_t)P.cap, s));
         R.epoch = 0;
     }
     if (P.freeze) {
-        R.edgeless = reinterpret_cast<uint32_t*>(ws + P.o_edgeless);
+        R.edgeless = reinterpret_cast<uint32_t*>(gws + P.o_edgeless);
         R.bm[0] = p.bitmap;
         R.bm[1] = reinterpret_cast<uint32_t*>(ws + P.o_bm2);
         R.bm_cur = 0;
@@ -653,7 +749,6 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
             KB_CUDA(ctx, cudaMemsetAsync(R.frozen_min, 0, bw, s));
             KB_CUDA(ctx, cudaMemsetAsync(p.shared, 0, bw, s));
         }
-        kb::launch_edgeless_bits(n, p.row, R.edgeless, s);
         KB_CUDA(ctx, cudaGetLastError());
     }
     return KB_OK;
@@ -749,7 +844,7 @@ struct LevelRows {
 // *stopped_stable whether a round reproduced its input partition.
 kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
                       int k, const LevelRows& rows, int64_t* counts, int* levels_computed, int64_t* last_count,
-                      bool* stopped_stable = nullptr) {
+                      bool* stopped_stable = nullptr, const kb_prepared* pg = nullptr) {
     const int64_t n = g->n;
     const bool fixpoint = rows.levels == nullptr;
     if (levels_computed) *levels_computed = i_start;
@@ -763,7 +858,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     cudaStream_t s = ctx->stream;
     ctx->round_keyed.clear();
     Prepared R;
-    KB_TRY(prepare(ctx, g, opt, R, k - i_start));
+    KB_TRY(prepare(ctx, g, opt, R, k - i_start, false, pg));
     kb::RoundParams& p = R.p;
 
     // ---- the subject part of every key (generic CSE rounds)
@@ -877,7 +972,8 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
 }
 
 kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
-                      int k, int32_t* levels, int64_t* counts, int* levels_computed);
+                      int k, int32_t* levels, int64_t* counts, int* levels_computed,
+                      const kb_prepared* pg = nullptr);
 
 // Incremental refinement (kb_refine_update): levels holds the levels of the
 // graph before the change (same options); each round re-keys only the work set
@@ -1043,7 +1139,7 @@ kb_status update_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
 }
 
 kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
-                      int k, int32_t* levels, int64_t* counts, int* levels_computed) {
+                      int k, int32_t* levels, int64_t* counts, int* levels_computed, const kb_prepared* pg) {
     KB_TRY(check_graph(ctx, g, opt, k));
     if (i_start < 0 || i_start > k) return fail(ctx, KB_ERR_INVALID_ARG, "i_start must be in [0, k]");
     if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
@@ -1053,7 +1149,7 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     LevelRows rows;
     rows.levels = levels;
     rows.n = g->n;
-    return refine_core(ctx, g, opt, start, i_start, k, rows, counts, levels_computed, nullptr);
+    return refine_core(ctx, g, opt, start, i_start, k, rows, counts, levels_computed, nullptr, nullptr, pg);
 }
 
 // Summary graph of (src_level, dst_level): distinct triples in order of first
@@ -2032,6 +2128,104 @@ kb_status kb_refine_from(kb_context* ctx, const kb_graph* g, const kb_options* o
     if (!ctx) return KB_ERR_INVALID_ARG;
     if (!start && g && g->n > 0) return fail(ctx, KB_ERR_INVALID_ARG, "start is NULL");
     return refine_impl(ctx, g, opt, start, i_start, k, levels, counts, levels_computed);
+}
+
+kb_status kb_graph_prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, kb_prepared** out) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    if (!out) return fail(ctx, KB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    KB_TRY(check_graph(ctx, g, opt, 0));
+    KB_CUDA(ctx, cudaSetDevice(ctx->device));
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = ctx->stream;
+    std::unique_ptr<kb_prepared> pg(new kb_prepared);
+    pg->device = ctx->device;
+    pg->g = *g;
+    pg->dir = opt->direction;
+    pg->edge_labels = opt->use_edge_labels ? 1 : 0;
+    const int64_t n = g->n;
+    KB_CUDA(ctx, cudaMemsetAsync(ctx->d_ctr, 0, sizeof(Counters), s));
+    if (opt->validate && n > 0) {
+        kb::launch_validate(n, g->m, g->row_offsets, g->col_indices, ctx->d_ctr, s);
+        KB_CUDA(ctx, cudaGetLastError());
+        KB_TRY(read_counters(ctx));
+        KB_TRY(device_error(ctx));
+    }
+    Plan& P = pg->P;
+    P.graph_ext = true;
+    Plan probe;
+    probe.n = n;
+    probe.m = g->m;
+    probe.dir = opt->direction;
+    probe.m_proc = probe.dir == KB_DIR_BOTH ? 2 * g->m : g->m;
+    probe.labels = opt->use_edge_labels && g->edge_labels != nullptr;
+    layout_csr(probe);
+    auto alloc = [&](char** ptr, size_t bytes) -> kb_status {
+        if (cudaMalloc(reinterpret_cast<void**>(ptr), std::max<size_t>(bytes, 256)) != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            return fail(ctx, KB_ERR_OOM, "cannot allocate %zu bytes of device memory", bytes);
+        }
+        return KB_OK;
+    };
+    if (probe.csr_bytes) KB_TRY(alloc(&pg->csr, probe.csr_bytes));
+    char* base = pg->csr;
+    if (n > 0) KB_TRY(make_plan(ctx, g, opt, P, &base, false, 1, false));
+    KB_TRY(alloc(&pg->gbuf, P.graph_bytes));
+    if (n > 0) {
+        char* count_tmp = nullptr;
+        if (P.reorder) KB_TRY(alloc(&count_tmp, sizeof(uint32_t) * (size_t)n));
+        kb::RoundParams p{};
+        p.n = n;
+        p.small_max = P.small_max;
+        const kb_status st = bind_graph_part(ctx, g, P, pg->csr, pg->gbuf, true,
+                                             reinterpret_cast<uint32_t*>(count_tmp), p, s);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(count_tmp);
+        KB_TRY(st);
+        if (e != cudaSuccess) return fail(ctx, KB_ERR_CUDA, "prepare: %s", cudaGetErrorString(e));
+        pg->n_med = p.n_med;
+    }
+    // the hub lists are on the device now
+    std::vector<int32_t>().swap(P.hub_v);
+    std::vector<int64_t>().swap(P.chunk_off);
+    std::vector<int64_t>().swap(P.set_off);
+    std::vector<int32_t>().swap(P.chunk_hub);
+    pg->build_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = pg.release();
+    return KB_OK;
+}
+
+kb_status kb_graph_release(kb_prepared* pg) {
+    delete pg;
+    return KB_OK;
+}
+
+kb_status kb_prepared_get_info(const kb_prepared* pg, kb_prepared_info* info) {
+    if (!pg || !info) return KB_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->device_bytes = (pg->csr ? pg->P.csr_bytes : 0) + pg->P.graph_bytes;
+    info->n_hubs = (int64_t)pg->P.n_hubs;
+    info->n_hub_chunks = pg->P.n_chunks;
+    info->n_medium = pg->n_med;
+    info->reorder = pg->P.reorder ? 1 : 0;
+    info->hub_threshold = pg->P.thr;
+    info->small_max_degree = pg->P.small_max;
+    info->hub_chunk_edges = pg->P.hub_chunk;
+    info->build_ms = pg->build_ms;
+    return KB_OK;
+}
+
+kb_status kb_refine_prepared(kb_context* ctx, const kb_prepared* pg, const kb_options* opt, int k, int32_t* levels,
+                             int64_t* counts, int* levels_computed) {
+    if (!ctx) return KB_ERR_INVALID_ARG;
+    if (!pg || !opt) return fail(ctx, KB_ERR_INVALID_ARG, "prepared graph and options must not be NULL");
+    if (pg->device != ctx->device)
+        return fail(ctx, KB_ERR_INVALID_ARG, "the graph was prepared on device %d, the context is on %d", pg->device,
+                    ctx->device);
+    if (opt->direction != pg->dir || (opt->use_edge_labels ? 1 : 0) != pg->edge_labels)
+        return fail(ctx, KB_ERR_INVALID_ARG, "direction and use_edge_labels must be those of kb_graph_prepare");
+    return refine_impl(ctx, &pg->g, opt, nullptr, 0, k, levels, counts, levels_computed, pg);
 }
 
 kb_status kb_refine_update(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k, const int32_t* changed,

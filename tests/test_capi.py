@@ -67,7 +67,7 @@ def test_ctypes_structs_match_the_header():
     structs = header_structs()
     pairs = {"kb_graph": _capi.KbGraph, "kb_options": _capi.KbOptions,
              "kb_server_config": _capi.KbServerConfig, "kb_server_stats": _capi.KbServerStats,
-             "kb_tuning": _capi.KbTuning}
+             "kb_tuning": _capi.KbTuning, "kb_prepared_info": _capi.KbPreparedInfo}
     assert set(pairs) <= set(structs)
     for cname, py in pairs.items():
         want = structs[cname]
