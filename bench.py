@@ -195,9 +195,26 @@ def cpu_baseline(cfg, target_s=12.0, max_reps=40):
         oracle.refine_graph(g, 0, True, True, k=1, early_stop=False)
         total += time.perf_counter() - t0
         reps += 1
-    return {"value": g.m * reps / total, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle (single-threaded C++ map refinement) on the same recipe scaled to n=%d, m=%d: "
-                      "%d call(s) of one round after level 0, %.1f s in all" % (g.n, g.m, reps, total)}
+    out = {"value": g.m * reps / total, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+           "sample": "oracle (single-threaded C++ map refinement) on the same recipe scaled to n=%d, m=%d: "
+                     "%d call(s) of one round after level 0, %.1f s in all" % (g.n, g.m, reps, total)}
+    # the multi-core CPU baseline (OpenMP, every host core) on the same sample
+    import cpu_parallel
+
+    L, C, _ = oracle.refine_graph(g, 0, True, True, k=1, early_stop=False)
+    P, PC, _ = cpu_parallel.refine_graph(g, 0, True, True, k=1, early_stop=False)
+    ptotal, preps = 0.0, 0
+    while preps < max_reps and (preps == 0 or ptotal < target_s / 3):
+        t0 = time.perf_counter()
+        cpu_parallel.refine_graph(g, 0, True, True, k=1, early_stop=False)
+        ptotal += time.perf_counter() - t0
+        preps += 1
+    out["parallel"] = {"value": g.m * preps / ptotal, "unit": UNIT, "cores": cpu_parallel.threads(),
+                       "kind": "OpenMP signatures + parallel sort (cpu_parallel/)",
+                       "equal_to_oracle": bool(np.array_equal(P, L) and np.array_equal(PC, C)),
+                       "sample": "the same graph: %d call(s) of one round after level 0, %.1f s in all"
+                                 % (preps, ptotal)}
+    return out
 
 
 # ----------------------------------------------------------------------------- reference arm
