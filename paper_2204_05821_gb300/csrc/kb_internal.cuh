@@ -58,9 +58,12 @@ struct RoundParams {
     const int32_t* prev;  // [n] previous level (vertex labels at level 0)
     // Locality order (optional).  perm[v] is v's position in an order that puts
     // often-gathered vertices first; col then holds positions instead of ids and
-    // gat holds the previous level in that order (gat[perm[v]] = prev[v]), so
+    // gat holds the previous level in that order, each block named by its
+    // smallest member instead of its rank (gat[perm[v]] = smallest member of
+    // v's block; any injective naming of blocks gives the same partition), so
     // the per-edge gather of neighbour blocks hits a compact, cache-resident
-    // head.  perm == nullptr: col holds ids and the gather reads prev.
+    // head, and the renumbering rewrites gat only where a block's smallest
+    // member changed.  perm == nullptr: col holds ids and the gather reads prev.
     const int32_t* perm;
     int32_t* gat;
     // Generic CSE rounds (Def. "cse"): the subject part of every key, one class

@@ -407,10 +407,9 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
         uint32_t mark = kNoMark;
         if (!vertex_active(p, v)) {
             if (!p.vmask) {  // a batched graph that stopped: its ids shift with the graphs before it
+                // (batched runs never use the locality order)
                 const int32_t g = p.vgraph[v];
-                const int32_t b = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
-                out[v] = b;
-                if (p.perm) p.gat[p.perm[v]] = b;
+                out[v] = (int32_t)((uint32_t)p.prev[v] - p.gbase_prev[g] + p.gbase_cur[g]);
                 continue;
             }
             mn = p.kmin[p.keep_old[v]];  // incremental: the smallest kept member of its old block
@@ -427,7 +426,7 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
         const uint32_t mw = p.bitmap[mn >> 5];
         const int32_t b = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
         out[v] = b;
-        if (p.perm) p.gat[p.perm[v]] = b;
+        if (p.perm) p.gat[p.perm[v]] = (int32_t)mn;  // the block by its smallest member
         if (p.shared) {
             // one lane per distinct minimum in the warp, then the CTA's cache,
             // then an L2 read: an atomic on a bit already set costs far more
@@ -491,13 +490,18 @@ __global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p,
             const uint32_t mw = p.bitmap[mn >> 5];
             const int32_t b = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
             out[v] = b;
-            if (p.perm) p.gat[p.perm[v]] = b;
             if (!fz) {
                 // a graph that computed its level 0 here has no previous level
+                bool new_min = true;
                 if (moved && !vertex_level0(p, v)) {
                     const uint32_t pm = ((p.bitmap_prev[v >> 5] >> (v & 31)) & 1u) ? (uint32_t)v : p.minof[v];
                     mv = pm != mn;
+                    new_min = mv;
                 }
+                // the locality order's copy of the level names every block by
+                // its smallest member, which only moved vertices change (a
+                // frozen block keeps its members and its smallest member)
+                if (p.perm && new_min) p.gat[p.perm[v]] = (int32_t)mn;
                 if (mn != (uint32_t)v) p.minof[v] = mn;
             }
         }
