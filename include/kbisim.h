@@ -83,7 +83,9 @@ typedef struct {
  *   use_edge_labels    pairs carry the edge label (else every label reads 0)
  *   early_stop         stop once a round keeps the block count (paper Alg. 1, the
  *                      count test); later levels are then copies
- *   load_factor        block-table load factor in (0, 0.9]; 0 -> 0.5
+ *   load_factor        block-table load factor in (0, 0.9]; 0 -> 0.5 (the table has
+ *                      a power of two of slots, at most 2^31: above 2^30 vertices it
+ *                      is fuller than asked)
  *   hub_threshold      vertices with more edges than this (in the chosen direction)
  *                      take the multi-CTA hub path; 0 -> default 1024; at most 1024
  *   hash_mode          0: full 64-bit signature hash.  1: weak hash of the previous

@@ -113,6 +113,18 @@ uint64_t next_pow2(uint64_t x) {
     return p;
 }
 
+// Block-table slots for n vertices at load factor lf: a power of two of at
+// least 1024 and at most 2^31, since a vertex's slot index is kept in the 31
+// low bits of its slot_of entry (bit 31 marks an empty signature).  Above
+// 2^30 vertices the table can thus be fuller than lf asks (it still holds
+// every block: n <= 2^31 - 2).
+uint64_t table_capacity(int64_t n, float lf) {
+    uint64_t cap = next_pow2((uint64_t)((double)std::max<int64_t>(n, 1) / (double)lf) + 1);
+    if (cap < 1024) cap = 1024;
+    if (cap > ((uint64_t)1 << 31)) cap = (uint64_t)1 << 31;
+    return cap;
+}
+
 // Device buffers of one refine call, carved from one workspace allocation.
 struct Plan {
     int64_t n = 0, m = 0, m_proc = 0;
@@ -406,9 +418,7 @@ void resolve_call_fields(Plan& P, const kb_options* opt, int rounds, bool multi,
     P.warp_verts = pick_field(opt->small_task_vertices, T ? T->small_task_vertices : 0, kb::kDefaultWarpVerts);
     float lf = opt->load_factor > 0.f ? opt->load_factor : (T ? T->load_factor : 0.f);
     if (!(lf > 0.f)) lf = 0.5f;
-    P.cap = next_pow2((uint64_t)((double)std::max<int64_t>(P.n, 1) / (double)lf) + 1);
-    if (P.cap < 1024) P.cap = 1024;
-    if (P.cap > ((uint64_t)1 << 32)) P.cap = (uint64_t)1 << 32;
+    P.cap = table_capacity(P.n, lf);
 }
 
 // `rounds`: refinement rounds the call runs (decides the automatic locality
@@ -2510,8 +2520,7 @@ kb_status kb_server_create(kb_server** out, int device, void* stream, const kb_s
     alloc((void**)&sv->slot_n, sizeof(int64_t) * (size_t)S);
     // the arena's block table and empty-signature minima, sized for a full arena
     const float lf = cfg->load_factor > 0.f ? cfg->load_factor : 0.5f;
-    sv->table_cap = next_pow2((uint64_t)((double)N / (double)lf) + 1);
-    if (sv->table_cap < 1024) sv->table_cap = 1024;
+    sv->table_cap = table_capacity(N, lf);
     alloc((void**)&sv->table, sizeof(uint64_t) * (size_t)sv->table_cap);
     alloc((void**)&sv->emin, sizeof(uint64_t) * (size_t)N);
     const size_t bwN = sizeof(uint32_t) * (size_t)((N >> 5) + 1);
