@@ -6,7 +6,8 @@ properties that hold at any size (canonical numbering, nesting, counts,
 early-stop copies), and sampled vertices -- random ones, whole sampled blocks
 and hubs -- against the CPU oracle's signature (Def. "signature") one by one:
 within the sample, two vertices share a block exactly when they share the
-previous block and the signature.
+previous block and the signature.  The levels come from a prepared graph with
+the locality order, as bench.py times them, and must equal a plain kb_refine.
 """
 import numpy as np
 import pytest
@@ -32,12 +33,25 @@ def run():
     wl = graphgen.chung_lu_torch(device="cuda:0", **cfg)
     dg = kb.DeviceGraph(wl["row_offsets"], wl["col"], wl["elabel"], wl["vlabel"])
     ctx = kb.Context(0)
-    res = ctx.refine(dg, K, kb.Options(direction=kb.DIR_OUT))
+    opts = kb.Options(direction=kb.DIR_OUT)
+    # the bench's path: a prepared graph (locality order on), then one call
+    with ctx.prepare(dg, opts) as pg:
+        assert pg.info()["reorder"] == 1
+        res = ctx.refine(pg, K, opts)
     torch.cuda.synchronize()
-    yield wl, res
+    yield wl, dg, ctx, res
     ctx.close()
     del wl, dg, res
     torch.cuda.empty_cache()
+
+
+def test_prepared_equals_plain_call(run):
+    # the prepared path (locality order on) and a plain kb_refine (off) agree
+    wl, dg, ctx, res = run
+    plain = ctx.refine(dg, K, kb.Options(direction=kb.DIR_OUT))
+    assert torch.equal(plain.levels, res.levels)
+    assert np.array_equal(plain.counts, res.counts) and plain.levels_computed == res.levels_computed
+    del plain
 
 
 def _block_minima(L, cnt):
@@ -48,7 +62,7 @@ def _block_minima(L, cnt):
 
 
 def test_levels_are_canonical_nested_partitions(run):
-    wl, res = run
+    wl, _, _, res = run
     L, counts, lc = res.levels, res.counts, res.levels_computed
     n = wl["n"]
     assert counts[0] == 5000 and 1 <= lc <= K
@@ -92,7 +106,7 @@ def _sample(wl, L_i, rng):
 
 @pytest.mark.parametrize("level", [1, 2, "last"])
 def test_sampled_keys_match_oracle(run, level):
-    wl, res = run
+    wl, _, _, res = run
     i = res.levels_computed if level == "last" else level
     rng = np.random.Generator(np.random.PCG64(100 + i))
     L_prev, L_i = res.levels[i - 1], res.levels[i]

@@ -9,6 +9,7 @@ tests/golden/make_fullsize_digests.py from oracle/ only); equal digests mean
 equal levels, element by element.  The graph is drawn on the GPU with the
 same counter-based generator the script used on the host, and its own digest
 is checked first.  On a mismatch the digests of 16 vertex ranges say where.
+Both the plain call and a prepared graph (locality order on) are checked.
 """
 import hashlib
 import json
@@ -60,14 +61,21 @@ def rdf():
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("prepared", [False, True])
 @pytest.mark.parametrize("early_stop", [True, False])
 @pytest.mark.parametrize("direction", ["out", "both"])
-def test_rdf_full_size_levels_equal_oracle(rdf, direction, early_stop):
+def test_rdf_full_size_levels_equal_oracle(rdf, direction, early_stop, prepared):
     G, dg, ctx = rdf
     K = G["k"]
     gold = G["directions"][direction]
     d = kb.DIR_OUT if direction == "out" else kb.DIR_BOTH
-    res = ctx.refine(dg, K, kb.Options(direction=d, early_stop=early_stop))
+    opts = kb.Options(direction=d, early_stop=early_stop)
+    if prepared:  # a prepared graph, with the locality order (automatic at this size)
+        with ctx.prepare(dg, opts) as pg:
+            assert pg.info()["reorder"] == 1
+            res = ctx.refine(pg, K, opts)
+    else:
+        res = ctx.refine(dg, K, opts)
     torch.cuda.synchronize()
     chunks = G["chunks"]
     for i in range(K + 1):
