@@ -536,8 +536,9 @@ kb_status kb_server_get_stats(kb_server* server, kb_server_stats* stats);
  * Its scratch is one static device array of about 33 MB inside the library,
  * which every device that loads the library keeps until the process exits.
  * The first call on a device looks up the array's device address (and sets
- * the round kernels' shared-memory attributes); make that first call before
- * any stream capture.  Every call synchronises `stream` before returning.
+ * the round kernels' shared-memory attributes).  Every call synchronises
+ * `stream` and reads results back to the host before returning, so no call
+ * can be part of a CUDA-graph capture.
  * Every call shares the array, which keeps the previous call's contents
  * (each call resets what it uses), so calls that overlap on the GPU -- from
  * several streams or threads -- race; the caller must serialise them.

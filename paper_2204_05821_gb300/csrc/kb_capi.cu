@@ -233,7 +233,7 @@ void layout_round(Plan& P) {
     P.o_slot = take(sizeof(int32_t) * (size_t)std::max<int64_t>(P.n, 1));
     P.o_table = take(P.ext_table ? 0 : sizeof(uint64_t) * (size_t)P.cap);
     P.o_bitmap = take(sizeof(uint32_t) * (size_t)nw);
-    P.o_prefix = take(sizeof(uint32_t) * (size_t)(nw + 1));
+    P.o_prefix = take(sizeof(uint2) * (size_t)(nw + 1));
     P.o_scan = take(sizeof(uint32_t) * kb::scan_tmp_words(nw));
     P.o_acc = take(sizeof(uint64_t) * H);
     P.o_cnt = take(sizeof(uint32_t) * H);
@@ -518,7 +518,7 @@ struct Prepared {
     Plan P;
     char* ws = nullptr;  // workspace base (round buffers)
     kb::RoundParams p{};
-    uint32_t* prefix = nullptr;
+    uint2* prefix = nullptr;  // rank words of the renumbering (launch_renumber)
     uint32_t* scan_tmp = nullptr;
     int64_t total_chunks = 0;
     size_t set_bytes = 0;
@@ -725,7 +725,7 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
     p.hub_acc = reinterpret_cast<uint64_t*>(ws + P.o_acc);
     p.hub_cnt = reinterpret_cast<uint32_t*>(ws + P.o_cnt);
     if (P.reorder) p.gat = reinterpret_cast<int32_t*>(ws + P.o_gat);
-    R.prefix = reinterpret_cast<uint32_t*>(ws + P.o_prefix);
+    R.prefix = reinterpret_cast<uint2*>(ws + P.o_prefix);
     R.scan_tmp = reinterpret_cast<uint32_t*>(ws + P.o_scan);
     R.total_chunks = P.n_chunks;
     R.set_bytes = sizeof(uint64_t) * (size_t)P.set_slots;

@@ -366,16 +366,20 @@ __global__ void __launch_bounds__(kScanThreads) scan_block_sums_kernel(uint32_t*
     if (threadIdx.x == 0) ctr->count = (int64_t)carry;
 }
 
+// prefix[w] = set bits before word w; with rank given instead, rank[w] =
+// (prefix[w], bitmap[w]), so a rank lookup is one 8-byte load.
 __global__ void __launch_bounds__(kScanThreads) popc_scan_kernel(const uint32_t* bitmap, int64_t nw,
-                                                                const uint32_t* block_sums, uint32_t* prefix) {
+                                                                const uint32_t* block_sums, uint32_t* prefix,
+                                                                uint2* rank) {
     __shared__ uint32_t tmp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t c[kScanItems];
+    uint32_t w[kScanItems], c[kScanItems];
     uint32_t s = 0;
 #pragma unroll
     for (int u = 0; u < kScanItems; ++u) {
         const int64_t i = base + u;
-        c[u] = i < nw ? (uint32_t)__popc(bitmap[i]) : 0u;
+        w[u] = i < nw ? bitmap[i] : 0u;
+        c[u] = (uint32_t)__popc(w[u]);
         s += c[u];
     }
     uint32_t total;
@@ -383,7 +387,12 @@ __global__ void __launch_bounds__(kScanThreads) popc_scan_kernel(const uint32_t*
 #pragma unroll
     for (int u = 0; u < kScanItems; ++u) {
         const int64_t i = base + u;
-        if (i < nw) prefix[i] = ex;
+        if (i < nw) {
+            if (rank)
+                rank[i] = make_uint2(ex, w[u]);
+            else
+                prefix[i] = ex;
+        }
         ex += c[u];
     }
 }
@@ -395,7 +404,7 @@ __global__ void __launch_bounds__(kScanThreads) popc_scan_kernel(const uint32_t*
 constexpr int kMarkCache = 1024;
 constexpr uint32_t kNoMark = 0xffffffffu;
 
-__global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const uint32_t* prefix, int32_t* out) {
+__global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const uint2* rank, int32_t* out) {
     __shared__ uint32_t s_mark[kMarkCache];
     if (p.shared) {
         for (int i = threadIdx.x; i < kMarkCache; i += blockDim.x) s_mark[i] = kNoMark;
@@ -423,8 +432,8 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
             if ((int64_t)mn >= p.n) mn = (uint32_t)v;  // only after a reported device error
             mark = mn;  // v is not the minimum: its block has another member
         }
-        const uint32_t mw = p.bitmap[mn >> 5];
-        const int32_t b = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
+        const uint2 rw = rank[mn >> 5];
+        const int32_t b = (int32_t)(rw.x + __popc(rw.y & ((1u << (mn & 31)) - 1u)));
         out[v] = b;
         if (p.perm) p.gat[p.perm[v]] = (int32_t)mn;  // the block by its smallest member
         if (p.shared) {
@@ -453,7 +462,7 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
 // warp.  Frozen vertices keep minof, and their blocks keep their shared marks
 // (the freeze pass carries them over), so only re-keyed vertices mark.  moved
 // may be null (the starting level).
-__global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p, const uint32_t* prefix, int32_t* out,
+__global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p, const uint2* rank, int32_t* out,
                                                              uint32_t* moved) {
     __shared__ uint32_t s_mark[kMarkCache];
     for (int i = threadIdx.x; i < kMarkCache; i += blockDim.x) s_mark[i] = kNoMark;
@@ -487,8 +496,8 @@ __global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p,
                     mark = kNoMark;
                 }
             }
-            const uint32_t mw = p.bitmap[mn >> 5];
-            const int32_t b = (int32_t)(prefix[mn >> 5] + __popc(mw & ((1u << (mn & 31)) - 1u)));
+            const uint2 rw = rank[mn >> 5];
+            const int32_t b = (int32_t)(rw.x + __popc(rw.y & ((1u << (mn & 31)) - 1u)));
             out[v] = b;
             if (!fz) {
                 // a graph that computed its level 0 here has no previous level
@@ -812,15 +821,16 @@ __global__ void __launch_bounds__(256) clear_hub_sets_kernel(const RoundParams p
 
 // rank of every graph's first vertex (the first vertex of a graph is always
 // the smallest member of its block)
-__global__ void graph_base_kernel(const RoundParams p, const uint32_t* prefix) {
+__global__ void graph_base_kernel(const RoundParams p, const uint2* rank) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g > p.n_graphs) return;
     const int64_t x = p.voff[g];
     uint32_t r;
     if (x >= p.n) {
-        r = prefix[(p.n >> 5) + 1];
+        r = rank[(p.n >> 5) + 1].x;
     } else {
-        r = prefix[x >> 5] + __popc(p.bitmap[x >> 5] & ((1u << (x & 31)) - 1u));
+        const uint2 rw = rank[x >> 5];
+        r = rw.x + __popc(rw.y & ((1u << (x & 31)) - 1u));
     }
     p.gbase_cur[g] = r;
 }
@@ -858,8 +868,8 @@ __global__ void vertex_graph_kernel(const int64_t* voff, int32_t G, int64_t n, i
     for (int64_t v = voff[g] + threadIdx.x; v < voff[g + 1]; v += blockDim.x) vgraph[v] = g;
 }
 
-__global__ void write_total_kernel(uint32_t* prefix, int64_t nw, const Counters* ctr) {
-    prefix[nw] = (uint32_t)ctr->count;
+__global__ void write_total_kernel(uint2* rank, int64_t nw, const Counters* ctr) {
+    rank[nw] = make_uint2((uint32_t)ctr->count, 0u);
 }
 
 __global__ void fill_i32_kernel(int32_t* out, int64_t n, int32_t value) {
@@ -972,27 +982,30 @@ void launch_bitmap_rank(const uint32_t* bitmap, int64_t nw, uint32_t* scan_tmp, 
     const int64_t nb = (nw + kScanTile - 1) / kScanTile;
     popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(bitmap, nw, scan_tmp);
     scan_block_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, nb, ctr);
-    popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(bitmap, nw, scan_tmp, prefix);
+    popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(bitmap, nw, scan_tmp, prefix, nullptr);
 }
 
-void launch_renumber(const RoundParams& p, uint32_t* prefix, uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
+void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
     const int64_t nw = (p.n >> 5) + 1;
-    launch_bitmap_rank(p.bitmap, nw, scan_tmp, prefix, p.ctr, s);
+    const int64_t nb = (nw + kScanTile - 1) / kScanTile;
+    popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp);
+    scan_block_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, nb, p.ctr);
+    popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp, nullptr, rank);
     if (batched(p)) {
-        // prefix[nw] (one past the last word) is not written by the scan: the
-        // total sits in the counters; graph_base_kernel reads prefix only for
-        // x < n, and takes the total from gbase of the last graph otherwise.
-        write_total_kernel<<<1, 1, 0, s>>>(prefix, nw, p.ctr);
-        graph_base_kernel<<<(p.n_graphs + 1 + 255) / 256, 256, 0, s>>>(p, prefix);
+        // rank[nw] (one past the last word) is not written by the scan: the
+        // total sits in the counters, and graph_base_kernel reads it there
+        // for a graph that starts at n.
+        write_total_kernel<<<1, 1, 0, s>>>(rank, nw, p.ctr);
+        graph_base_kernel<<<(p.n_graphs + 1 + 255) / 256, 256, 0, s>>>(p, rank);
     }
     if (p.minof) {
         if (p.moved && p.perm) cudaMemsetAsync(p.moved, 0, sizeof(uint32_t) * (size_t)nw, s);
-        if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out, p.moved);
+        if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, rank, out, p.moved);
         if (p.moved) count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(
             p.moved, nw, &p.ctr->moved);
         return;
     }
-    if (p.n > 0) assign_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, prefix, out);
+    if (p.n > 0) assign_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, rank, out);
 }
 
 void launch_carry_minima(const RoundParams& p, cudaStream_t s) {

@@ -26,7 +26,7 @@ constexpr size_t kOffSlot = kOffTable + up(sizeof(uint64_t) * kTableCap);
 constexpr size_t kOffEmin = kOffSlot + up(sizeof(int32_t) * kMaxVertices);
 constexpr size_t kOffBitmap = kOffEmin + up(sizeof(uint64_t) * kMaxVertices);
 constexpr size_t kOffPrefix = kOffBitmap + up(sizeof(uint32_t) * kWords);
-constexpr size_t kOffScan = kOffPrefix + up(sizeof(uint32_t) * (kWords + 1));
+constexpr size_t kOffScan = kOffPrefix + up(sizeof(uint2) * (kWords + 1));  // rank words
 constexpr size_t kScanWords = (size_t)((kWords + 4095) / 4096) + 1;
 constexpr size_t kOffMed = kOffScan + up(sizeof(uint32_t) * kScanWords);
 constexpr size_t kScratchBytes = kOffMed + up(sizeof(int32_t) * kMaxVertices);
@@ -172,7 +172,7 @@ extern "C" kb_status kb_refine_round_noalloc(void* stream, const kb_graph* g, co
 
     kb::launch_small_round(p, false, false, s);
     kb::launch_medium_round(p, s);
-    kb::launch_renumber(p, reinterpret_cast<uint32_t*>(base + kOffPrefix), reinterpret_cast<uint32_t*>(base + kOffScan),
+    kb::launch_renumber(p, reinterpret_cast<uint2*>(base + kOffPrefix), reinterpret_cast<uint32_t*>(base + kOffScan),
                         out, s);
     NA_CUDA(cudaGetLastError());
     NA_CUDA(cudaMemcpyAsync(&host_ctr, ctr, sizeof(host_ctr), cudaMemcpyDeviceToHost, s));

@@ -107,12 +107,15 @@ template <bool kLevel0, bool kCompact>
 __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_round_kernel(const RoundParams p) {
     __shared__ uint64_t s_pairs[kSmallThreads];
     __shared__ JoinMap M;
+    __shared__ unsigned long long s_l0[kLevel0 ? 256 : 1];
     const int lane = threadIdx.x & 31;
     uint64_t* wpairs = s_pairs + (threadIdx.x & ~31);
     for (int i = threadIdx.x; i < kMapCap; i += kSmallThreads) {
         M.key[i] = kMapEmpty;
         M.vmin[i] = 0xffffffffu;
     }
+    if (kLevel0)
+        for (int i = threadIdx.x; i < 256; i += kSmallThreads) s_l0[i] = ~0ull;
     __syncthreads();
 
     const int64_t cta_base = (int64_t)blockIdx.x * kSmallWarps * p.warp_verts;
@@ -290,6 +293,24 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
             wpairs[lane] = pr;  // lanes >= E hold unused values
             __syncwarp();
         }
+        // Level 0 of one graph: the key is the label alone, so a slot that a
+        // lane of this CTA found (or claimed) for a label serves later lanes
+        // with the same label without a probe or a compare (a direct-mapped
+        // cache of (label, slot) words).
+        uint32_t l0c = 0;
+        bool resolved = false;
+        if (kLevel0 && !batched(p)) {
+            l0c = ((uint32_t)own * 2654435761u) >> 24;
+            if (pending) {
+                const unsigned long long e = s_l0[l0c];
+                if (e != ~0ull && (uint32_t)(e >> 32) == (uint32_t)own) {
+                    pos = (uint32_t)e;
+                    if (!map_join(M, pos, hi, (uint32_t)v)) flush_join(p, pos, hi, (uint32_t)v);
+                    p.slot_of[v] = (int32_t)pos;
+                    pending = false;
+                }
+            }
+        }
         const unsigned vmask = cd >= 32 ? kFull : ((1u << cd) - 1u);
         while (__any_sync(kFull, pending)) {
             if (!pending) continue;
@@ -346,10 +367,13 @@ __global__ void __launch_bounds__(kSmallThreads, KB_SMALL_MIN_BLOCKS) small_roun
                 if (!map_join(M, pos, hi, (uint32_t)v)) flush_join(p, pos, hi, (uint32_t)v);
                 p.slot_of[v] = (int32_t)pos;
                 pending = false;
+                resolved = true;
             } else {
                 pos = (pos + 1) & p.mask;
             }
         }
+        if (kLevel0 && !batched(p) && (resolved || inserted))
+            s_l0[l0c] = ((unsigned long long)(uint32_t)own << 32) | (uint32_t)pos;
         // new-block owners of this window: one atomicXor per bitmap word (the
         // window's vertices lie in at most kLook / 32 + 1 words)
         if (!kCompact) {
