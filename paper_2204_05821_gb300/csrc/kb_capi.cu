@@ -62,6 +62,8 @@ struct kb_context {
     size_t upd_buf_bytes = 0;
     unsigned long long* d_work = nullptr;  // |W| of the current round
     cudaStream_t cap_stream = nullptr;  // non-default stream used only to capture CUDA graphs
+    cudaStream_t copy_stream = nullptr;  // level rows back to the host (kb_refine_host)
+    cudaEvent_t row_ev = nullptr;
     // timing: CUDA events per kernel family; with work, also the vertices and
     // edges every round re-keys (one extra pass over the row offsets a round)
     bool timing = false;
@@ -845,7 +847,30 @@ struct LevelRows {
     int32_t* levels = nullptr;
     int32_t* ping[2] = {nullptr, nullptr};
     int64_t n = 0;
+    // optional host copy of `levels` (kb_refine_host): every row is copied on
+    // a second stream as soon as it is final, overlapping the later rounds
+    int32_t* host = nullptr;
     int32_t* row(int i) const { return levels ? levels + (size_t)i * (size_t)n : ping[i & 1]; }
+};
+
+// Queue the device-to-host copy of rows first..last (final on ctx->stream).
+kb_status emit_rows(kb_context* ctx, const LevelRows& rows, int first, int last) {
+    if (!rows.host || rows.n == 0 || last < first) return KB_OK;
+    KB_CUDA(ctx, cudaEventRecord(ctx->row_ev, ctx->stream));
+    KB_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->row_ev, 0));
+    KB_CUDA(ctx, cudaMemcpyAsync(rows.host + (size_t)first * (size_t)rows.n, rows.row(first),
+                                 sizeof(int32_t) * (size_t)rows.n * (size_t)(last - first + 1), cudaMemcpyDeviceToHost,
+                                 ctx->copy_stream));
+    return KB_OK;
+}
+
+// Waits for the row copies when leaving refine_core by any path, so no copy
+// into the caller's host buffer outlives the call.
+struct RowCopyGuard {
+    cudaStream_t cs;
+    ~RowCopyGuard() {
+        if (cs) cudaStreamSynchronize(cs);
+    }
 };
 
 // The refinement driver shared by kb_refine, kb_refine_from and
@@ -867,6 +892,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     }
     cudaStream_t s = ctx->stream;
     ctx->round_keyed.clear();
+    RowCopyGuard copies{rows.host ? ctx->copy_stream : nullptr};
     Prepared R;
     KB_TRY(prepare(ctx, g, opt, R, k - i_start, false, pg));
     kb::RoundParams& p = R.p;
@@ -911,6 +937,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     }
     if (counts) counts[i_start] = prev_count;
     if (last_count) *last_count = prev_count;
+    KB_TRY(emit_rows(ctx, rows, i_start, i_start));
 
     // ---- refinement rounds
     for (int i = i_start + 1; i <= k; ++i) {
@@ -933,6 +960,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         if (ctx->work) kb::launch_round_work(p, s);
         T.begin(KB_KERNEL_RENUMBER);
         kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
+        KB_TRY(emit_rows(ctx, rows, i, i));
         // the next round's frozen blocks: singletons; a block formed by this
         // round that holds an edgeless vertex holds only edgeless vertices with
         // one previous block; and clean blocks, none of whose members has an
@@ -969,7 +997,10 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
             // stratified levels only split blocks, so an unchanged count means an
             // unchanged partition; generic CSE levels were compared entry by entry
             if (stopped_stable) *stopped_stable = true;
-            if (!fixpoint && i < k) kb::launch_copy_rows(rows.levels, n, i, i + 1, k, s);
+            if (!fixpoint && i < k) {
+                kb::launch_copy_rows(rows.levels, n, i, i + 1, k, s);
+                KB_TRY(emit_rows(ctx, rows, i + 1, k));
+            }
             if (counts)
                 for (int j = i + 1; j <= k; ++j) counts[j] = c;
             KB_CUDA(ctx, cudaGetLastError());
@@ -983,7 +1014,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
 
 kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
                       int k, int32_t* levels, int64_t* counts, int* levels_computed,
-                      const kb_prepared* pg = nullptr);
+                      const kb_prepared* pg = nullptr, int32_t* host_levels = nullptr);
 
 // Incremental refinement (kb_refine_update): levels holds the levels of the
 // graph before the change (same options); each round re-keys only the work set
@@ -1149,7 +1180,8 @@ kb_status update_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
 }
 
 kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt, const int32_t* start, int i_start,
-                      int k, int32_t* levels, int64_t* counts, int* levels_computed, const kb_prepared* pg) {
+                      int k, int32_t* levels, int64_t* counts, int* levels_computed, const kb_prepared* pg,
+                      int32_t* host_levels) {
     KB_TRY(check_graph(ctx, g, opt, k));
     if (i_start < 0 || i_start > k) return fail(ctx, KB_ERR_INVALID_ARG, "i_start must be in [0, k]");
     if (!counts) return fail(ctx, KB_ERR_INVALID_ARG, "counts is NULL");
@@ -1159,6 +1191,11 @@ kb_status refine_impl(kb_context* ctx, const kb_graph* g, const kb_options* opt,
     LevelRows rows;
     rows.levels = levels;
     rows.n = g->n;
+    rows.host = host_levels;
+    if (host_levels && !ctx->copy_stream) {
+        KB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        KB_CUDA(ctx, cudaEventCreateWithFlags(&ctx->row_ev, cudaEventDisableTiming));
+    }
     return refine_core(ctx, g, opt, start, i_start, k, rows, counts, levels_computed, nullptr, nullptr, pg);
 }
 
@@ -2097,6 +2134,8 @@ kb_status kb_destroy(kb_context* ctx) {
     cudaFree(ctx->upd_buf);
     cudaFree(ctx->d_work);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->row_ev) cudaEventDestroy(ctx->row_ev);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     delete ctx;
@@ -2291,9 +2330,8 @@ kb_status kb_refine_host(kb_context* ctx, const kb_graph* g, const kb_options* o
     dg.edge_labels = el ? reinterpret_cast<const int32_t*>(b + o_el) : nullptr;
     dg.vertex_labels = vl ? reinterpret_cast<const int32_t*>(b + o_vl) : nullptr;
     int32_t* dlev = reinterpret_cast<int32_t*>(b + o_lv);
-    KB_TRY(refine_impl(ctx, &dg, opt, nullptr, 0, k, dlev, counts, levels_computed));
-    if (n > 0)
-        KB_CUDA(ctx, cudaMemcpyAsync(levels, dlev, sizeof(int32_t) * (size_t)n * (size_t)(k + 1), cudaMemcpyDeviceToHost, s));
+    // every level row goes back to the host as soon as it is final
+    KB_TRY(refine_impl(ctx, &dg, opt, nullptr, 0, k, dlev, counts, levels_computed, nullptr, levels));
     KB_CUDA(ctx, cudaStreamSynchronize(s));
     return KB_OK;
 }

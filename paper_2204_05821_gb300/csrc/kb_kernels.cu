@@ -132,17 +132,25 @@ __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParam
         if (i >= nu) continue;
         const uint64_t pr = prs[u];
         uint64_t slot = slots[u], old = olds[u];
+        bool placed = false;
         for (uint64_t t = 0; t < gcap; ++t) {
             if (old == kEmptyPair) {
                 lacc += pair_mix(pr);
                 ++lnew;
+                placed = true;
                 break;
             }
-            if (old == pr) break;
+            if (old == pr) {
+                placed = true;
+                break;
+            }
             slot = slot + 1 == gcap ? 0 : slot + 1;
             old = atomicCAS(reinterpret_cast<unsigned long long*>(&gset[slot]), (unsigned long long)kEmptyPair,
                             (unsigned long long)pr);
         }
+        // sets hold 1.5 x the hub's degree: a pair that finds no slot means
+        // corrupted sets (reported as a device check failure)
+        if (!placed) set_error(p.ctr, kErrHubSet);
     }
     // CTA sums of the pairs new to the hub: hash and count
 #pragma unroll

@@ -389,11 +389,16 @@ def test_initial_partition(ctx, er_tiny):
 
 
 def test_host_buffers(ctx, er_tiny):
+    # every row reaches the host buffer (rows are copied as they become final,
+    # early-stop copies included), whatever the output held before
     for d in (0, 2):
-        L, C, lc = oracle.refine_graph(er_tiny, d, True, True, k=10)
-        res = ctx.refine_host(er_tiny.row_offsets, er_tiny.col, er_tiny.elabel, er_tiny.vlabel, 10,
-                              kb.Options(direction=d))
-        assert np.array_equal(res.levels, L) and np.array_equal(res.counts, C) and res.levels_computed == lc
+        for early, k in ((True, 10), (False, 6), (True, 0)):
+            L, C, lc = oracle.refine_graph(er_tiny, d, True, True, k=k, early_stop=early)
+            out = np.full((k + 1, er_tiny.n), -1, dtype=np.int32)
+            res = ctx.refine_host(er_tiny.row_offsets, er_tiny.col, er_tiny.elabel, er_tiny.vlabel, k,
+                                  kb.Options(direction=d, early_stop=early), out=out)
+            assert np.array_equal(out, L) and np.array_equal(res.levels, L), (d, early, k)
+            assert np.array_equal(res.counts, C) and res.levels_computed == lc
 
 
 def test_torch_workspace(er_tiny):
