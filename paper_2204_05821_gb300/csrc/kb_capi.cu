@@ -538,6 +538,7 @@ struct Prepared {
     uint32_t* moved = nullptr;
     uint32_t* mark = nullptr;
     bool compact = false;  // small-kernel windows skip frozen vertices (many frozen)
+    bool sparse = false;   // fewer than 1/64 of the vertices refine: long warp tasks
     // A caller-held block table (ext_cap slots) and empty-signature minima
     // (at least n entries) that outlive one prepare: they are neither carved
     // from the workspace nor cleared, and the table epoch carries on (the
@@ -813,7 +814,15 @@ kb_status launch_round_body(kb_context* ctx, Prepared& R, cudaStream_t s, Timer*
     if (hub && !p.frozen && R.set_bytes) KB_CUDA(ctx, cudaMemsetAsync(p.hub_sets, 0xff, R.set_bytes, s));
     if (T) T->end();
     if (T) T->begin(KB_KERNEL_SMALL);
-    kb::launch_small_round(p, false, R.compact, s);
+    if (R.sparse) {
+        // few vertices refine: long warp tasks, so that far fewer CTAs set up
+        // and flush a join map for a handful of vertices each
+        kb::RoundParams q = p;
+        q.warp_verts = 4096;
+        kb::launch_small_round(q, false, true, s);
+    } else {
+        kb::launch_small_round(p, false, R.compact, s);
+    }
     if (T) T->end();
     if (med) {
         if (T) T->begin(KB_KERNEL_MEDIUM);
@@ -923,6 +932,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         KB_TRY(device_error(ctx));
         prev_count = ctx->h_ctr->count;
         R.compact = R.P.freeze && ctx->h_ctr->frozen * 4 > n;
+        R.sparse = R.P.freeze && (n - ctx->h_ctr->frozen) * 64 < n;
         R.med_on = ctx->h_ctr->med_on > 0;
         R.hub_on = ctx->h_ctr->hub_on > 0;
     } else {
@@ -967,9 +977,11 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         // edge to a vertex whose smallest block member this round changed
         if (p.shared) {
             KB_CUDA(ctx, cudaMemsetAsync(R.mark, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
-            kb::launch_dirty_blocks(p, R.edgeless, R.moved, out, kb::kMaxHubThreshold, R.mark, s);
+            // under early stop a round that keeps the count is the last one
+            const int64_t stable = (opt->early_stop || fixpoint) ? prev_count : -1;
+            kb::launch_dirty_blocks(p, R.edgeless, R.moved, out, kb::kMaxHubThreshold, R.mark, s, stable);
             kb::launch_freeze_clean(n, p.bitmap, p.shared, R.edgeless, out, R.mark, R.frozen, R.frozen_min,
-                                    ctx->d_ctr, s);
+                                    ctx->d_ctr, s, nullptr, nullptr, stable);
             kb::launch_count_refining(p, R.frozen, ctx->d_ctr, s);
         }
         T.end();
@@ -984,6 +996,7 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         }
         // compacted small-kernel windows pay once a quarter of the vertices are frozen
         R.compact = R.P.freeze && ctx->h_ctr->frozen * 4 > n;
+        R.sparse = R.P.freeze && (n - ctx->h_ctr->frozen) * 64 < n;
         R.med_on = ctx->h_ctr->med_on > 0;
         R.hub_on = ctx->h_ctr->hub_on > 0;
         ctx->round_ms.push_back(T.collect());

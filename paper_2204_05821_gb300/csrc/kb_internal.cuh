@@ -217,8 +217,10 @@ void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream
 // level-i id; a vertex above max_scan edges counts as such).  Only vertices
 // that are neither alone in their block (bitmap & ~shared) nor edgeless are
 // scanned, and nothing when more than an eighth of the vertices moved.
+// stable_count >= 0: the pass does nothing when this round's count equals it
+// (a stable round under early stop is the last one).
 void launch_dirty_blocks(const RoundParams& p, const uint32_t* edgeless, const uint32_t* moved, const int32_t* level,
-                         int32_t max_scan, uint32_t* mark, cudaStream_t s);
+                         int32_t max_scan, uint32_t* mark, cudaStream_t s, int64_t stable_count = -1);
 // After the renumbering (single-graph stratified rounds): the frozen blocks
 // of the next round.  A vertex is frozen when it is alone in its block (a
 // minimum in bitmap that no other vertex marked in shared), edgeless
@@ -233,7 +235,7 @@ void launch_dirty_blocks(const RoundParams& p, const uint32_t* edgeless, const u
 void launch_freeze_clean(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
                          const int32_t* level, const uint32_t* mark, uint32_t* frozen, uint32_t* frozen_min,
                          Counters* ctr, cudaStream_t s, const int32_t* vgraph = nullptr,
-                         const uint8_t* gmode = nullptr);
+                         const uint8_t* gmode = nullptr, int64_t stable_count = -1);
 // Clear bits a..b-1 of a bitmap.
 void launch_clear_bits(uint32_t* words, int64_t a, int64_t b, cudaStream_t s);
 // The vertices this round re-keys (not in p.frozen) and their edges, per

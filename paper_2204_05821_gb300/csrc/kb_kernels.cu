@@ -586,8 +586,9 @@ __device__ __forceinline__ bool few_moved(const RoundParams& p) { return p.ctr->
 
 __global__ void __launch_bounds__(256) dirty_blocks_kernel(const RoundParams p, const uint32_t* edgeless,
                                                             const uint32_t* moved, const int32_t* level,
-                                                            int32_t max_scan, uint32_t* mark) {
+                                                            int32_t max_scan, uint32_t* mark, int64_t stable_count) {
     if (!few_moved(p)) return;
+    if (stable_count >= 0 && p.ctr->count == stable_count) return;  // the last round: nothing follows
     const int lane = threadIdx.x & 31;
     const int64_t nw = (p.n >> 5) + 1;
     const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
@@ -635,12 +636,13 @@ __global__ void __launch_bounds__(256) freeze_clean_kernel(int64_t n, const uint
                                                             const uint32_t* edgeless, const int32_t* level,
                                                             const uint32_t* mark, uint32_t* frozen,
                                                             uint32_t* frozen_min, Counters* ctr, const int32_t* vgraph,
-                                                            const uint8_t* gmode) {
+                                                            const uint8_t* gmode, int64_t stable_count) {
     __shared__ uint32_t s_clean[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t nw = (n >> 5) + 1;
     const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * 32;
     if (w0 >= nw) return;  // uniform over the warp
+    if (stable_count >= 0 && ctr->count == stable_count) return;  // the last round: nothing follows
     if (mark && ctr->moved * 8 > n) mark = nullptr;  // the dirty pass scanned nothing
     const int64_t w = w0 + lane;
     uint32_t b = 0, sh = 0, e = 0, c = 0;
@@ -924,19 +926,21 @@ void launch_clear_hub_sets(const RoundParams& p, int64_t total_slots, cudaStream
 }
 
 void launch_dirty_blocks(const RoundParams& p, const uint32_t* edgeless, const uint32_t* moved, const int32_t* level,
-                         int32_t max_scan, uint32_t* mark, cudaStream_t s) {
+                         int32_t max_scan, uint32_t* mark, cudaStream_t s, int64_t stable_count) {
     if (p.n <= 0) return;
     const int64_t warps = ((p.n >> 5) + 1 + 31) / 32;  // 32 bitmap words each
-    dirty_blocks_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(p, edgeless, moved, level, max_scan, mark);
+    dirty_blocks_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(p, edgeless, moved, level, max_scan, mark,
+                                                                     stable_count);
 }
 
 void launch_freeze_clean(int64_t n, const uint32_t* bitmap, uint32_t* shared, const uint32_t* edgeless,
                          const int32_t* level, const uint32_t* mark, uint32_t* frozen, uint32_t* frozen_min,
-                         Counters* ctr, cudaStream_t s, const int32_t* vgraph, const uint8_t* gmode) {
+                         Counters* ctr, cudaStream_t s, const int32_t* vgraph, const uint8_t* gmode,
+                         int64_t stable_count) {
     if (n <= 0) return;
     const int64_t warps = ((n >> 5) + 1 + 31) / 32;  // 32 bitmap words each
     freeze_clean_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(n, bitmap, shared, edgeless, level, mark, frozen,
-                                                                     frozen_min, ctr, vgraph, gmode);
+                                                                     frozen_min, ctr, vgraph, gmode, stable_count);
     const int64_t nw = (n >> 5) + 1;
     count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(frozen, nw, &ctr->frozen);
 }
