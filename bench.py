@@ -47,9 +47,9 @@ METRIC = "k-bisim edges/s per round"
 # must match.
 KERNEL_HEADERS = ("paper_2204_05821_gb300/csrc/kb_device.cuh", "paper_2204_05821_gb300/csrc/kb_internal.cuh")
 TRAFFIC_PER_ALGO_BYTE = {
-    "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "45283f75d524238d1ecc312aa7a09d2bc0d3f16c", 2.481),
-    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "4c39faee6108619951a26d9486dc1f3c088b4893", 6.909),
-    "medium": ("paper_2204_05821_gb300/csrc/kb_medium.cu", "b84b91b2680bc39015fe4214f4b73893a0d48428", 2.066),
+    "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "11bf5728efbba3d990c3e2002a3735c0fad7e8f7", 2.206),
+    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "67ed725f886db0a4b4a94df68f4b390e3a2596bb", 5.504),
+    "medium": ("paper_2204_05821_gb300/csrc/kb_medium.cu", "95201ca2b41d3a9fb6af3239846eb6557252be28", 1.964),
 }
 
 
