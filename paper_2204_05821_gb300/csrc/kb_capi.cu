@@ -1426,12 +1426,14 @@ kb_status batch_impl(kb_context* ctx, const kb_graph* g, const int64_t* voff_h, 
             p.gbase_prev = bases + (size_t)(i - 1) * (size_t)(G + 1);
             p.gbase_cur = bases + (size_t)i * (size_t)(G + 1);
             // frozen blocks as in a single-graph call (blocks never span
-            // graphs); the small kernel keeps consecutive windows and the
-            // medium and hub kernels always launch (no host reads inside the
-            // captured rounds)
+            // graphs); the medium and hub kernels always launch (no host
+            // reads inside the captured rounds)
             p.frozen = R.frozen;
             p.frozen_min = R.frozen_min;
             p.moved = R.moved;
+            // from round 2 on, windows packed from the vertices that refine
+            // (frozen blocks and stopped graphs take no lane)
+            R.compact = i >= 2;
             int32_t* out = levels + (size_t)i * (size_t)n;
             st = launch_round_body(ctx, R, cs, nullptr);
             if (st != KB_OK) break;

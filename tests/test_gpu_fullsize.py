@@ -9,9 +9,12 @@ within the sample, two vertices share a block exactly when they share the
 previous block and the signature.  The levels come from a prepared graph with
 the locality order, as bench.py times them, and must equal a plain kb_refine.
 """
+import os
+
 import numpy as np
 import pytest
 
+import cpu_parallel
 import graphgen
 import oracle
 
@@ -136,3 +139,26 @@ def test_sampled_keys_match_oracle(run, level):
         assert id_to_key.setdefault(b, key) == key, ("one block, different keys", v, i)
     # the sample must contain both shared and separate blocks to mean anything
     assert len(id_to_key) > 100 and len(id_to_key) < len(vs)
+
+
+def _host_bytes():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+def test_every_level_equals_the_openmp_implementation(run):
+    # A cross-check over all 2e8 vertices and every level: the multi-core CPU
+    # implementation (cpu_parallel/, written apart from the library and
+    # compared with the oracle on smaller graphs in test_cpu_parallel.py)
+    # refines the same graph, and every id of every level must agree.
+    if _host_bytes() < 120e9:
+        pytest.skip("the CPU run on the 2e9-edge graph needs about 70 GB of host memory")
+    wl, _, _, res = run
+    host = [wl[name].cpu().numpy() for name in ("row_offsets", "col", "elabel", "vlabel")]
+    L, C, lc = cpu_parallel.refine(wl["n"], host[0], host[1], host[2], host[3], 0, True, True, k=K)
+    del host
+    assert np.array_equal(res.counts, C) and res.levels_computed == lc
+    for i in range(K + 1):
+        assert np.array_equal(res.levels[i].cpu().numpy(), L[i]), i
