@@ -82,10 +82,15 @@ __device__ __forceinline__ bool map_join(JoinMap& M, uint64_t key, uint32_t hi, 
 }
 
 // Global atomicMin of a CTA's smallest joining vertex, with minimum toggles.
+// A block's minimum only decreases during a round, so a read that finds it at
+// or below v makes the atomic (and its toggles) a no-op, and it is skipped:
+// hot keys would otherwise take one serialised atomic per CTA.
 __device__ __forceinline__ void flush_join(const RoundParams& p, uint64_t key, uint32_t hi, uint32_t v) {
     if (key & kEmptyKeyBit) {
         const int32_t own = (int32_t)(uint32_t)key;
         const uint64_t want = ((uint64_t)p.ehigh << 32) | v;
+        const uint64_t seen = volatile_load(&p.emin[own]);
+        if ((uint32_t)(seen >> 32) == p.ehigh && (uint32_t)seen <= v) return;  // minima only decrease
         const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(&p.emin[own]), (unsigned long long)want);
         if ((uint32_t)(old >> 32) != p.ehigh) {
             toggle_min(p.bitmap, v);
@@ -95,6 +100,8 @@ __device__ __forceinline__ void flush_join(const RoundParams& p, uint64_t key, u
         }
     } else {
         const uint64_t want = ((uint64_t)hi << 32) | v;
+        const uint64_t seen = volatile_load(&p.table[key]);
+        if ((uint32_t)(seen >> 32) == hi && (uint32_t)seen <= v) return;  // minima only decrease
         const uint64_t old = atomicMin(reinterpret_cast<unsigned long long*>(&p.table[key]), (unsigned long long)want);
         if (v < (uint32_t)old) {
             toggle_min(p.bitmap, v);
