@@ -48,7 +48,7 @@ METRIC = "k-bisim edges/s per round"
 KERNEL_HEADERS = ("paper_2204_05821_gb300/csrc/kb_device.cuh", "paper_2204_05821_gb300/csrc/kb_internal.cuh")
 TRAFFIC_PER_ALGO_BYTE = {
     "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "11bf5728efbba3d990c3e2002a3735c0fad7e8f7", 2.206),
-    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "67ed725f886db0a4b4a94df68f4b390e3a2596bb", 5.504),
+    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "1e804b0e6e827db39309b799aefc5ed8b439450b", 5.520),
     "medium": ("paper_2204_05821_gb300/csrc/kb_medium.cu", "95201ca2b41d3a9fb6af3239846eb6557252be28", 1.964),
 }
 
