@@ -969,7 +969,9 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         KB_TRY(launch_round_body(ctx, R, s, &T));
         if (ctx->work) kb::launch_round_work(p, s);
         T.begin(KB_KERNEL_RENUMBER);
-        kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s);
+        // under early stop a round that keeps the count is the last one
+        const int64_t stable = (opt->early_stop || fixpoint) && !R.P.subject ? prev_count : -1;
+        kb::launch_renumber(p, R.prefix, R.scan_tmp, out, s, stable);
         KB_TRY(emit_rows(ctx, rows, i, i));
         // the next round's frozen blocks: singletons; a block formed by this
         // round that holds an edgeless vertex holds only edgeless vertices with
@@ -977,8 +979,6 @@ kb_status refine_core(kb_context* ctx, const kb_graph* g, const kb_options* opt,
         // edge to a vertex whose smallest block member this round changed
         if (p.shared) {
             KB_CUDA(ctx, cudaMemsetAsync(R.mark, 0, sizeof(uint32_t) * (size_t)((n >> 5) + 1), s));
-            // under early stop a round that keeps the count is the last one
-            const int64_t stable = (opt->early_stop || fixpoint) ? prev_count : -1;
             kb::launch_dirty_blocks(p, R.edgeless, R.moved, out, kb::kMaxHubThreshold, R.mark, s, stable);
             kb::launch_freeze_clean(n, p.bitmap, p.shared, R.edgeless, out, R.mark, R.frozen, R.frozen_min,
                                     ctx->d_ctr, s, nullptr, nullptr, stable);

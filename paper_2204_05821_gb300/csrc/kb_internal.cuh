@@ -257,7 +257,10 @@ void launch_hub_chunk(const RoundParams& p, int64_t total_chunks, cudaStream_t s
 void launch_hub_final(const RoundParams& p, cudaStream_t s);
 // Canonical renumbering: prefix of block minima, then ids.
 // rank: (n/32 + 2) words, rank[w] = (minima before word w, minima bits of word w).
-void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int32_t* out, cudaStream_t s);
+// stable_count >= 0 (frozen-block rounds under early stop): a round whose
+// count equals it copies the previous level (it is the last round).
+void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int32_t* out, cudaStream_t s,
+                     int64_t stable_count = -1);
 size_t scan_tmp_words(int64_t n_items);
 void launch_fill_i32(int32_t* out, int64_t n, int32_t value, cudaStream_t s);
 // Batched runs: inactive graphs keep the block minima of the previous level.

@@ -471,8 +471,16 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
 // (the freeze pass carries them over), so only re-keyed vertices mark.  moved
 // may be null (the starting level).
 __global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p, const uint2* rank, int32_t* out,
-                                                             uint32_t* moved) {
+                                                             uint32_t* moved, int64_t stable_count) {
     __shared__ uint32_t s_mark[kMarkCache];
+    if (stable_count >= 0 && p.ctr->count == stable_count) {
+        // The round kept the block count: blocks only split, so it kept every
+        // block and its ids are the previous level's.  Under early stop it is
+        // the last round, and nothing else of it is needed.
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) out[v] = p.prev[v];
+        return;
+    }
     for (int i = threadIdx.x; i < kMarkCache; i += blockDim.x) s_mark[i] = kNoMark;
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -997,7 +1005,8 @@ void launch_bitmap_rank(const uint32_t* bitmap, int64_t nw, uint32_t* scan_tmp, 
     popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(bitmap, nw, scan_tmp, prefix, nullptr);
 }
 
-void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
+void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int32_t* out, cudaStream_t s,
+                     int64_t stable_count) {
     const int64_t nw = (p.n >> 5) + 1;
     const int64_t nb = (nw + kScanTile - 1) / kScanTile;
     popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp);
@@ -1012,7 +1021,7 @@ void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int3
     }
     if (p.minof) {
         if (p.moved && p.perm) cudaMemsetAsync(p.moved, 0, sizeof(uint32_t) * (size_t)nw, s);
-        if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, rank, out, p.moved);
+        if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, rank, out, p.moved, stable_count);
         if (p.moved) count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(
             p.moved, nw, &p.ctr->moved);
         return;
