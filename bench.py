@@ -388,13 +388,14 @@ def run_ours(args, rank, world, local):
                 "per_launch_ms": {kname: fam_ms[kname] / max(1, fam_n[kname]) for kname in fam_ms}}
     # our kernels per family event: the medium family is a warp kernel and a
     # CTA kernel, the hub-chunk family clears the refining hubs' sets first,
-    # renumbering is the 3-kernel rank scan, the assignment, the moved count,
-    # the dirty, freeze and frozen-count passes and the refining count;
-    # "other" is memsets only; per call add level 0 (small kernel, rank scan,
-    # assignment, freeze, frozen count, refining count); the setup kernels ran
-    # once, in kb_graph_prepare
-    per_event = {"small": 1, "medium": 2, "hub_chunk": 2, "hub_final": 1, "renumber": 9, "other": 0}
-    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 8 * args.steps
+    # renumbering is the 3-kernel rank scan, the stable-round copy, the
+    # assignment, the moved count, the dirty, freeze and frozen-count passes
+    # and the refining count; "other" is memsets only; per call add level 0
+    # over the small labels (label minima, minima marks, rank scan, label ids,
+    # assignment, freeze, frozen count, refining count); the setup kernels
+    # ran once, in kb_graph_prepare
+    per_event = {"small": 1, "medium": 2, "hub_chunk": 2, "hub_final": 1, "renumber": 10, "other": 0}
+    launches = int(sum(per_event.get(kname, 1) * cnt for kname, cnt in fam_n.items())) + 10 * args.steps
     # Round 1 is the one round that keys every vertex and every edge (nothing
     # is frozen before it): the full-work figure, with the whole round's
     # algorithmic bytes taken as 12 B per edge (neighbour id, edge label,

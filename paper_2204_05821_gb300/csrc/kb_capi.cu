@@ -142,6 +142,7 @@ struct Plan {
     bool reorder = false;  // locality order of the gather (RoundParams::perm)
     int subject = 0;       // kb_options::subject (generic CSE rounds when > 0)
     bool freeze = false;   // frozen blocks skip the rounds (RoundParams::frozen)
+    bool dense0 = false;   // one graph: level 0 may take the small-label path (launch_dense_level0)
     bool ext_table = false;  // block table and empty-signature minima live outside the workspace
     bool ext_freeze = false;  // frozen-block state lives outside the workspace
     // the per-graph part (processed CSR, degree classes, hub plan, locality
@@ -161,7 +162,8 @@ struct Plan {
     size_t csr_bytes = 0;
     size_t o_emin = 0, o_med = 0, o_slot = 0, o_table = 0, o_bitmap = 0, o_prefix = 0, o_scan = 0, o_hubv = 0, o_chunk = 0, o_setoff = 0,
            o_chunkhub = 0, o_chunkext = 0, o_perm = 0, o_gat = 0, o_colr = 0, o_hist = 0, o_ownkey = 0, o_acc = 0, o_cnt = 0, o_sets = 0,
-           o_frozen = 0, o_fmin = 0, o_edgeless = 0, o_shared = 0, o_minof = 0, o_bm2 = 0, o_moved = 0, o_mark = 0;
+           o_frozen = 0, o_fmin = 0, o_edgeless = 0, o_shared = 0, o_minof = 0, o_bm2 = 0, o_moved = 0, o_mark = 0,
+           o_dense = 0;
     size_t total = 0;
 };
 
@@ -250,6 +252,7 @@ void layout_round(Plan& P) {
     P.o_bm2 = take(P.freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_moved = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
     P.o_mark = take(own_freeze ? sizeof(uint32_t) * (size_t)nw : 0);
+    P.o_dense = take(P.dense0 ? (sizeof(uint32_t) + sizeof(uint2)) * (size_t)kb::kDenseLabels : 0);
     P.total = off;
 }
 
@@ -416,6 +419,7 @@ void resolve_call_fields(Plan& P, const kb_options* opt, int rounds, bool multi,
     // incremental refinement plans without, and generic CSE keys need not
     // hold the own previous block
     P.freeze = (rounds >= 0 || multi) && P.subject == KB_SUBJECT_PREVIOUS && opt->rekey_all == 0;
+    P.dense0 = !multi;
     P.med_split = pick_field(opt->medium_split, T ? T->medium_split : 0, kb::kDefaultMedSplit);
     P.warp_verts = pick_field(opt->small_task_vertices, T ? T->small_task_vertices : 0, kb::kDefaultWarpVerts);
     float lf = opt->load_factor > 0.f ? opt->load_factor : (T ? T->load_factor : 0.f);
@@ -537,6 +541,8 @@ struct Prepared {
     int bm_cur = 0;
     uint32_t* moved = nullptr;
     uint32_t* mark = nullptr;
+    uint32_t* dense_min = nullptr;  // launch_dense_labels / launch_dense_level0 (Plan::dense0)
+    uint2* dense_pair = nullptr;
     bool compact = false;  // small-kernel windows skip frozen vertices (many frozen)
     bool sparse = false;   // fewer than 1/64 of the vertices refine: long warp tasks
     // A caller-held block table (ext_cap slots) and empty-signature minima
@@ -730,6 +736,10 @@ kb_status prepare(kb_context* ctx, const kb_graph* g, const kb_options* opt, Pre
     if (P.reorder) p.gat = reinterpret_cast<int32_t*>(ws + P.o_gat);
     R.prefix = reinterpret_cast<uint2*>(ws + P.o_prefix);
     R.scan_tmp = reinterpret_cast<uint32_t*>(ws + P.o_scan);
+    if (P.dense0) {
+        R.dense_min = reinterpret_cast<uint32_t*>(ws + P.o_dense);
+        R.dense_pair = reinterpret_cast<uint2*>(ws + P.o_dense + align_up(sizeof(uint32_t) * kb::kDenseLabels));
+    }
     R.total_chunks = P.n_chunks;
     R.set_bytes = sizeof(uint64_t) * (size_t)P.set_slots;
     if (!R.ext_table) {
@@ -787,8 +797,21 @@ kb_status launch_level0(kb_context* ctx, Prepared& R, const int32_t* key, int32_
     R.p.prev = key;
     R.p.frozen = nullptr;
     R.p.frozen_min = nullptr;
-    kb::launch_small_round(R.p, true, false, s);
-    kb::launch_renumber(R.p, R.prefix, R.scan_tmp, out, s);
+    // small non-negative keys (one graph): each label's smallest vertex
+    // directly; the check for the range costs one host round trip
+    bool dense = false;
+    if (key && R.dense_min && !kb::batched(R.p) && R.p.n > 0) {
+        KB_CUDA(ctx, cudaMemsetAsync(R.dense_min, 0xff, sizeof(uint32_t) * kb::kDenseLabels, s));
+        kb::launch_dense_labels(R.p.n, key, R.dense_min, ctx->d_ctr, s);
+        KB_TRY(read_counters(ctx));
+        dense = ctx->h_ctr->dense_bad == 0;
+    }
+    if (dense) {
+        kb::launch_dense_level0(R.p, key, R.dense_min, R.dense_pair, R.prefix, R.scan_tmp, out, s);
+    } else {
+        kb::launch_small_round(R.p, true, false, s);
+        kb::launch_renumber(R.p, R.prefix, R.scan_tmp, out, s);
+    }
     // a starting level may mix edgeless vertices with others in one block:
     // only its singletons are frozen in the first round
     if (R.p.shared) {
@@ -2151,6 +2174,7 @@ kb_status kb_destroy(kb_context* ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->row_ev) cudaEventDestroy(ctx->row_ev);
+
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
     delete ctx;

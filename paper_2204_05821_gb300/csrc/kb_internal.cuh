@@ -47,6 +47,7 @@ struct Counters {
     // direction, per kernel family: small, medium, hub
     int64_t keyed_v[3];
     int64_t keyed_e[3];
+    int32_t dense_bad;  // a level-0 key outside [0, kDenseLabels) (launch_dense_labels)
 };
 
 // Everything one refinement round reads and writes.
@@ -262,6 +263,19 @@ void launch_hub_final(const RoundParams& p, cudaStream_t s);
 void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int32_t* out, cudaStream_t s,
                      int64_t stable_count = -1);
 size_t scan_tmp_words(int64_t n_items);
+// Level 0 of one graph whose keys (vertex labels, or a starting partition)
+// are all in [0, kDenseLabels): the label partition straight from each
+// label's smallest vertex, without the block table.  launch_dense_labels
+// lowers lmin[label] (all ones for an unused label) to the label's smallest
+// vertex and sets ctr->dense_bad if some key lies outside the range (the
+// caller then takes the general path).  launch_dense_level0 then writes what
+// the general level-0 pass writes: the minima bitmap and the shared-block
+// marks of p, the rank words, ctr->count, the level (out), minof and the
+// locality order's copy gat.  lpair: kDenseLabels (minimum, id) words of scratch.
+constexpr int kDenseLabels = 8192;
+void launch_dense_labels(int64_t n, const int32_t* key, uint32_t* lmin, Counters* ctr, cudaStream_t s);
+void launch_dense_level0(const RoundParams& p, const int32_t* key, const uint32_t* lmin, uint2* lpair, uint2* rank,
+                         uint32_t* scan_tmp, int32_t* out, cudaStream_t s);
 void launch_fill_i32(int32_t* out, int64_t n, int32_t value, cudaStream_t s);
 // Batched runs: inactive graphs keep the block minima of the previous level.
 void launch_carry_minima(const RoundParams& p, cudaStream_t s);

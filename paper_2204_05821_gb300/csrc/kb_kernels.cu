@@ -462,6 +462,25 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
     }
 }
 
+// The round kept the block count: blocks only split, so it kept every block
+// and its ids are the previous level's.  Under early stop it is the last
+// round, and nothing else of it is needed.  (Apart from assign_frozen_kernel,
+// whose registers bound its occupancy.)
+__global__ void __launch_bounds__(256) stable_copy_kernel(const RoundParams p, int32_t* out, int64_t stable_count) {
+    if (p.ctr->count != stable_count) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(p.prev) | reinterpret_cast<uintptr_t>(out)) & 15) == 0) {
+        const int64_t n4 = p.n >> 2;  // 16-byte copies while both rows allow them
+        const int4* src = reinterpret_cast<const int4*>(p.prev);
+        int4* dst = reinterpret_cast<int4*>(out);
+        for (int64_t i = t; i < n4; i += stride) dst[i] = __ldcs(src + i);
+        done = n4 << 2;
+    }
+    for (int64_t v = done + t; v < p.n; v += stride) out[v] = p.prev[v];
+}
+
 // Canonical ids of a stratified round with frozen blocks (RoundParams::minof;
 // one graph, or several at once): assign_kernel's work with every lane of a warp on one
 // bitmap word (a warp-uniform loop), so that the moved vertices (re-keyed
@@ -473,14 +492,8 @@ __global__ void __launch_bounds__(256) assign_kernel(const RoundParams p, const 
 __global__ void __launch_bounds__(256) assign_frozen_kernel(const RoundParams p, const uint2* rank, int32_t* out,
                                                              uint32_t* moved, int64_t stable_count) {
     __shared__ uint32_t s_mark[kMarkCache];
-    if (stable_count >= 0 && p.ctr->count == stable_count) {
-        // The round kept the block count: blocks only split, so it kept every
-        // block and its ids are the previous level's.  Under early stop it is
-        // the last round, and nothing else of it is needed.
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) out[v] = p.prev[v];
-        return;
-    }
+    // a round that kept the block count is copied by stable_copy_kernel
+    if (stable_count >= 0 && p.ctr->count == stable_count) return;
     for (int i = threadIdx.x; i < kMarkCache; i += blockDim.x) s_mark[i] = kNoMark;
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -837,6 +850,83 @@ __global__ void __launch_bounds__(256) clear_hub_sets_kernel(const RoundParams p
     }
 }
 
+// ----------------------------------------------------------------------------
+// Level 0 over small labels.  Vertices of a warp are consecutive, so the
+// smallest vertex of a group of lanes with one label is its lowest lane.
+// ----------------------------------------------------------------------------
+constexpr int kDenseThreads = 512;
+
+__global__ void __launch_bounds__(kDenseThreads) dense_label_min_kernel(int64_t n, const int32_t* key, uint32_t* lmin,
+                                                                         Counters* ctr) {
+    __shared__ uint32_t s_min[kDenseLabels];
+    for (int i = threadIdx.x; i < kDenseLabels; i += blockDim.x) s_min[i] = 0xffffffffu;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    bool bad = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t v = base + lane;
+        const int32_t l = v < n ? __ldcs(key + v) : 0;
+        const bool in = v < n && (uint32_t)l < (uint32_t)kDenseLabels;
+        bad |= v < n && !in;
+        const unsigned grp = __match_any_sync(kFull, in ? (uint32_t)l : 0xffffffffu);
+        if (in && lane == __ffs(grp) - 1 && (uint32_t)v < s_min[l]) atomicMin(&s_min[l], (uint32_t)v);
+    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(&ctr->dense_bad, 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kDenseLabels; i += blockDim.x)
+        if (s_min[i] != 0xffffffffu) atomicMin(&lmin[i], s_min[i]);
+}
+
+// Every used label's smallest vertex is a block minimum.
+__global__ void dense_mark_kernel(const RoundParams p, const uint32_t* lmin) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= kDenseLabels) return;
+    const uint32_t m = lmin[l];
+    if (m != 0xffffffffu) atomicOr(&p.bitmap[m >> 5], 1u << (m & 31));
+}
+
+// (smallest vertex, canonical id) of every used label
+__global__ void dense_ids_kernel(const uint32_t* lmin, const uint2* rank, uint2* lpair) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= kDenseLabels) return;
+    const uint32_t m = lmin[l];
+    uint32_t id = 0u;
+    if (m != 0xffffffffu) {
+        const uint2 rw = rank[m >> 5];
+        id = rw.x + __popc(rw.y & ((1u << (m & 31)) - 1u));
+    }
+    lpair[l] = make_uint2(m, id);
+}
+
+// The level, minof, the locality order's copy and the shared-block marks (a
+// block is shared when a vertex other than its smallest member has its label;
+// each CTA marks a label once).  The 64 KB label table stays in L1.
+__global__ void __launch_bounds__(256) dense_assign_kernel(const RoundParams p, const int32_t* key,
+                                                           const uint2* lpair, int32_t* out) {
+    __shared__ uint32_t s_marked[kDenseLabels / 32];
+    for (int i = threadIdx.x; i < kDenseLabels / 32; i += blockDim.x) s_marked[i] = 0u;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        const uint32_t l = (uint32_t)__ldcs(key + v);
+        if (l >= (uint32_t)kDenseLabels) {  // the keys changed since they were checked
+            set_error(p.ctr, kErrInvalid);
+            continue;
+        }
+        const uint2 e = __ldg(lpair + l);
+        const uint32_t mn = e.x;
+        out[v] = (int32_t)e.y;
+        if (p.perm) p.gat[p.perm[v]] = (int32_t)mn;  // the block by its smallest member
+        if (mn != (uint32_t)v) {
+            if (p.minof) p.minof[v] = mn;
+            const uint32_t bit = 1u << (l & 31);
+            if (p.shared && !(s_marked[l >> 5] & bit) && !(atomicOr(&s_marked[l >> 5], bit) & bit))
+                atomicOr(&p.shared[mn >> 5], 1u << (mn & 31));
+        }
+    }
+}
+
 // rank of every graph's first vertex (the first vertex of a graph is always
 // the smallest member of its block)
 __global__ void graph_base_kernel(const RoundParams p, const uint2* rank) {
@@ -1021,12 +1111,35 @@ void launch_renumber(const RoundParams& p, uint2* rank, uint32_t* scan_tmp, int3
     }
     if (p.minof) {
         if (p.moved && p.perm) cudaMemsetAsync(p.moved, 0, sizeof(uint32_t) * (size_t)nw, s);
+        if (p.n > 0 && stable_count >= 0)
+            stable_copy_kernel<<<grid_for(p.n, 256) < 1216 ? grid_for(p.n, 256) : 1216, 256, 0, s>>>(p, out,
+                                                                                                 stable_count);
         if (p.n > 0) assign_frozen_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, rank, out, p.moved, stable_count);
         if (p.moved) count_bits_kernel<<<grid_for(nw, 256) < 1216 ? grid_for(nw, 256) : 1216, 256, 0, s>>>(
             p.moved, nw, &p.ctr->moved);
         return;
     }
     if (p.n > 0) assign_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, rank, out);
+}
+
+void launch_dense_labels(int64_t n, const int32_t* key, uint32_t* lmin, Counters* ctr, cudaStream_t s) {
+    if (n <= 0) return;
+    int64_t grid = (n + kDenseThreads - 1) / kDenseThreads;
+    if (grid > 152 * 4) grid = 152 * 4;  // each CTA flushes its label table once
+    dense_label_min_kernel<<<(unsigned)grid, kDenseThreads, 0, s>>>(n, key, lmin, ctr);
+}
+
+void launch_dense_level0(const RoundParams& p, const int32_t* key, const uint32_t* lmin, uint2* lpair, uint2* rank,
+                         uint32_t* scan_tmp, int32_t* out, cudaStream_t s) {
+    if (p.n <= 0) return;
+    const int64_t nw = (p.n >> 5) + 1;
+    const int64_t nb = (nw + kScanTile - 1) / kScanTile;
+    dense_mark_kernel<<<(kDenseLabels + 255) / 256, 256, 0, s>>>(p, lmin);
+    popc_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp);
+    scan_block_sums_kernel<<<1, kScanThreads, 0, s>>>(scan_tmp, nb, p.ctr);
+    popc_scan_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(p.bitmap, nw, scan_tmp, nullptr, rank);
+    dense_ids_kernel<<<(kDenseLabels + 255) / 256, 256, 0, s>>>(lmin, rank, lpair);
+    dense_assign_kernel<<<grid_for(p.n, 256), 256, 0, s>>>(p, key, lpair, out);
 }
 
 void launch_carry_minima(const RoundParams& p, cudaStream_t s) {

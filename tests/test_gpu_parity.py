@@ -483,3 +483,41 @@ def test_clean_blocks_are_skipped(ctx):
     keyed = [sum(v for v, _ in w.values()) for w in work]
     assert keyed[0] == g.n
     assert all(v <= 500 for v in keyed[2:]), keyed
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_small_label_level0_boundaries(ctx, power_law, d):
+    # level 0 over keys in [0, 8192) takes each label's smallest vertex
+    # directly; other keys go through the block table.  Moving the labels
+    # across the boundary (8191 -> 8192, or below 0) keeps the partition, so
+    # every level stays identical, and equal to the oracle's.
+    g = graphgen.Graph(n=power_law.n, m=power_law.m, row_offsets=power_law.row_offsets, col=power_law.col,
+                       elabel=power_law.elabel, vlabel=power_law.vlabel.copy())
+    base = (power_law.vlabel.astype(np.int64) % 3) * 4095  # 0, 4095, 8190
+    ref = None
+    for shift in (0, 1, 2, -8191):  # 8191 stays inside the range; 8192 and negative keys do not
+        g.vlabel = (base + shift).astype(np.int32)
+        for rekey in (False, True):
+            got, _, _ = gpu_levels(ctx, g, d, True, True, 6, early_stop=False, rekey_all=rekey)
+            if ref is None:
+                ref = got
+                L, _, _ = oracle.refine_graph(g, d, True, True, k=6, early_stop=False)
+                assert np.array_equal(got, L)
+            assert np.array_equal(got, ref), (shift, rekey)
+        assert np.array_equal(gpu_levels(ctx, g, d, True, True, 6, early_stop=False, reorder=2)[0], ref), shift
+
+
+def test_small_label_level0_single_vertex_labels(ctx, er_tiny):
+    # up to 8192 distinct keys (dense), every vertex its own label (keys up
+    # to n - 1 > 8192), one label for all; plain and prepared (locality order)
+    ids = np.arange(er_tiny.n, dtype=np.int32)
+    for lab in (ids % 8192, ids[::-1] % 8192, ids, np.zeros(er_tiny.n, dtype=np.int32),
+                np.full(er_tiny.n, 8191, dtype=np.int32)):
+        g = graphgen.Graph(n=er_tiny.n, m=er_tiny.m, row_offsets=er_tiny.row_offsets, col=er_tiny.col,
+                           elabel=er_tiny.elabel, vlabel=lab)
+        assert_same(ctx, g, 0, True, True, 5)
+        L, C, _ = oracle.refine_graph(g, 0, True, True, k=5)
+        dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+        with ctx.prepare(dg, kb.Options(reorder=2)) as pg:
+            res = ctx.refine(pg, 5, kb.Options(reorder=2))
+            assert np.array_equal(res.levels.cpu().numpy(), L) and np.array_equal(res.counts, C)
