@@ -47,9 +47,9 @@ METRIC = "k-bisim edges/s per round"
 # must match.
 KERNEL_HEADERS = ("paper_2204_05821_gb300/csrc/kb_device.cuh", "paper_2204_05821_gb300/csrc/kb_internal.cuh")
 TRAFFIC_PER_ALGO_BYTE = {
-    "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "064abe71312d35b42630cded0b47dd30bf5896df", 2.205),
-    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "418b1ae92c98051647a17b59a2bcce530bd73462", 5.520),
-    "medium": ("paper_2204_05821_gb300/csrc/kb_medium.cu", "e9661aa9c66da9953eecc3c8dc423cc6aaf447c3", 1.964),
+    "hub_chunk": ("paper_2204_05821_gb300/csrc/kb_kernels.cu", "9734ccc8cb4fa02be0fff878a6f1f298d83277e3", 2.206),
+    "small": ("paper_2204_05821_gb300/csrc/kb_small.cu", "5fe82d2a0a4fa2dc30c2c8474321b9501eb6d7f1", 5.522),
+    "medium": ("paper_2204_05821_gb300/csrc/kb_medium.cu", "98941f79c3ef798d184d25adb0e052b61de81aa0", 1.965),
 }
 
 

@@ -851,28 +851,43 @@ __global__ void __launch_bounds__(256) clear_hub_sets_kernel(const RoundParams p
 }
 
 // ----------------------------------------------------------------------------
-// Level 0 over small labels.  Vertices of a warp are consecutive, so the
-// smallest vertex of a group of lanes with one label is its lowest lane.
+// Level 0 over small labels.  A shared minimum is read before the atomicMin
+// that would lower it: after a label's first members, a CTA's later (larger)
+// vertices leave its minimum alone.
 // ----------------------------------------------------------------------------
 constexpr int kDenseThreads = 512;
+
+__device__ __forceinline__ void see_label(uint32_t* s_min, int64_t v, int32_t l, bool& bad) {
+    if ((uint32_t)l >= (uint32_t)kDenseLabels) {
+        bad = true;
+        return;
+    }
+    if ((uint32_t)v < s_min[l]) atomicMin(&s_min[l], (uint32_t)v);
+}
 
 __global__ void __launch_bounds__(kDenseThreads) dense_label_min_kernel(int64_t n, const int32_t* key, uint32_t* lmin,
                                                                          Counters* ctr) {
     __shared__ uint32_t s_min[kDenseLabels];
     for (int i = threadIdx.x; i < kDenseLabels; i += blockDim.x) s_min[i] = 0xffffffffu;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
     bool bad = false;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t v = base + lane;
-        const int32_t l = v < n ? __ldcs(key + v) : 0;
-        const bool in = v < n && (uint32_t)l < (uint32_t)kDenseLabels;
-        bad |= v < n && !in;
-        const unsigned grp = __match_any_sync(kFull, in ? (uint32_t)l : 0xffffffffu);
-        if (in && lane == __ffs(grp) - 1 && (uint32_t)v < s_min[l]) atomicMin(&s_min[l], (uint32_t)v);
+    int64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(key) & 15) == 0) {
+        const int64_t n4 = n >> 2;  // four keys per 16-byte load
+        const int4* k4 = reinterpret_cast<const int4*>(key);
+        for (int64_t i = t; i < n4; i += stride) {
+            const int4 q = __ldcs(k4 + i);
+            see_label(s_min, 4 * i, q.x, bad);
+            see_label(s_min, 4 * i + 1, q.y, bad);
+            see_label(s_min, 4 * i + 2, q.z, bad);
+            see_label(s_min, 4 * i + 3, q.w, bad);
+        }
+        done = n4 << 2;
     }
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(&ctr->dense_bad, 1);
+    for (int64_t v = done + t; v < n; v += stride) see_label(s_min, v, __ldcs(key + v), bad);
+    if (bad) atomicOr(&ctr->dense_bad, 1);
     __syncthreads();
     for (int i = threadIdx.x; i < kDenseLabels; i += blockDim.x)
         if (s_min[i] != 0xffffffffu) atomicMin(&lmin[i], s_min[i]);
