@@ -26,7 +26,8 @@ namespace {
 // ----------------------------------------------------------------------------
 // Hub chunks: kChunk edges of one hub per CTA.  Chunk-local dedup in shared
 // memory, then the chunk's distinct pairs go into the hub's global set; pairs
-// new to the hub are appended to its list and summed into its hash.
+// new to the hub (the CAS that placed them found the slot empty) are counted
+// and summed into its hash.
 // ----------------------------------------------------------------------------
 template <int kChunk>
 __global__ void __launch_bounds__(kHubThreads) hub_chunk_kernel(const RoundParams p) {
