@@ -204,8 +204,9 @@ kb_status kb_set_workspace(kb_context* ctx, void* device_ptr, size_t bytes);
  *   levels_computed  HOST, may be NULL; the last level actually refined (< k when
  *                    early_stop found a stable partition; rows after it are copies)
  * Synchronises the stream once per round to read the block count, and once
- * more at level 0 when the vertex labels may all lie in [0, 8192) (one graph:
- * such labels take a path without the block table). */
+ * more at level 0 when it has keys (vertex labels or a starting partition): a
+ * range check decides whether they all lie in [0, 8192), which takes a path
+ * without the block table. */
 kb_status kb_refine(kb_context* ctx, const kb_graph* g, const kb_options* opt, int k,
                     int32_t* levels, int64_t* counts, int* levels_computed);
 
