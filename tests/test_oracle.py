@@ -353,6 +353,27 @@ def test_vertex_renumbering_invariance():
             assert partition(A[i]) == partition(B[i][perm])
 
 
+def test_label_renaming_invariance():
+    # labels enter only through equality (Defs. "edge-labeled-fw-bisimulation",
+    # "vertex-labeled-bw-bisimulation") and ids are ranks of smallest members,
+    # so injective renamings of vertex and edge labels, into large and negative
+    # values too, leave every level identical, not just the same partitions
+    g = graphgen.erdos_renyi(600, 2400, 6, 4, seed=12)
+    rng = np.random.Generator(np.random.PCG64(5))
+    vmap = rng.choice(np.array([-2147483648, -7, 0, 8191, 8192, 2147483647], dtype=np.int64), 6, replace=False)
+    emap = rng.choice(np.array([-2147483648, -1, 9000, 2147483647], dtype=np.int64), 4, replace=False)
+    src, dst, lab = g.edges()
+    h = graphgen.from_edges(g.n, src, dst, emap[lab].astype(np.int32), vmap[g.vlabel].astype(np.int32))
+    for d in (0, 1, 2):
+        A, CA, _ = oracle.refine_graph(g, d, True, True, k=6, early_stop=False)
+        B, CB, _ = oracle.refine_graph(h, d, True, True, k=6, early_stop=False)
+        assert np.array_equal(A, B) and np.array_equal(CA, CB)
+    # a non-injective renaming merges classes: level 0 gets coarser
+    merged = graphgen.from_edges(g.n, src, dst, lab, (g.vlabel // 2).astype(np.int32))
+    L, C, _ = oracle.refine_graph(merged, 0, True, True, k=1, early_stop=False)
+    assert C[0] < len(np.unique(g.vlabel))
+
+
 def test_initial_partition_equals_label_partition():
     g = graphgen.erdos_renyi(400, 1500, 5, 3, seed=4)
     A, CA, _ = oracle.refine_graph(g, 0, True, True, k=6, early_stop=False)
