@@ -380,6 +380,21 @@ def test_refine_from_matches_full_run(ctx, er_tiny):
             assert np.array_equal(res.counts[j:], C[j:])
 
 
+def test_start_partition_rows_at_any_alignment(ctx):
+    # a starting partition passed as a row of a levels array: with n odd its
+    # rows start at every 4-byte offset modulo 16 (the level-0 label pass
+    # reads 16 bytes at a time only from 16-byte aligned keys)
+    g = graphgen.erdos_renyi(3001, 12000, 5, 3, seed=17)
+    L, C, _ = oracle.refine_graph(g, 0, True, True, k=6, early_stop=False)
+    dg = kb.DeviceGraph.from_numpy(g, "cuda:0")
+    rows = torch.from_numpy(L).to("cuda:0")
+    for j in (0, 1, 2, 3):
+        assert (rows[j].data_ptr() - rows.data_ptr()) % 16 == (4 * j * g.n) % 16
+        res = ctx.refine_from(dg, rows[j], j, 6, kb.Options(early_stop=False))
+        assert np.array_equal(res.levels.cpu().numpy()[j:], L[j:])
+        assert np.array_equal(res.counts[j:], C[j:])
+
+
 def test_initial_partition(ctx, er_tiny):
     init = (er_tiny.vlabel.astype(np.int64) * 1000003 % 7 - 3).astype(np.int32)
     L, C, _ = oracle.refine_graph(er_tiny, 0, False, True, k=6, early_stop=False, initial=init)
